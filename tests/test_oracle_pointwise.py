@@ -1,0 +1,119 @@
+"""Pins of the oracle's pointwise chain (no GPU): PW92 correlation, q0,
+saturation (Eq. Sat), q mesh and the cardinal cubic splines (Eq. fofx).
+
+* PW92: the coefficient of ln r_s in the high-density limit is the exact
+  Gell-Mann--Brueckner value (1 - ln 2)/pi^2; derivatives match finite
+  differences.
+* q0: the uniform-gas value k_F - (4 pi/3) eps_c, positivity, derivatives.
+* h: h(x) ~ x below q_c, h -> q_c above, monotone, derivative.
+* Splines: partition of unity, exact for linear data, identical to scipy's
+  natural cubic spline through arbitrary data.
+* theta derivatives: analytic vs finite differences.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def fd(f, x, h):
+    return (f(x + h) - f(x - h)) / (2 * h)
+
+
+def test_pw92_high_density_log_coefficient():
+    # eps_c ~ A ln rs + const for rs -> 0, with A = (1 - ln 2)/pi^2 exactly
+    r1, r2 = 1e-10, 1e-12
+    e1, _ = O.pw92_eps_c(r1)
+    e2, _ = O.pw92_eps_c(r2)
+    slope = (e1 - e2) / (np.log(r1) - np.log(r2))
+    assert abs(slope - (1 - np.log(2)) / np.pi ** 2) < 2e-5
+
+
+def test_pw92_negative_and_derivative():
+    rs = np.array([0.1, 0.5, 1.0, 2.0, 5.0, 20.0, 100.0])
+    e, de = O.pw92_eps_c(rs)
+    assert np.all(e < 0)
+    np.testing.assert_allclose(de, fd(lambda r: O.pw92_eps_c(r)[0], rs, 1e-6 * rs), rtol=1e-7)
+
+
+def test_q0_uniform_gas_and_derivatives():
+    n = np.array([1e-6, 1e-3, 0.01, 0.1, 1.0, 5.0])
+    g = np.zeros_like(n)
+    q0, dqn, dqg = O.q0_unsaturated(n, g)
+    kF = (3 * np.pi ** 2 * n) ** (1 / 3)
+    ec, _ = O.pw92_eps_c((3 / (4 * np.pi * n)) ** (1 / 3))
+    np.testing.assert_allclose(q0, kF - 4 * np.pi / 3 * ec, rtol=1e-14)
+    assert np.all(q0 > 0)
+    g = np.array([1e-7, 1e-3, 0.05, 0.2, 3.0, 1.0])
+    q0, dqn, dqg = O.q0_unsaturated(n, g)
+    np.testing.assert_allclose(dqn, fd(lambda x: O.q0_unsaturated(x, g)[0], n, 1e-5 * n), rtol=1e-5)
+    np.testing.assert_allclose(dqg * g, fd(lambda x: O.q0_unsaturated(n, x)[0], g, 1e-5 * g), rtol=1e-5)
+    assert np.all(q0 > 0)
+
+
+def test_saturation_limits_and_derivative():
+    qc, mc = 5.0, 12
+    x = np.array([1e-3, 0.1, 0.5, 1.0])
+    h, _ = O.saturate(x, qc, mc)
+    # h = x + O((x/qc)^(mc+1)) for x << qc
+    assert np.all(np.abs(h - x) <= 2 * qc * (x / qc) ** (mc + 1) + 1e-15)
+    xs = np.linspace(0.01, 30, 3000)
+    hs, dh = O.saturate(xs, qc, mc)
+    assert np.all(np.diff(hs) >= 0) and np.all(hs <= qc)
+    assert abs(O.saturate(100.0, qc, mc)[0] - qc) == 0.0
+    np.testing.assert_allclose(dh, fd(lambda t: O.saturate(t, qc, mc)[0], xs, 1e-6), rtol=1e-5, atol=1e-9)
+
+
+def test_q_mesh_is_logarithmic():
+    p = O.Params()
+    qm = O.q_mesh(p)
+    d = np.diff(qm)
+    np.testing.assert_allclose(d[1:] / d[:-1], p.lam, rtol=1e-12)
+    assert qm[0] == p.q_1 and abs(qm[-1] - p.q_c) < 1e-14
+
+
+def test_cardinal_splines():
+    from scipy.interpolate import CubicSpline
+    p = O.Params()
+    qm = O.q_mesh(p)
+    M = O.cardinal_M(qm)
+    q = np.concatenate([np.random.default_rng(0).uniform(qm[0], qm[-1], 500), qm])
+    P, dP = O.cardinal_eval(qm, M, q)
+    np.testing.assert_allclose(P.sum(0), 1.0, atol=1e-12)
+    np.testing.assert_allclose(dP.sum(0), 0.0, atol=1e-9)
+    np.testing.assert_allclose((qm[:, None] * P).sum(0), q, rtol=1e-12)
+    f = np.random.default_rng(3).normal(size=qm.size)
+    cs = CubicSpline(qm, f, bc_type="natural")
+    np.testing.assert_allclose((f[:, None] * P).sum(0), cs(q), rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose((f[:, None] * dP).sum(0), cs(q, 1), rtol=1e-8, atol=1e-8)
+    # on a knot p_a = delta
+    Pk, _ = O.cardinal_eval(qm, M, qm)
+    np.testing.assert_allclose(Pk, np.eye(qm.size), atol=1e-13)
+
+
+def test_theta_derivatives_match_fd(table):
+    rng = np.random.default_rng(5)
+    n = rng.uniform(1e-3, 2.0, 40)
+    g = rng.normal(size=(3, 40)) * rng.uniform(0.0, 2.0, 40)
+    pw = O.pointwise(n, g, table)
+    # d theta_a / d n = p_a + n p_a' dq/dn
+    dth_dn = pw["P"] + pw["n"] * pw["dP"] * pw["dq_dn"]
+    h = 1e-6 * n
+    tp = O.pointwise(n + h, g, table)["theta"]
+    tm = O.pointwise(n - h, g, table)["theta"]
+    np.testing.assert_allclose(dth_dn, (tp - tm) / (2 * h), rtol=1e-5, atol=1e-8)
+    # d theta_a / d g_c = n p_a' (dq/d|g|)/|g| g_c
+    for c in range(3):
+        e = np.zeros_like(g)
+        e[c] = 1e-6
+        tp = O.pointwise(n, g + e, table)["theta"]
+        tm = O.pointwise(n, g - e, table)["theta"]
+        an = pw["n"] * pw["dP"] * pw["dq_dg"] * g[c]
+        np.testing.assert_allclose(an, (tp - tm) / 2e-6, rtol=1e-5, atol=1e-8)
+
+
+def test_theta_zero_below_density_floor(table):
+    n = np.array([0.0, 1e-13, -1.0, np.nan, 0.5])
+    g = np.zeros((3, 5))
+    pw = O.pointwise(n, g, table)
+    assert np.all(pw["theta"][:, :4] == 0) and np.all(pw["theta"][:, 4] > -1)
