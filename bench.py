@@ -1,0 +1,342 @@
+"""Benchmark: grid points per second of one E_c^nl + v_nl evaluation
+(Nq = 20, FP32 with FP64 energy) on the 180 x 180 x 72 double-wall nanotube
+cell, through the C ABI of libvdwnl.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) are independent
+replicas: the method has no exchange between cells, so each rank evaluates
+its own cell and the value is the points of all ranks over the slowest
+rank's time (weak scaling).
+
+--impl reference times the FP64 CPU oracle (the only other implementation:
+the paper ships no code) on the host cores, on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "grid points/s for E_c^nl+v_nl (Nq=20, FP32)"
+UNIT = "grid_points/s"
+WORKLOAD = "dwnt_180x180x72_nq20"
+HBM_FALLBACK = 6800.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+# algorithmic bytes per grid point of each stage (FP32 fields, complex64
+# half spectrum with Nh/N1 of the points); see the design doc
+def stage_bytes_per_point(Nq, N1):
+    h = (N1 // 2 + 1) / N1
+    return {
+        "pointwise": 16 + 5,                       # n, grad in; t, k out
+        "theta_plane": 9 + Nq * 8 * h,             # n, t, k in; theta(G) out
+        "pencil_contract": 2 * Nq * 8 * h,         # theta(G) in, u(G) out
+        "energy_final": 0.0,
+        "assemble": Nq * 8 * h + 16 + 5 + 4 + 3 * 8 * h,  # u(G), n, grad, t, k in; v_loc, w(G) out
+        "pencil_div": 3 * 8 * h + 8 * h,           # w(G) in, D.w(G) out
+        "div_final": 8 * h + 4 + 4,                # D.w(G), v_loc in; v out
+    }
+
+
+def b_alg(Nq):
+    """Whole-call algorithmic bytes per point, 16 Nq + 76 (one HBM round trip
+    of the Nq spectra per direction, inputs and outputs once)."""
+    return 16 * Nq + 76
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, name):
+        setattr(self, name, time.time())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for t, l in self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((t, float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        t0, t1 = getattr(self, "start", 0), getattr(self, "stop", 1e30)
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        use = inside if inside else rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in use:
+            for nm, val in zip(names, r[3][1:]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "reasons": sorted(reasons), "samples": len(use),
+                "window": "timed region" if inside else "whole run (no sample fell inside the timed region)"}
+
+
+def oracle_sample_rate(timeout=600):
+    """Time the FP64 oracle (as it stands) on one axial period of the tube
+    (180 x 180 x 18 points, the same grid spacing and density recipe) in a
+    single-threaded child process; returns (points/s, seconds, points)."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+import oracle as O
+from paper_0812_0244_gb300 import synthetic as S
+T = O.kernel_table(O.Params())
+d = S.tube_density(0, shape=(18, 180, 180), cell_ang=(25.0, 25.0, 2.46))
+n = d["n"].astype(np.float32).astype(np.float64)
+g = d["grad"].astype(np.float32).astype(np.float64)
+t0 = time.perf_counter()
+r = O.energy_potential(n, g, d["L"], T)
+dt = time.perf_counter() - t0
+print(json.dumps({"points": int(n.size), "seconds": dt, "E": r["E"]}))
+""" % ROOT
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["points"] / d["seconds"], d["seconds"], d["points"]
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    K = max(1, min(args.steps, 4))
+    W = min(args.warmup, 1)
+    total_pts, total_s = 0, 0.0
+    for i in range(W + K):
+        rate, sec, pts = oracle_sample_rate()
+        if i >= W:
+            total_pts += pts
+            total_s += sec
+    value = total_pts / total_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "one axial period, 180x180x18 points"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "FP64 numpy/C oracle, E and v on one axial period of the tube "
+                                       "(180x180x18 of the 180x180x72 grid), single thread, %d steps" % K},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_0812_0244_gb300 import synthetic as S
+    from paper_0812_0244_gb300 import vdwnl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # CPU baseline first (child process, before this process does GPU work)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sec, pts = oracle_sample_rate()
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 numpy/C oracle, E and v on one axial period of the tube (180x180x18 of the "
+                         "180x180x72 grid, %d points, %.1f s), single thread" % (pts, sec)}
+
+    d = S.tube_density(rank)
+    n_h = d["n"].astype(np.float32)
+    g_h = d["grad"].astype(np.float32)
+    N = n_h.size
+    params = vdwnl.Params()
+    ctx = vdwnl.VdwNL(params)
+    ctx.plan(n_h.shape, d["L"])
+    n = torch.tensor(n_h, device=dev)
+    g = torch.tensor(g_h, device=dev)
+    E = torch.empty(3, dtype=torch.float64, device=dev)
+    v = torch.empty_like(n)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctx.energy_potential(n, g, E, v)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        clk.mark("start")
+        for i in range(K):
+            flush.zero_()
+            starts[i].record(stream)
+            ctx.energy_potential(n, g, E, v)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        clk.mark("stop")
+        barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / K
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N / (ms * 1e-3)
+    Eh = E.cpu().numpy()
+
+    # per-stage durations (separate, untimed iterations with stage events)
+    ctx.profile(True)
+    acc = {}
+    reps = min(K, 50)
+    for _ in range(reps):
+        flush.zero_()
+        ctx.energy_potential(n, g, E, v)
+        for k2, t2 in ctx.profile_read().items():
+            acc[k2] = acc.get(k2, 0.0) + t2 / reps
+    ctx.profile(False)
+    sb = stage_bytes_per_point(params.Nq, n_h.shape[2])
+    top = max((k2 for k2 in acc if k2 != "energy_final"), key=lambda k2: acc[k2])
+    peak, peak_kind = measured_peaks()
+    achieved = sb[top] * N / (acc[top] * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(top)
+        except Exception:
+            traffic = None
+
+    # end to end through the host-pointer entry point (pinned buffers)
+    n_p = torch.from_numpy(n_h).pin_memory()
+    g_p = torch.from_numpy(g_h).pin_memory()
+    v_p = torch.empty(n_h.shape, dtype=torch.float32).pin_memory()
+    E_p = np.zeros(3)
+    Ke = max(1, min(K, 50))
+    for _ in range(2):
+        ctx.energy_potential_host(n_p.numpy(), g_p.numpy(), E_p, v_p.numpy())
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        ctx.energy_potential_host(n_p.numpy(), g_p.numpy(), E_p, v_p.numpy())
+    e2e_s = (time.perf_counter() - t0) / Ke
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank == 0:
+        clocks = clk.summary()
+        stage_frac = {k2: round(sb[k2] * N / (t2 * 1e-3) / 1e9 / peak, 4) for k2, t2 in acc.items() if sb[k2] > 0}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [180, 180, 72], "Nq": params.Nq, "cell_angstrom": [25, 25, 9.84],
+                       "sites": int(d["natoms"]), "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "energy_fp64": float(Eh[0])},
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                         "peak_kind": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind if peak_kind == "measured"
+                         else "fallback 6.8 TB/s", "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "bytes_per_point": sb[top], "launch_ms": acc[top]},
+            "step_roofline": {"bytes_per_point": b_alg(params.Nq),
+                              "achieved_gbs": b_alg(params.Nq) * N / (ms * 1e-3) / 1e9,
+                              "frac": b_alg(params.Nq) * N / (ms * 1e-3) / 1e9 / peak},
+            "stages_ms": {k2: round(t2, 4) for k2, t2 in acc.items()},
+            "stages_hbm_frac": stage_frac,
+            "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
+                    "d2h_bytes_per_step": 4 * N + 24},
+            "gpu_launches": 7 * K,
+            "clocks": clocks,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

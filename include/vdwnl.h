@@ -1,0 +1,171 @@
+/*
+ * vdwnl: the nonlocal van der Waals correlation energy E_c^nl and potential
+ * v_nl of Dion et al. on a periodic real-space grid, evaluated with the
+ * kernel factorisation and FFT method of Roman-Perez and Soler
+ * (arXiv:0812.0244), on one NVIDIA GB300 (sm_103a).
+ *
+ * The boundary follows the paper's statement that the implementation accepts
+ * n(r_i) on a uniform real-space grid and returns the energy and the
+ * potential on the same grid (text after Eq. epsofk).  Every entry point
+ * returns VDW_OK (0) or a negative error code; no C++ exception crosses it.
+ *
+ * Conventions shared by all entry points
+ *   - Grid N1 x N2 x N3 (x = axis 1 fastest): flat index i = i1 + N1 (i2 + N2 i3),
+ *     N = N1 N2 N3.  The cell is orthorhombic with edge lengths L[3] (bohr).
+ *     r_i = (i1 L1/N1, i2 L2/N2, i3 L3/N3).
+ *   - All densities and potentials are in atomic units (bohr, Hartree).
+ *   - "device" pointers are CUDA device (or managed) memory, FP32 unless noted,
+ *     caller-owned.  "host" pointers are ordinary (preferably pinned) memory.
+ *   - stream is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Calls taking a stream only enqueue work on it and return,
+ *     except where a host read-back is documented.
+ *   - Fourier convention: theta(G) = (1/N) sum_i theta_i exp(-i G.r_i),
+ *     G = 2 pi (m1/L1, m2/L2, m3/L3).
+ */
+#ifndef VDWNL_H
+#define VDWNL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define VDW_OK 0
+#define VDW_ERR_ARG (-1)     /* null pointer, non-positive size, bad parameter */
+#define VDW_ERR_SIZE (-2)    /* grid not {2,3,5}-smooth, odd N1 or N3, too large
+                                for on-chip staging, or |G|max > k_max         */
+#define VDW_ERR_CUDA (-3)    /* a CUDA runtime call failed                      */
+#define VDW_ERR_OOM (-4)     /* device allocation failed                         */
+#define VDW_ERR_STATE (-5)   /* call made before vdw_plan                        */
+#define VDW_ERR_UNSUPPORTED (-6) /* Nq not compiled in                           */
+
+/* ---- method parameters --------------------------------------------------
+ * Nq, q_c, m_c   interpolation mesh size (paper: "N_alpha ~ 20"), saturation
+ *                cutoff and order of Eq. (Sat) ("m_c ~ 12 and q_c ~ 5 a.u.").
+ * q_1, lambda    first point and ratio of the logarithmic mesh
+ *                (q_{a+1}-q_a) = lambda (q_a - q_{a-1}), q_Nq = q_c.
+ * d_s            radius of the soft kernel of Eq. (PhiSoft) in
+ *                d = sqrt(d1^2 + d2^2); phi0 is set so that phi4 = 0 on the
+ *                diagonal ray d1 = d2.
+ * na, a_max      Gauss-Legendre nodes in t = atan(a), t in [0, atan(a_max)],
+ *                for the Dion et al. double integral defining phi(d1, d2).
+ * d_asym         phi takes its closed-form large-separation limit
+ *                -12 (4 pi/9)^3 / (d1^2 d2^2 (d1^2 + d2^2)) when
+ *                min(d1, d2) >= d_asym.
+ * r_c, Nr        radial transform of phi_ab(r) cut at r_c, Simpson's rule on
+ *                Nr (even) intervals.
+ * k_max, Nk      uniform k mesh of the radial table, natural cubic spline in k.
+ * n_cs           Gauss-Legendre nodes for the softening constant C_s of
+ *                Eq. (Depsnl).
+ * n_min          points with n <= n_min (or n not finite) carry theta = 0.   */
+typedef struct vdw_params {
+    int Nq;
+    double q_1, q_c, lambda;
+    int m_c;
+    double d_s;
+    int na;
+    double a_max, d_asym;
+    double r_c;
+    int Nr;
+    double k_max;
+    int Nk;
+    int n_cs;
+    double n_min;
+} vdw_params;
+
+/* Fill p with the defaults: Nq 20, q_1 1e-5, q_c 5, lambda 1.2, m_c 12,
+ * d_s 1, na 256, a_max 64, d_asym 8, r_c 100, Nr 4096, k_max 40, Nk 1024,
+ * n_cs 64, n_min 1e-12. */
+int vdw_params_default(vdw_params* p);
+
+/* ---- kernel table (init, FP64 on the GPU) -------------------------------
+ * The radial Fourier transform of the factorised kernel
+ *   phi_ab(k) = 4 pi Int_0^{r_c} r^2 phi_s(q_a r, q_b r) j0(k r) dr
+ * (the paper: phi_ab(k) "can be calculated in spherical coordinates, and
+ * stored in a radial mesh of points k", text after Eq. Eoffk), the soft
+ * kernel of Eq. (PhiSoft), and the softening constant
+ *   C_s = Int_0^{d_s/sqrt2} 4 pi x^2 [phi(x,x) - phi_s(x,x)] dx
+ * of Eq. (Depsnl), all computed in FP64 by kernels on the current device.
+ * Outputs (host, caller-owned, any may be NULL): q_mesh[Nq];
+ * phi_k[Nq*Nq*Nk] with phi_k[(a*Nq + b)*Nk + m] = phi_ab(m k_max/(Nk-1));
+ * phi0; C_s.  Synchronous. */
+int vdw_kernel_table(const vdw_params* p, double* q_mesh, double* phi_k,
+                     double* phi0, double* C_s);
+
+/* ---- context ------------------------------------------------------------ */
+typedef struct vdw_ctx* vdw_handle;
+
+/* Create a context on the current device.  If phi_k (host, FP64, layout as
+ * in vdw_kernel_table) is NULL the table is generated on the GPU by
+ * vdw_kernel_table and C_s is ignored; otherwise phi_k and C_s are used as
+ * given.  The context owns its tables and (after vdw_plan) its workspace.
+ * Synchronous. */
+int vdw_create(vdw_handle* h, const vdw_params* p, const double* phi_k, double C_s);
+
+/* Fix the grid N1 x N2 x N3 and the orthorhombic cell L[3] (bohr) and
+ * allocate the workspace (about (Nq + 3) (N1/2+1) N2 N3 complex FP32 values
+ * plus 5 N bytes).  Requirements: each N_d is {2,3,5}-smooth, 4 <= N_d <= 256,
+ * N1 and N3 even, the largest |G| of the grid <= k_max.  May be called again
+ * to re-plan.  Synchronous. */
+int vdw_plan(vdw_handle h, int n1, int n2, int n3, const double L[3]);
+
+/* E_c^nl and, on request, its potential (device pointers, caller-owned).
+ *   n        [N]    density (FP32)
+ *   grad     [3][N] its gradient, components x, y, z (FP32)
+ *   E        [3]    FP64 device output {E_c^nl, E_soft, Delta E} (Hartree);
+ *                   E_soft is Eq. (Eoffk) with the soft kernel, Delta E the
+ *                   local correction of Eqs. (DEnl, Depsnl); may be NULL.
+ *   v        [N]    output or NULL.
+ *   w        [3][N] output or NULL.
+ * With v != NULL and w == NULL, v is v_nl of Eq. (Vi): (1/dOmega) dE/dn_i
+ * with grad n_j = sum_i D_ji n_i and D the spectral derivative with the
+ * Nyquist components removed, i.e. v = v_loc - sum_c D_c w_c.
+ * With w != NULL, v (if given) receives only v_loc = (1/dOmega) dE/dn_i at
+ * fixed gradient and w receives (1/dOmega) dE/d(grad_c n)_i, leaving the
+ * chain through the gradient to the caller (a finite-difference stencil, or
+ * autograd).
+ * With v == NULL and w == NULL only the energy is computed.
+ * Asynchronous on stream. */
+int vdw_energy_potential(vdw_handle h, const float* n, const float* grad,
+                         double* E, float* v, float* w, void* stream);
+
+/* The same computation on host buffers (n[N], grad[3N] in; E[3], v[N] out):
+ * copies the inputs to context-owned device buffers (allocated on first use),
+ * runs vdw_energy_potential with the full potential, copies E and v back and
+ * synchronises stream before returning. */
+int vdw_energy_potential_host(vdw_handle h, const float* n, const float* grad,
+                              double* E, float* v, void* stream);
+
+/* Number of points of the last completed call whose density was negative or
+ * not finite (they were treated as n = 0).  Synchronises the device. */
+int vdw_last_invalid_points(vdw_handle h, long long* count);
+
+/* Per-stage timing, for measurement.  While enabled, vdw_energy_potential
+ * records a CUDA event on its stream before its first kernel and after each
+ * stage: 0 pointwise (q, interval, Delta E), 1 theta planes + plane FFT,
+ * 2 pencil FFT + contraction + energy, 3 energy reduction, 4 inverse plane
+ * FFT + potential assembly, 5 divergence pencils, 6 final planes.
+ * vdw_profile_read synchronises on the last recorded event and writes the
+ * durations (ms) of the stages the last call ran into ms[0..6] (-1 for stages
+ * it skipped).  Disabled by default; enabling costs 8 event records a call. */
+#define VDW_NSTAGES 7
+int vdw_profile_enable(vdw_handle h, int enable);
+int vdw_profile_read(vdw_handle h, float* ms);
+
+/* Bytes of device memory the context holds. */
+int vdw_workspace_bytes(vdw_handle h, size_t* bytes);
+
+int vdw_destroy(vdw_handle h);
+
+/* Static description of an error code. */
+const char* vdw_error_string(int code);
+
+/* Text of the last error raised on this thread (empty if none). */
+const char* vdw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VDWNL_H */

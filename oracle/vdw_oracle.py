@@ -222,11 +222,17 @@ def _lib():
         os.makedirs(bdir, exist_ok=True)
         so = os.path.join(bdir, "liboracle_dion.so")
         src = os.path.join(_HERE, "dion.c")
-        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        def compile_():
             tmp = so + ".%d.tmp" % os.getpid()
             subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", tmp, src, "-lm"])
             os.replace(tmp, so)
-        lib = ctypes.CDLL(so)
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            compile_()
+        try:
+            lib = ctypes.CDLL(so)
+        except OSError:  # built for another machine
+            compile_()
+            lib = ctypes.CDLL(so)
         P = ctypes.POINTER(ctypes.c_double)
         lib.oracle_dion_phi.argtypes = [ctypes.c_int, P, P, ctypes.c_int, P, P, P, P]
         lib.oracle_dion_phi.restype = None

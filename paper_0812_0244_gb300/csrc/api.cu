@@ -1,0 +1,283 @@
+// C ABI of the vdwnl library (declared in include/vdwnl.h).
+#include "common.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+namespace vdw {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& s) { g_last_error = s; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return (e == cudaErrorMemoryAllocation) ? VDW_ERR_OOM : VDW_ERR_CUDA;
+}
+
+static bool smooth235(int n) {
+    if (n < 1) return false;
+    for (int r : {2, 3, 5})
+        while (n % r == 0) n /= r;
+    return n == 1;
+}
+
+static void free_plan(vdw_ctx* c) {
+    cudaFree(c->d_tw);
+    cudaFree(c->d_spec);
+    cudaFree(c->d_wspec);
+    cudaFree(c->d_t);
+    cudaFree(c->d_k);
+    cudaFree(c->d_epart);
+    cudaFree(c->d_invalid);
+    cudaFree(c->d_acc);
+    cudaFree(c->d_in);
+    cudaFree(c->d_v);
+    cudaFree(c->d_E);
+    c->d_tw = nullptr;
+    c->d_spec = c->d_wspec = nullptr;
+    c->d_t = nullptr;
+    c->d_k = nullptr;
+    c->d_epart = nullptr;
+    c->d_invalid = nullptr;
+    c->d_acc = nullptr;
+    c->d_in = c->d_v = nullptr;
+    c->d_E = nullptr;
+    c->planned = 0;
+}
+
+}  // namespace vdw
+
+using namespace vdw;
+
+extern "C" {
+
+int vdw_params_default(vdw_params* p) {
+    if (!p) return VDW_ERR_ARG;
+    p->Nq = 20;
+    p->q_1 = 1e-5;
+    p->q_c = 5.0;
+    p->lambda = 1.2;
+    p->m_c = 12;
+    p->d_s = 1.0;
+    p->na = 256;
+    p->a_max = 64.0;
+    p->d_asym = 8.0;
+    p->r_c = 100.0;
+    p->Nr = 4096;
+    p->k_max = 40.0;
+    p->Nk = 1024;
+    p->n_cs = 64;
+    p->n_min = 1e-12;
+    return VDW_OK;
+}
+
+int vdw_kernel_table(const vdw_params* p, double* q_mesh, double* phi_k, double* phi0, double* C_s) {
+    return table_build(p, q_mesh, phi_k, phi0, C_s);
+}
+
+int vdw_create(vdw_handle* h, const vdw_params* p, const double* phi_k, double C_s) {
+    if (!h || !p) return VDW_ERR_ARG;
+    *h = nullptr;
+    if (p->Nq != 8 && p->Nq != 12 && p->Nq != 16 && p->Nq != 20) {
+        set_error("Nq must be one of 8, 12, 16, 20");
+        return VDW_ERR_UNSUPPORTED;
+    }
+    vdw_ctx* c = new (std::nothrow) vdw_ctx();
+    if (!c) return VDW_ERR_OOM;
+    std::memset((void*)c, 0, sizeof(vdw_ctx));
+    c->p = *p;
+    cudaGetDevice(&c->device);
+    int rc = VDW_OK;
+    const int Nq = p->Nq, Nk = p->Nk;
+    double* table = nullptr;
+    if (!phi_k) {
+        table = new (std::nothrow) double[(size_t)Nq * Nq * Nk];
+        if (!table) { delete c; return VDW_ERR_OOM; }
+        rc = table_build(p, nullptr, table, &c->phi0, &C_s);
+        phi_k = table;
+    }
+    if (rc == VDW_OK) rc = table_upload(c, phi_k, C_s);
+    delete[] table;
+    if (rc != VDW_OK) {
+        cudaFree(c->d_kcoef);
+        delete c;
+        return rc;
+    }
+    c->bytes = sizeof(float4) * (size_t)(Nk - 1) * (Nq * (Nq + 1) / 2);
+    *h = c;
+    return VDW_OK;
+}
+
+int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
+    if (!c || !L) return VDW_ERR_ARG;
+    if (!(L[0] > 0 && L[1] > 0 && L[2] > 0)) return VDW_ERR_ARG;
+    const int dims[3] = {n1, n2, n3};
+    for (int d : dims)
+        if (d < 4 || d > MAX_DIM || !smooth235(d)) {
+            set_error("grid dimensions must be {2,3,5}-smooth and in [4, 256]");
+            return VDW_ERR_SIZE;
+        }
+    if ((n1 & 1) || (n3 & 1)) {
+        set_error("N1 and N3 must be even");
+        return VDW_ERR_SIZE;
+    }
+    const double PI_D = 3.14159265358979323846;
+    const double gmax = 2.0 * PI_D * std::sqrt(std::pow((n1 / 2) / L[0], 2) + std::pow((n2 / 2) / L[1], 2) +
+                                               std::pow((n3 / 2) / L[2], 2));
+    if (gmax > c->p.k_max) {
+        set_error("largest |G| of the grid exceeds k_max of the kernel table");
+        return VDW_ERR_SIZE;
+    }
+    cudaSetDevice(c->device);
+    free_plan(c);
+    GridArgs& g = c->g;
+    g.N1 = n1;
+    g.N2 = n2;
+    g.N3 = n3;
+    g.Nh = n1 / 2 + 1;
+    g.N = (long long)n1 * n2 * n3;
+    g.ncols = n3 * g.Nh;
+    for (int d = 0; d < 3; ++d) c->L[d] = L[d];
+    g.gx = (float)(2.0 * PI_D / L[0]);
+    g.gy = (float)(2.0 * PI_D / L[1]);
+    g.gz = (float)(2.0 * PI_D / L[2]);
+    g.gx2 = g.gx * g.gx;
+    g.gy2 = g.gy * g.gy;
+    g.gz2 = g.gz * g.gz;
+    g.Nk = c->p.Nk;
+    g.inv_dk = (float)((c->p.Nk - 1) / c->p.k_max);
+    g.invN = (float)(1.0 / (double)g.N);
+    int rc = make_line_plan(n1, &g.p1);
+    if (!rc) rc = make_line_plan(n2, &g.p2);
+    if (!rc) rc = make_line_plan(n3, &g.p3);
+    if (rc) return rc;
+    size_t sp, spen, sa, sd;
+    rc = pipeline_plan_check(c, &sp, &spen, &sa, &sd);
+    if (rc) {
+        set_error("grid too large for on-chip staging");
+        return rc;
+    }
+    const int Nq = c->p.Nq;
+    const size_t spec_n = (size_t)Nq * n2 * g.ncols;
+    c->nb_point = (int)std::min<long long>((g.N + 255) / 256, 4096);
+    c->nb_pencil = (g.ncols + c->pencil_cols - 1) / c->pencil_cols;
+    VDW_CUDA(cudaMalloc(&c->d_tw, sizeof(float2) * (n1 + n2 + n3)));
+    VDW_CUDA(cudaMalloc(&c->d_spec, sizeof(float2) * spec_n));
+    VDW_CUDA(cudaMalloc(&c->d_wspec, sizeof(float2) * 3 * (size_t)n2 * g.ncols));
+    VDW_CUDA(cudaMalloc(&c->d_t, sizeof(float) * g.N));
+    VDW_CUDA(cudaMalloc(&c->d_k, g.N));
+    VDW_CUDA(cudaMalloc(&c->d_epart, sizeof(double) * (c->nb_point + c->nb_pencil)));
+    VDW_CUDA(cudaMalloc(&c->d_invalid, sizeof(unsigned long long)));
+    VDW_CUDA(cudaMemset(c->d_invalid, 0, sizeof(unsigned long long)));
+    if (c->acc_global) VDW_CUDA(cudaMalloc(&c->d_acc, sizeof(float) * 2 * g.N));
+    rc = pipeline_make_twiddles(c);
+    if (rc) return rc;
+    const int npairs = Nq * (Nq + 1) / 2;
+    c->bytes = sizeof(float4) * (size_t)(c->p.Nk - 1) * npairs + sizeof(float2) * (n1 + n2 + n3) +
+               sizeof(float2) * (spec_n + 3 * (size_t)n2 * g.ncols) + 5 * (size_t)g.N +
+               sizeof(double) * (c->nb_point + c->nb_pencil) + (c->acc_global ? 8 * (size_t)g.N : 0);
+    c->planned = 1;
+    return VDW_OK;
+}
+
+int vdw_energy_potential(vdw_handle c, const float* n, const float* grad, double* E, float* v, float* w,
+                         void* stream) {
+    if (!c || !n || !grad) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    return pipeline_run(c, n, grad, E, v, w, (cudaStream_t)stream);
+}
+
+int vdw_energy_potential_host(vdw_handle c, const float* n, const float* grad, double* E, float* v, void* stream) {
+    if (!c || !n || !grad) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = c->g.N;
+    if (!c->d_in) {
+        VDW_CUDA(cudaMalloc(&c->d_in, sizeof(float) * 4 * N));
+        VDW_CUDA(cudaMalloc(&c->d_v, sizeof(float) * N));
+        VDW_CUDA(cudaMalloc(&c->d_E, sizeof(double) * 3));
+        c->bytes += sizeof(float) * 5 * N + sizeof(double) * 3;
+    }
+    VDW_CUDA(cudaMemcpyAsync(c->d_in, n, sizeof(float) * N, cudaMemcpyHostToDevice, s));
+    VDW_CUDA(cudaMemcpyAsync(c->d_in + N, grad, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s));
+    int rc = pipeline_run(c, c->d_in, c->d_in + N, c->d_E, v ? c->d_v : nullptr, nullptr, s);
+    if (rc) return rc;
+    if (E) VDW_CUDA(cudaMemcpyAsync(E, c->d_E, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    if (v) VDW_CUDA(cudaMemcpyAsync(v, c->d_v, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
+    VDW_CUDA(cudaStreamSynchronize(s));
+    return VDW_OK;
+}
+
+int vdw_last_invalid_points(vdw_handle c, long long* count) {
+    if (!c || !count) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    unsigned long long v = 0;
+    VDW_CUDA(cudaDeviceSynchronize());
+    VDW_CUDA(cudaMemcpy(&v, c->d_invalid, sizeof(v), cudaMemcpyDeviceToHost));
+    *count = (long long)v;
+    return VDW_OK;
+}
+
+int vdw_profile_enable(vdw_handle c, int enable) {
+    if (!c) return VDW_ERR_ARG;
+    if (enable && !c->ev[0]) {
+        for (int i = 0; i <= VDW_NSTAGES; ++i) VDW_CUDA(cudaEventCreate(&c->ev[i]));
+    }
+    c->prof = enable ? 1 : 0;
+    return VDW_OK;
+}
+
+int vdw_profile_read(vdw_handle c, float* ms) {
+    if (!c || !ms) return VDW_ERR_ARG;
+    if (!c->ev[0]) return VDW_ERR_STATE;
+    int last = -1;
+    for (int i = 0; i < VDW_NSTAGES; ++i)
+        if (c->ev_done[i]) last = i;
+    if (last < 0) return VDW_ERR_STATE;
+    VDW_CUDA(cudaEventSynchronize(c->ev[last + 1]));
+    int prev = 0;  // event that opened the next recorded stage
+    for (int i = 0; i < VDW_NSTAGES; ++i) {
+        ms[i] = -1.f;
+        if (!c->ev_done[i]) continue;
+        VDW_CUDA(cudaEventElapsedTime(&ms[i], c->ev[prev], c->ev[i + 1]));
+        prev = i + 1;
+    }
+    return VDW_OK;
+}
+
+int vdw_workspace_bytes(vdw_handle c, size_t* bytes) {
+    if (!c || !bytes) return VDW_ERR_ARG;
+    *bytes = c->bytes;
+    return VDW_OK;
+}
+
+int vdw_destroy(vdw_handle c) {
+    if (!c) return VDW_ERR_ARG;
+    cudaSetDevice(c->device);
+    free_plan(c);
+    cudaFree(c->d_kcoef);
+    for (int i = 0; i <= VDW_NSTAGES; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    delete c;
+    return VDW_OK;
+}
+
+const char* vdw_error_string(int code) {
+    switch (code) {
+        case VDW_OK: return "ok";
+        case VDW_ERR_ARG: return "invalid argument";
+        case VDW_ERR_SIZE: return "unsupported grid size";
+        case VDW_ERR_CUDA: return "CUDA runtime error";
+        case VDW_ERR_OOM: return "device out of memory";
+        case VDW_ERR_STATE: return "context not planned";
+        case VDW_ERR_UNSUPPORTED: return "unsupported parameter";
+        default: return "unknown error";
+    }
+}
+
+const char* vdw_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Shared definitions of the vdwnl CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+
+#include "../../include/vdwnl.h"
+
+namespace vdw {
+
+constexpr int MAX_NQ = 32;     // largest interpolation mesh the kernels take
+constexpr int MAX_DIM = 256;   // largest grid dimension (FFT line length)
+constexpr uint8_t K_INVALID = 255;  // interval code of a point with theta = 0
+
+// Radix schedule of one line length: Stockham passes of radix 4 (c4 times),
+// then 2, 3 and 5, with n = 4^c4 2^c2 3^c3 5^c5.
+struct LinePlan {
+    int n;
+    int c4, c2, c3, c5;
+};
+
+// Pointwise constants, passed by value (kernel parameter space).
+struct PointParams {
+    int Nq;
+    int m_c;
+    float q_c;
+    float n_min;
+    float C_s;
+    float qm[MAX_NQ];            // q mesh
+    float Mq[MAX_NQ][MAX_NQ];    // Mq[a][k]: second derivative of p_a at knot k
+};
+
+// Grid geometry shared by the plane and pencil kernels.
+struct GridArgs {
+    int N1, N2, N3, Nh;    // Nh = N1/2 + 1
+    long long N;           // N1 N2 N3
+    int ncols;             // N3 * Nh: columns of the half spectrum per y
+    float gx2, gy2, gz2;   // (2 pi / L_d)^2
+    float gx, gy, gz;      // 2 pi / L_d
+    float inv_dk;          // 1 / Delta k of the radial table
+    int Nk;                // points of the radial table
+    float invN;            // 1 / N
+    LinePlan p1, p2, p3;   // line transforms along x, y, z
+};
+
+}  // namespace vdw
+
+// The context behind the opaque vdw_handle.
+struct vdw_ctx {
+    vdw_params p;
+    int device;
+    // tables
+    vdw::PointParams pp;        // host copy of the pointwise constants
+    double phi0, C_s;
+    float4* d_kcoef;            // [Nk-1][npairs] cubic coefficients in local t
+    // plan
+    int planned;
+    vdw::GridArgs g;
+    double L[3];
+    float2* d_tw;               // twiddles: N1, N2, N3 entries
+    float2* d_spec;             // [Nq][N2][N3][Nh] theta(G) then u(G), in place
+    float2* d_wspec;            // [3][N2][N3][Nh] w(G); component 0 then D.w
+    float* d_t;                 // [N] position of q inside its mesh interval
+    uint8_t* d_k;               // [N] mesh interval of q (K_INVALID: theta = 0)
+    double* d_epart;            // per-block energy partial sums
+    int nb_point, nb_pencil;    // their counts (pointwise, pencil kernels)
+    unsigned long long* d_invalid;  // count of negative / non-finite densities
+    int pencil_cols;            // columns per pencil block
+    int acc_global;             // assembly accumulators in global memory
+    float* d_acc;               // [2N] their scratch (only when acc_global)
+    // buffers of the host-pointer entry point (allocated on first use)
+    float* d_in;                // [4N]
+    float* d_v;                 // [N]
+    double* d_E;                // [3]
+    size_t bytes;
+    // per-stage timing (vdw_profile_enable)
+    int prof;
+    cudaEvent_t ev[VDW_NSTAGES + 1];
+    int ev_done[VDW_NSTAGES];
+};
+
+namespace vdw {
+
+void set_error(const std::string& s);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define VDW_CUDA(call)                                         \
+    do {                                                       \
+        cudaError_t _e = (call);                               \
+        if (_e != cudaSuccess) return ::vdw::cuda_fail(_e, #call); \
+    } while (0)
+
+// pipeline launchers (pipeline.cu)
+int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w,
+                 cudaStream_t s);
+int pipeline_plan_check(vdw_ctx* c, size_t* smem_plane, size_t* smem_pencil, size_t* smem_assemble,
+                        size_t* smem_div);
+int pipeline_make_twiddles(vdw_ctx* c);
+
+// table launchers (table.cu)
+int table_build(const vdw_params* p, double* h_qmesh, double* h_phik, double* phi0, double* C_s);
+int table_upload(vdw_ctx* c, const double* h_phik, double C_s);
+
+int make_line_plan(int n, LinePlan* lp);
+
+}  // namespace vdw

@@ -1,0 +1,94 @@
+// Pointwise chain of the method, FP32: q0(n, |grad n|) (Dion et al., with the
+// Perdew-Wang 1992 LDA correlation), saturation h(q0, q_c) of Eq. (Sat), the
+// interval of the logarithmic q mesh and the cardinal cubic splines p_a of
+// Eq. (fofx) with their q derivatives.
+#pragma once
+
+#include "common.cuh"
+
+namespace vdw {
+
+struct QPoint {
+    float q;      // saturated q, clamped to the mesh
+    float dq_dn;  // d q / d n
+    float dq_dg;  // (d q / d|grad n|) / |grad n|
+    float t;      // (q - q_k) / (q_{k+1} - q_k)
+    int k;        // mesh interval, or K_INVALID when theta = 0
+};
+
+__device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz, const PointParams& P) {
+    QPoint r;
+    if (!(n > P.n_min) || !isfinite(n)) {
+        r.q = P.qm[0]; r.dq_dn = 0.f; r.dq_dg = 0.f; r.t = 0.f; r.k = K_INVALID;
+        return r;
+    }
+    const float PI_F = 3.14159265358979f;
+    const float A = 0.031091f, a1 = 0.21370f;
+    const float b1 = 7.5957f, b2 = 3.5876f, b3 = 1.6382f, b4 = 0.49294f;
+    const float Z = -0.8491f;
+    const float kF = cbrtf(3.0f * PI_F * PI_F * n);
+    const float rs = cbrtf(3.0f / (4.0f * PI_F * n));
+    const float g2 = gx * gx + gy * gy + gz * gz;
+    const float inv_n = 1.0f / n;
+    const float s2 = g2 * (0.25f * inv_n * inv_n) / (kF * kF);
+    const float srs = sqrtf(rs);
+    const float Q = 2.f * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
+    const float dQ = 2.f * A * (0.5f * b1 / srs + b2 + 1.5f * b3 * srs + 2.f * b4 * rs);
+    const float Lg = log1pf(1.0f / Q);
+    const float ec = -2.f * A * (1.f + a1 * rs) * Lg;
+    const float dec = -2.f * A * a1 * Lg + 2.f * A * (1.f + a1 * rs) * dQ / (Q * Q + Q);
+    const float q0 = kF * (1.f - Z / 9.f * s2) - 4.f * PI_F / 3.f * ec;
+    const float dq0_dn = kF * inv_n * (1.f / 3.f) - Z / 9.f * (kF * s2 * inv_n * (1.f / 3.f) - kF * 8.f * s2 * inv_n * (1.f / 3.f))
+                         + 4.f * PI_F / 3.f * dec * rs * inv_n * (1.f / 3.f);
+    const float dq0_dg = -Z / (18.f * kF) * inv_n * inv_n;
+    // saturation: h = q_c (1 - exp(-S)), S = sum_{m=1}^{m_c} y^m/m, y = q0/q_c.
+    // For y > 4 exp(-S) is far below the FP32 (and FP64) range: h = q_c, h' = 0.
+    const float y = q0 / P.q_c;
+    float h, hp;
+    if (y > 4.f) {
+        h = P.q_c; hp = 0.f;
+    } else {
+        float S = 0.f, dS = 0.f, yp = 1.f;
+        for (int m = 1; m <= P.m_c; ++m) {
+            dS += yp;
+            yp *= y;
+            S += yp / (float)m;
+        }
+        // 1 - exp(-S) through expm1: no cancellation for small q0
+        h = -P.q_c * expm1f(-S);
+        hp = expf(-S) * dS;
+    }
+    float q = fminf(fmaxf(h, P.qm[0]), P.qm[P.Nq - 1]);
+    // interval: number of knots <= q, minus one, in [0, Nq-2]
+    int lo = 0, hi = P.Nq - 1;  // invariant: qm[lo] <= q (or lo = 0), answer in [lo, hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (P.qm[mid] <= q) lo = mid; else hi = mid;
+    }
+    r.k = lo;
+    r.t = (q - P.qm[lo]) / (P.qm[lo + 1] - P.qm[lo]);
+    r.q = q;
+    r.dq_dn = hp * dq0_dn;
+    r.dq_dg = hp * dq0_dg;
+    return r;
+}
+
+// p_a and dp_a/dq on interval k at local position t.
+__device__ __forceinline__ void cardinal(const PointParams& P, int a, int k, float t, float& pa, float& dpa) {
+    const float h = P.qm[k + 1] - P.qm[k];
+    const float A = 1.f - t, B = t;
+    const float M0 = P.Mq[a][k], M1 = P.Mq[a][k + 1];
+    const float y0 = (a == k) ? 1.f : 0.f, y1 = (a == k + 1) ? 1.f : 0.f;
+    pa = A * y0 + B * y1 + ((A * A * A - A) * M0 + (B * B * B - B) * M1) * (h * h * (1.f / 6.f));
+    dpa = (y1 - y0) / h - (3.f * A * A - 1.f) * (1.f / 6.f) * h * M0 + (3.f * B * B - 1.f) * (1.f / 6.f) * h * M1;
+}
+
+__device__ __forceinline__ float cardinal_value(const PointParams& P, int a, int k, float t) {
+    const float h = P.qm[k + 1] - P.qm[k];
+    const float A = 1.f - t, B = t;
+    const float M0 = P.Mq[a][k], M1 = P.Mq[a][k + 1];
+    const float y0 = (a == k) ? 1.f : 0.f, y1 = (a == k + 1) ? 1.f : 0.f;
+    return A * y0 + B * y1 + ((A * A * A - A) * M0 + (B * B * B - B) * M1) * (h * h * (1.f / 6.f));
+}
+
+}  // namespace vdw

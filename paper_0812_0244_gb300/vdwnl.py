@@ -1,0 +1,237 @@
+"""Thin ctypes binding of libvdwnl.so (C ABI in include/vdwnl.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Device buffers are torch CUDA tensors (FP32,
+contiguous, shape (N3, N2, N1) for scalars and (3, N3, N2, N1) for vectors);
+work is enqueued on torch's current CUDA stream unless a stream is given.
+If the library cannot be loaded every entry point raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvdwnl.so")
+
+VDW_OK = 0
+ERRORS = {-1: "VDW_ERR_ARG", -2: "VDW_ERR_SIZE", -3: "VDW_ERR_CUDA", -4: "VDW_ERR_OOM",
+          -5: "VDW_ERR_STATE", -6: "VDW_ERR_UNSUPPORTED"}
+
+
+class VdwError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = "%s failed: %s (%d)" % (where, ERRORS.get(code, "?"), code)
+        try:
+            detail = lib().vdw_last_error().decode()
+            if detail:
+                msg += ": " + detail
+        except Exception:  # pragma: no cover
+            pass
+        super().__init__(msg)
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("Nq", ctypes.c_int), ("q_1", ctypes.c_double), ("q_c", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("m_c", ctypes.c_int), ("d_s", ctypes.c_double),
+                ("na", ctypes.c_int), ("a_max", ctypes.c_double), ("d_asym", ctypes.c_double),
+                ("r_c", ctypes.c_double), ("Nr", ctypes.c_int), ("k_max", ctypes.c_double),
+                ("Nk", ctypes.c_int), ("n_cs", ctypes.c_int), ("n_min", ctypes.c_double)]
+
+
+@dataclass
+class Params:
+    """Method parameters (same meaning and defaults as vdw_params)."""
+    Nq: int = 20
+    q_1: float = 1e-5
+    q_c: float = 5.0
+    lam: float = 1.2
+    m_c: int = 12
+    d_s: float = 1.0
+    na: int = 256
+    a_max: float = 64.0
+    d_asym: float = 8.0
+    r_c: float = 100.0
+    Nr: int = 4096
+    k_max: float = 40.0
+    Nk: int = 1024
+    n_cs: int = 64
+    n_min: float = 1e-12
+
+    def to_c(self):
+        p = _Params()
+        for f in fields(self):
+            setattr(p, "lambda_" if f.name == "lam" else f.name, getattr(self, f.name))
+        return p
+
+
+EXPORTS = ["vdw_params_default", "vdw_kernel_table", "vdw_create", "vdw_plan", "vdw_energy_potential",
+           "vdw_energy_potential_host", "vdw_last_invalid_points", "vdw_profile_enable", "vdw_profile_read",
+           "vdw_workspace_bytes", "vdw_destroy",
+           "vdw_error_string", "vdw_last_error"]
+
+_LIB = None
+
+
+def lib():
+    """Load libvdwnl.so (raises if it is missing: no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libvdwnl.so not built (run paper_0812_0244_gb300.build.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    dp, fp, vp = P(ctypes.c_double), P(ctypes.c_float), ctypes.c_void_p
+    L.vdw_params_default.argtypes = [P(_Params)]
+    L.vdw_kernel_table.argtypes = [P(_Params), dp, dp, dp, dp]
+    L.vdw_create.argtypes = [P(vp), P(_Params), dp, ctypes.c_double]
+    L.vdw_plan.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+    L.vdw_energy_potential.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.vdw_energy_potential_host.argtypes = [vp, fp, fp, dp, fp, vp]
+    L.vdw_last_invalid_points.argtypes = [vp, P(ctypes.c_longlong)]
+    L.vdw_profile_enable.argtypes = [vp, ctypes.c_int]
+    L.vdw_profile_read.argtypes = [vp, fp]
+    L.vdw_workspace_bytes.argtypes = [vp, P(ctypes.c_size_t)]
+    L.vdw_destroy.argtypes = [vp]
+    L.vdw_error_string.argtypes = [ctypes.c_int]
+    L.vdw_error_string.restype = ctypes.c_char_p
+    L.vdw_last_error.argtypes = []
+    L.vdw_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("vdw_error_string", "vdw_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def _check(rc, where):
+    if rc != VDW_OK:
+        raise VdwError(rc, where)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def kernel_table(params: Params | None = None):
+    """vdw_kernel_table: q mesh, phi_ab(k) (Nq, Nq, Nk), phi0 and C_s in FP64."""
+    params = params or Params()
+    qm = np.zeros(params.Nq)
+    phik = np.zeros((params.Nq, params.Nq, params.Nk))
+    phi0 = np.zeros(1)
+    cs = np.zeros(1)
+    p = params.to_c()
+    _check(lib().vdw_kernel_table(ctypes.byref(p), _dptr(qm), _dptr(phik), _dptr(phi0), _dptr(cs)),
+           "vdw_kernel_table")
+    return dict(q_mesh=qm, phi_k=phik, phi0=float(phi0[0]), C_s=float(cs[0]))
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class VdwNL:
+    """A vdwnl context: kernel tables, and after plan() a grid and its workspace."""
+
+    def __init__(self, params: Params | None = None, phi_k: np.ndarray | None = None, C_s: float = 0.0):
+        self.params = params or Params()
+        self._h = ctypes.c_void_p()
+        p = self.params.to_c()
+        tab = None
+        if phi_k is not None:
+            tab = np.ascontiguousarray(phi_k, dtype=np.float64)
+            assert tab.shape == (self.params.Nq, self.params.Nq, self.params.Nk)
+        _check(lib().vdw_create(ctypes.byref(self._h), ctypes.byref(p), _dptr(tab) if tab is not None else None,
+                                float(C_s)), "vdw_create")
+        self.shape = None
+
+    def plan(self, shape, L):
+        """shape = (N3, N2, N1) of the arrays, L = (L1, L2, L3) edge lengths in bohr."""
+        N3, N2, N1 = (int(s) for s in shape)
+        Lc = np.ascontiguousarray(np.asarray(L, dtype=np.float64).reshape(3))
+        _check(lib().vdw_plan(self._h, N1, N2, N3, _dptr(Lc)), "vdw_plan")
+        self.shape = (N3, N2, N1)
+        self.L = Lc.copy()
+        return self
+
+    @property
+    def dOmega(self):
+        return float(np.prod(self.L)) / float(np.prod(self.shape))
+
+    def energy_potential(self, n, grad, E=None, v=None, w=None, stream=None):
+        """Enqueue vdw_energy_potential on device tensors; returns (E, v, w)."""
+        import torch
+        assert n.is_cuda and n.dtype == torch.float32 and n.is_contiguous() and tuple(n.shape) == self.shape
+        assert grad.is_cuda and grad.dtype == torch.float32 and grad.is_contiguous()
+        assert tuple(grad.shape) == (3,) + self.shape
+        for t, shp in ((v, self.shape), (w, (3,) + self.shape)):
+            if t is not None:
+                assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == shp
+        if E is not None:
+            assert E.is_cuda and E.dtype == torch.float64 and E.numel() >= 3
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(lib().vdw_energy_potential(self._h, ptr(n), ptr(grad), ptr(E), ptr(v), ptr(w),
+                                          _stream_handle(stream)), "vdw_energy_potential")
+        return E, v, w
+
+    def compute(self, n, grad, want_v=True, want_w=False, stream=None):
+        """Allocate outputs and run; returns (E[3] float64 device tensor, v, w)."""
+        import torch
+        E = torch.empty(3, dtype=torch.float64, device=n.device)
+        v = torch.empty_like(n) if want_v else None
+        w = torch.empty_like(grad) if want_w else None
+        return self.energy_potential(n, grad, E, v, w, stream)
+
+    def energy_potential_host(self, n, grad, E=None, v=None, stream=None):
+        """vdw_energy_potential_host on numpy float32 arrays (pinned or pageable)."""
+        n = np.ascontiguousarray(n, dtype=np.float32)
+        grad = np.ascontiguousarray(grad, dtype=np.float32)
+        if E is None:
+            E = np.zeros(3)
+        if v is None:
+            v = np.empty(self.shape, dtype=np.float32)
+        fp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        _check(lib().vdw_energy_potential_host(self._h, fp(n), fp(grad), _dptr(E), fp(v), _stream_handle(stream)),
+               "vdw_energy_potential_host")
+        return E, v
+
+    def invalid_points(self):
+        c = ctypes.c_longlong()
+        _check(lib().vdw_last_invalid_points(self._h, ctypes.byref(c)), "vdw_last_invalid_points")
+        return c.value
+
+    STAGES = ("pointwise", "theta_plane", "pencil_contract", "energy_final", "assemble", "pencil_div",
+              "div_final")
+
+    def profile(self, enable=True):
+        _check(lib().vdw_profile_enable(self._h, 1 if enable else 0), "vdw_profile_enable")
+
+    def profile_read(self):
+        """Stage durations (ms) of the last call, as a dict (skipped stages omitted)."""
+        ms = (ctypes.c_float * 7)()
+        _check(lib().vdw_profile_read(self._h, ms), "vdw_profile_read")
+        return {name: float(t) for name, t in zip(self.STAGES, ms) if t >= 0}
+
+    def workspace_bytes(self):
+        b = ctypes.c_size_t()
+        _check(lib().vdw_workspace_bytes(self._h, ctypes.byref(b)), "vdw_workspace_bytes")
+        return b.value
+
+    def close(self):
+        if self._h:
+            lib().vdw_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

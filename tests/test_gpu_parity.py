@@ -1,0 +1,155 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on a GB300.
+
+Tolerances: |Delta E| <= 1e-6 Ha per cell and max|Delta v| <= 1e-5 max|v|
+(FP32 FFTs and contraction, FP64 energy accumulation).  Both sides get the
+same FP32-rounded inputs; each builds its own kernel table (the oracle in
+numpy/C, the library in FP64 CUDA kernels) and the tables are compared too.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0812_0244_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-6
+V_REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def vd(torch_cuda):
+    from paper_0812_0244_gb300 import vdwnl
+    vdwnl.lib()
+    return vdwnl
+
+
+@pytest.fixture(scope="module")
+def ctx(vd):
+    return vd.VdwNL(vd.Params())
+
+
+def f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def run_gpu(torch, ctx, n, g, L, want_v=True, want_w=False):
+    ctx.plan(n.shape, L)
+    nt = torch.tensor(np.asarray(n, np.float32), device="cuda")
+    gt = torch.tensor(np.asarray(g, np.float32), device="cuda")
+    E, v, w = ctx.compute(nt, gt, want_v=want_v, want_w=want_w)
+    torch.cuda.synchronize()
+    return (E.cpu().numpy(), None if v is None else v.cpu().numpy().astype(np.float64),
+            None if w is None else w.cpu().numpy().astype(np.float64))
+
+
+def test_kernel_table_parity(vd, table):
+    t = vd.kernel_table(vd.Params())
+    np.testing.assert_allclose(t["q_mesh"], table.qm, rtol=1e-15)
+    assert abs(t["phi0"] - table.phi0) < 1e-12 * abs(table.phi0)
+    assert abs(t["C_s"] - table.C_s) < 1e-11 * abs(table.C_s)
+    scale = np.abs(table.phik).max(axis=2, keepdims=True)
+    assert np.max(np.abs(t["phi_k"] - table.phik) / scale) < 1e-10
+
+
+CASES = [
+    # (N3, N2, N1), L (bohr)   -- spans pencil tiles with ragged tails, odd N2
+    ((8, 10, 12), (9.0, 8.0, 10.0)),
+    ((12, 15, 16), (10.0, 11.0, 12.0)),
+    ((16, 27, 20), (11.0, 12.0, 13.0)),
+    ((24, 24, 24), None),
+]
+
+
+@pytest.mark.parametrize("shape,L", CASES)
+def test_energy_potential_small(torch_cuda, ctx, table, shape, L):
+    if L is None:
+        d = S.two_atom_density(0, shape=shape)
+        n, g, L = d["n"], d["grad"], d["L"]
+    else:
+        L = np.asarray(L)
+        rng = np.random.default_rng(sum(shape))
+        n, g = S._gaussian_sum(shape, L, [0.4 * L, 0.6 * L + 0.3], rng.uniform(0.1, 1.0, 2), rng.uniform(0.6, 1.4, 2),
+                               1e-5)
+    n, g = f32(n), f32(g)
+    ref = O.energy_potential(n, g, L, table)
+    E, v, _ = run_gpu(torch_cuda, ctx, n, g, L)
+    assert abs(E[1] - ref["E_soft"]) <= E_TOL, (E, ref["E_soft"])
+    assert abs(E[2] - ref["dE"]) <= E_TOL, (E, ref["dE"])
+    assert abs(E[0] - ref["E"]) <= E_TOL
+    assert np.max(np.abs(v - ref["v"])) <= V_REL * np.abs(ref["v"]).max()
+
+
+def test_gradient_outputs_and_energy_only(torch_cuda, ctx, table):
+    d = S.two_atom_density(3, shape=(12, 12, 12))
+    n, g, L = f32(d["n"]), f32(d["grad"]), d["L"]
+    ref = O.energy_potential(n, g, L, table)
+    E, vloc, w = run_gpu(torch_cuda, ctx, n, g, L, want_v=True, want_w=True)
+    assert np.max(np.abs(vloc - ref["v_loc"])) <= V_REL * np.abs(ref["v_loc"]).max()
+    assert np.max(np.abs(w - ref["w"])) <= V_REL * np.abs(ref["w"]).max()
+    E2, _, _ = run_gpu(torch_cuda, ctx, n, g, L, want_v=False, want_w=False)
+    assert abs(E2[0] - E[0]) <= 1e-12 * abs(E[0])
+
+
+def test_uniform_density_property_i(torch_cuda, ctx):
+    for nval in (0.01, 0.5):
+        d = S.uniform_density((8, 8, 8), (10.0, 11.0, 12.0), nval)
+        E, v, _ = run_gpu(torch_cuda, ctx, d["n"], d["grad"], d["L"])
+        assert abs(E[1] + E[2]) < 2e-2 * E[2]
+
+
+def test_invalid_points_are_counted_and_zeroed(torch_cuda, ctx, table):
+    d = S.two_atom_density(1, shape=(8, 8, 8))
+    n = f32(d["n"])
+    n[0, 0, 0] = -1.0
+    n[1, 2, 3] = np.nan
+    g = f32(d["grad"])
+    E, v, _ = run_gpu(torch_cuda, ctx, n, g, d["L"])
+    assert ctx.invalid_points() == 2
+    assert np.isfinite(E).all() and np.isfinite(v).all()
+    n0 = n.copy()
+    n0[0, 0, 0] = 0.0
+    n0[1, 2, 3] = 0.0
+    ref = O.energy_potential(n0, g, d["L"], table)
+    assert abs(E[0] - ref["E"]) <= E_TOL
+
+
+def test_host_entry_point_matches_device(torch_cuda, ctx):
+    d = S.two_atom_density(2, shape=(12, 12, 12))
+    n, g, L = d["n"], d["grad"], d["L"]
+    E, v, _ = run_gpu(torch_cuda, ctx, n, g, L)
+    Eh, vh = ctx.energy_potential_host(n.astype(np.float32), g.astype(np.float32))
+    assert np.array_equal(Eh, E)
+    assert np.array_equal(vh.astype(np.float64), v)
+
+
+def test_plan_rejects_bad_grids(vd, ctx):
+    with pytest.raises(vd.VdwError) as e:
+        ctx.plan((8, 8, 14), (10.0, 10.0, 10.0))  # N1 = 14 = 2 * 7
+    assert e.value.code == -2
+    with pytest.raises(vd.VdwError) as e:
+        ctx.plan((9, 8, 8), (10.0, 10.0, 10.0))   # N3 odd
+    assert e.value.code == -2
+    with pytest.raises(vd.VdwError) as e:
+        ctx.plan((8, 8, 8), (0.5, 10.0, 10.0))    # |G|max beyond k_max
+    assert e.value.code == -2
+
+
+@pytest.mark.slow
+def test_nanotube_cell_full_size(torch_cuda, ctx, table):
+    """The 180 x 180 x 72 double-wall tube (the benchmark workload)."""
+    d = S.tube_density(0)
+    n, g, L = f32(d["n"]), f32(d["grad"]), d["L"]
+    E, v, _ = run_gpu(torch_cuda, ctx, n, g, L)
+    ref = O.energy_potential(n, g, L, table)
+    assert abs(E[0] - ref["E"]) <= E_TOL, (E, ref["E"])
+    assert abs(E[1] - ref["E_soft"]) <= E_TOL
+    assert np.max(np.abs(v - ref["v"])) <= V_REL * np.abs(ref["v"]).max()

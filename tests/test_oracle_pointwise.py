@@ -21,12 +21,16 @@ def fd(f, x, h):
 
 
 def test_pw92_high_density_log_coefficient():
-    # eps_c ~ A ln rs + const for rs -> 0, with A = (1 - ln 2)/pi^2 exactly
+    # eps_c ~ c0 ln rs - c1 for rs -> 0: c0 = (1 - ln 2)/pi^2 exactly
+    # (Gell-Mann--Brueckner), c1 = 0.046644 Ha (the high-density constant the
+    # Perdew-Wang fit reproduces)
     r1, r2 = 1e-10, 1e-12
     e1, _ = O.pw92_eps_c(r1)
     e2, _ = O.pw92_eps_c(r2)
     slope = (e1 - e2) / (np.log(r1) - np.log(r2))
     assert abs(slope - (1 - np.log(2)) / np.pi ** 2) < 2e-5
+    const = e2 - slope * np.log(r2)
+    assert abs(const + 0.046644) < 1e-5
 
 
 def test_pw92_negative_and_derivative():
