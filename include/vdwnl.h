@@ -154,6 +154,33 @@ int vdw_last_invalid_points(vdw_handle h, long long* count);
 int vdw_profile_enable(vdw_handle h, int enable);
 int vdw_profile_read(vdw_handle h, float* ms);
 
+/* ---- Delta E without device allocation ---------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory when they evaluate the energy: a
+ * program whose device memory all belongs to its own pool allocator, a
+ * plugin host that forbids allocations inside a step, or code that cannot
+ * afford the synchronisation an allocation may cause.  Create the context
+ * once beforehand (vdw_create allocates its tables; vdw_plan is not needed);
+ * this call then allocates nothing.
+ *
+ * Computes Delta E = dOmega sum_i C_s n_i^2 / (2 q_i^3), the local correction
+ * of Eqs. (DEnl, Depsnl) -- the value vdw_energy_potential returns in E[2] --
+ * for n[npoints] and grad[3][npoints] (device, FP32) and writes it to *dE
+ * (device, FP64).  Its per-block partial sums live in a fixed 32 KiB array
+ * of the library (4096 FP64 slots, one per 4096 points), which every GPU that
+ * loads the library keeps reserved until the process exits.
+ *   - npoints > VDW_NOALLOC_MAX_POINTS (16,777,216) returns VDW_ERR_SIZE.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array: two calls that may overlap on the GPU (on
+ *     different streams, or from different threads) race and can return
+ *     wrong values.  Calls on one stream are ordered and safe.
+ * Asynchronous on stream. */
+#define VDW_NOALLOC_MAX_POINTS 16777216LL
+int vdw_delta_energy_noalloc(vdw_handle h, const float* n, const float* grad, long long npoints,
+                             double dOmega, double* dE, void* stream);
+
 /* Bytes of device memory the context holds. */
 int vdw_workspace_bytes(vdw_handle h, size_t* bytes);
 

@@ -72,7 +72,7 @@ class Params:
 
 EXPORTS = ["vdw_params_default", "vdw_kernel_table", "vdw_create", "vdw_plan", "vdw_energy_potential",
            "vdw_energy_potential_host", "vdw_last_invalid_points", "vdw_profile_enable", "vdw_profile_read",
-           "vdw_workspace_bytes", "vdw_destroy",
+           "vdw_delta_energy_noalloc", "vdw_workspace_bytes", "vdw_destroy",
            "vdw_error_string", "vdw_last_error"]
 
 _LIB = None
@@ -97,6 +97,7 @@ def lib():
     L.vdw_last_invalid_points.argtypes = [vp, P(ctypes.c_longlong)]
     L.vdw_profile_enable.argtypes = [vp, ctypes.c_int]
     L.vdw_profile_read.argtypes = [vp, fp]
+    L.vdw_delta_energy_noalloc.argtypes = [vp, vp, vp, ctypes.c_longlong, ctypes.c_double, vp, vp]
     L.vdw_workspace_bytes.argtypes = [vp, P(ctypes.c_size_t)]
     L.vdw_destroy.argtypes = [vp]
     L.vdw_error_string.argtypes = [ctypes.c_int]
@@ -207,6 +208,21 @@ class VdwNL:
         c = ctypes.c_longlong()
         _check(lib().vdw_last_invalid_points(self._h, ctypes.byref(c)), "vdw_last_invalid_points")
         return c.value
+
+    def delta_energy_noalloc(self, n, grad, dE, dOmega=None, stream=None):
+        """vdw_delta_energy_noalloc: Delta E into the FP64 device tensor dE[0]
+        with no device allocation (for callers that must not allocate)."""
+        import torch
+        assert n.is_cuda and n.dtype == torch.float32 and n.is_contiguous()
+        assert grad.is_cuda and grad.dtype == torch.float32 and grad.is_contiguous()
+        assert grad.numel() == 3 * n.numel()
+        assert dE.is_cuda and dE.dtype == torch.float64 and dE.numel() >= 1
+        if dOmega is None:
+            dOmega = self.dOmega
+        _check(lib().vdw_delta_energy_noalloc(self._h, ctypes.c_void_p(n.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                              n.numel(), float(dOmega), ctypes.c_void_p(dE.data_ptr()),
+                                              _stream_handle(stream)), "vdw_delta_energy_noalloc")
+        return dE
 
     STAGES = ("pointwise", "theta_plane", "pencil_contract", "energy_final", "assemble", "pencil_div",
               "div_final")
