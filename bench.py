@@ -285,6 +285,33 @@ def main():
         except Exception:
             traffic = None
 
+    # reference only: cuFFT (through torch.fft) on the transforms of one step:
+    # Nq forward and Nq inverse real 3D transforms, plus 3 forward and 1
+    # inverse for the gradient term (never on the product path)
+    cufft_ms = None
+    try:
+        fields = torch.randn((params.Nq,) + n_h.shape, device=dev, dtype=torch.float32)
+        wf = torch.randn((3,) + n_h.shape, device=dev, dtype=torch.float32)
+        for _ in range(3):
+            torch.fft.irfftn(torch.fft.rfftn(fields, dim=(1, 2, 3)), s=n_h.shape, dim=(1, 2, 3))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        reps = 10
+        for _ in range(reps):
+            flush.zero_()
+            e0.record(stream)
+            th = torch.fft.rfftn(fields, dim=(1, 2, 3))
+            torch.fft.irfftn(th, s=n_h.shape, dim=(1, 2, 3))
+            wh = torch.fft.rfftn(wf, dim=(1, 2, 3))
+            torch.fft.irfftn(wh[0], s=n_h.shape, dim=(0, 1, 2))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        cufft_ms = tot / reps
+        del fields, wf, th, wh
+    except Exception:
+        cufft_ms = None
+
     # end to end through the host-pointer entry point (pinned buffers)
     n_p = torch.from_numpy(n_h).pin_memory()
     g_p = torch.from_numpy(g_h).pin_memory()
@@ -328,6 +355,10 @@ def main():
             "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
                     "d2h_bytes_per_step": 4 * N + 24},
             "gpu_launches": 7 * K,
+            "cufft_reference": {"ms_per_step": cufft_ms,
+                                "what": "torch.fft (cuFFT) on the step's %d forward + %d inverse real 3D transforms "
+                                        "alone, no pointwise work or contraction; reference only"
+                                        % (params.Nq + 3, params.Nq + 1)},
             "clocks": clocks,
         }
         if cpu is not None:

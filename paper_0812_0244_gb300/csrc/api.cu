@@ -172,13 +172,15 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     VDW_CUDA(cudaMalloc(&c->d_epart, sizeof(double) * (c->nb_point + c->nb_pencil)));
     VDW_CUDA(cudaMalloc(&c->d_invalid, sizeof(unsigned long long)));
     VDW_CUDA(cudaMemset(c->d_invalid, 0, sizeof(unsigned long long)));
-    if (c->acc_global) VDW_CUDA(cudaMalloc(&c->d_acc, sizeof(float) * 2 * g.N));
+    if (c->acc_global) VDW_CUDA(cudaMalloc(&c->d_acc, sizeof(float) * 2 * 4 * g.N));
     rc = pipeline_make_twiddles(c);
+    if (rc) return rc;
+    rc = pipeline_configure(c);
     if (rc) return rc;
     const int npairs = Nq * (Nq + 1) / 2;
     c->bytes = sizeof(float4) * (size_t)(c->p.Nk - 1) * npairs + sizeof(float2) * (n1 + n2 + n3) +
                sizeof(float2) * (spec_n + 3 * (size_t)n2 * g.ncols) + 5 * (size_t)g.N +
-               sizeof(double) * (c->nb_point + c->nb_pencil) + (c->acc_global ? 8 * (size_t)g.N : 0);
+               sizeof(double) * (c->nb_point + c->nb_pencil) + (c->acc_global ? 32 * (size_t)g.N : 0);
     c->planned = 1;
     return VDW_OK;
 }

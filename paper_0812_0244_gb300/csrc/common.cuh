@@ -69,7 +69,8 @@ struct vdw_ctx {
     unsigned long long* d_invalid;  // count of negative / non-finite densities
     int pencil_cols;            // columns per pencil block
     int acc_global;             // assembly accumulators in global memory
-    float* d_acc;               // [2N] their scratch (only when acc_global)
+    int tk_smem;                // assembly keeps the plane's (t, k) in shared memory
+    float* d_acc;               // [4][2N] their scratch (only when acc_global)
     // buffers of the host-pointer entry point (allocated on first use)
     float* d_in;                // [4N]
     float* d_v;                 // [N]
@@ -98,6 +99,7 @@ int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float
 int pipeline_plan_check(vdw_ctx* c, size_t* smem_plane, size_t* smem_pencil, size_t* smem_assemble,
                         size_t* smem_div);
 int pipeline_make_twiddles(vdw_ctx* c);
+int pipeline_configure(vdw_ctx* c);
 
 // table launchers (table.cu)
 int table_build(const vdw_params* p, double* h_qmesh, double* h_phik, double* phi0, double* C_s);

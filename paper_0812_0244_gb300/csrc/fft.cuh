@@ -102,17 +102,27 @@ template <>
 __device__ __forceinline__ void dft<5, true>(float2* v) { dft5<true>(v); }
 
 // One Stockham pass of radix R over a line of length n (n <= MAX_DIM), by one warp.
+// j mod Ns through a multiply-high: with M = floor((2^32-1)/Ns) + 1 the
+// quotient umulhi(j, M) is exact for j < 2048, Ns <= 512 (checked
+// exhaustively); Ns = 1 is special-cased.
+__device__ __forceinline__ unsigned magic_of(int Ns) { return Ns > 1 ? 0xFFFFFFFFu / (unsigned)Ns + 1u : 0u; }
+__device__ __forceinline__ int mod_magic(int j, int Ns, unsigned M) {
+    return Ns > 1 ? j - (int)__umulhi((unsigned)j, M) * Ns : 0;
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void line_pass(float2* p, int es, int n, int Ns, const float2* tw, int lane) {
     constexpr int MAXB = (MAX_DIM / R + 31) / 32;
     const int m = n / R;
     const int tstride = n / (Ns * R);
+    const unsigned M = magic_of(Ns);
     float2 v[MAXB][R];
 #pragma unroll
     for (int b = 0; b < MAXB; ++b) {
-        const int j = lane + 32 * b;
-        if (j < m) {
-            const int k = j % Ns;
+        const int j0 = lane + 32 * b;
+        const int j = j0 < m ? j0 : 0;  // in-range index for tail lanes
+        if (j0 < m) {
+            const int k = mod_magic(j, Ns, M);
 #pragma unroll
             for (int r = 0; r < R; ++r) v[b][r] = p[(j + r * m) * es];
 #pragma unroll
@@ -126,9 +136,10 @@ __device__ __forceinline__ void line_pass(float2* p, int es, int n, int Ns, cons
     __syncwarp();
 #pragma unroll
     for (int b = 0; b < MAXB; ++b) {
-        const int j = lane + 32 * b;
-        if (j < m) {
-            const int k = j % Ns;
+        const int j0 = lane + 32 * b;
+        const int j = j0 < m ? j0 : 0;
+        if (j0 < m) {
+            const int k = mod_magic(j, Ns, M);
             const int base = (j - k) * R + k;
 #pragma unroll
             for (int r = 0; r < R; ++r) p[(base + r * Ns) * es] = v[b][r];
@@ -161,8 +172,9 @@ __device__ __forceinline__ void r2c_untangle(float2* p, int N, int lane) {
     float2 A[MAXK], B[MAXK];
 #pragma unroll
     for (int b = 0; b < MAXK; ++b) {
-        const int k = lane + 32 * b;
-        if (k < Nh) {
+        const int k0 = lane + 32 * b;
+        const int k = k0 < Nh ? k0 : 0;  // in-range index for tail lanes
+        if (k0 < Nh) {
             const float2 zk = p[k == N ? 0 : k];
             const float2 zm = p[k == 0 ? 0 : N - k];
             // A = (Z_k + conj Z_{-k})/2,  B = -i (Z_k - conj Z_{-k})/2
@@ -173,8 +185,9 @@ __device__ __forceinline__ void r2c_untangle(float2* p, int N, int lane) {
     __syncwarp();
 #pragma unroll
     for (int b = 0; b < MAXK; ++b) {
-        const int k = lane + 32 * b;
-        if (k < Nh) {
+        const int k0 = lane + 32 * b;
+        const int k = k0 < Nh ? k0 : 0;
+        if (k0 < Nh) {
             p[k] = A[b];
             p[Nh + k] = B[b];
         }
@@ -193,8 +206,9 @@ __device__ __forceinline__ void c2r_tangle(float2* p, int N, int lane) {
     float2 A[MAXK], B[MAXK];
 #pragma unroll
     for (int b = 0; b < MAXK; ++b) {
-        const int k = lane + 32 * b;
-        if (k < Nh) {
+        const int k0 = lane + 32 * b;
+        const int k = k0 < Nh ? k0 : 0;
+        if (k0 < Nh) {
             A[b] = p[k];
             B[b] = p[Nh + k];
             if (k == 0 || 2 * k == N) { A[b].y = 0.f; B[b].y = 0.f; }
@@ -203,13 +217,111 @@ __device__ __forceinline__ void c2r_tangle(float2* p, int N, int lane) {
     __syncwarp();
 #pragma unroll
     for (int b = 0; b < MAXK; ++b) {
-        const int k = lane + 32 * b;
-        if (k < Nh) {
+        const int k0 = lane + 32 * b;
+        const int k = k0 < Nh ? k0 : 0;
+        if (k0 < Nh) {
             p[k] = make_float2(A[b].x - B[b].y, A[b].y + B[b].x);
             if (k >= 1 && 2 * k < N) p[N - k] = make_float2(A[b].x + B[b].y, B[b].x - A[b].y);
         }
     }
     __syncwarp();
+}
+
+}  // namespace vdw
+
+// ---------------------------------------------------------------------------
+// Compile-time line lengths: the same Stockham passes with constant radices,
+// strides and twiddle steps, radix 8 first, and several lines per warp so
+// that short lines still fill the 32 lanes.
+// ---------------------------------------------------------------------------
+namespace vdw {
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+    const float r2 = 0.70710678118654752440f;
+    // two radix-4 transforms of the even and odd samples
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<INV>(e);
+    dft4<INV>(o);
+    // odd twiddles W8^k, k = 1..3 (conjugate for the inverse)
+    const float s = INV ? 1.f : -1.f;
+    const float2 o1 = make_float2(r2 * (o[1].x - s * o[1].y), r2 * (o[1].y + s * o[1].x));
+    const float2 o2 = make_float2(-s * o[2].y, s * o[2].x);
+    const float2 o3 = make_float2(r2 * (-o[3].x - s * o[3].y), r2 * (-o[3].y + s * o[3].x));
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+}
+template <>
+__device__ __forceinline__ void dft<8, false>(float2* v) { dft8<false>(v); }
+template <>
+__device__ __forceinline__ void dft<8, true>(float2* v) { dft8<true>(v); }
+
+constexpr int ct_radix(int n) {
+    return n % 8 == 0 ? 8 : n % 4 == 0 ? 4 : n % 2 == 0 ? 2 : n % 3 == 0 ? 3 : n % 5 == 0 ? 5 : 0;
+}
+constexpr int ct_npasses(int n) { return n <= 1 ? 0 : 1 + ct_npasses(n / ct_radix(n)); }
+// radix of pass s (in order) and the product Ns of the radices before it
+constexpr int ct_radix_at(int n, int s) { return s == 0 ? ct_radix(n) : ct_radix_at(n / ct_radix(n), s - 1); }
+constexpr int ct_ns_at(int n, int s) { return s == 0 ? 1 : ct_radix(n) * ct_ns_at(n / ct_radix(n), s - 1); }
+
+// One pass over L lines (line l at p + l*ls, element stride es) by one warp.
+template <int N, int S, int L, bool INV>
+__device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const float2* tw, int lane) {
+    constexpr int R = ct_radix_at(N, S);
+    constexpr int Ns = ct_ns_at(N, S);
+    constexpr int M = N / R;
+    constexpr int TS = N / (Ns * R);
+    constexpr int TOT = L * M;
+    constexpr int B = (TOT + 31) / 32;
+    float2 v[B][R];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int t0 = lane + 32 * b;
+        const int t = (TOT % 32 == 0 || t0 < TOT) ? t0 : 0;  // in-range index for tail lanes
+        if (TOT % 32 == 0 || t0 < TOT) {
+            const int l = t / M, j = t - l * M;
+            const int k = j % Ns;
+            const float2* q = p + l * ls;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = q[(j + r * M) * es];
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const float2 w = tw[r * k * TS];
+                v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+            }
+            dft<R, INV>(v[b]);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int t0 = lane + 32 * b;
+        const int t = (TOT % 32 == 0 || t0 < TOT) ? t0 : 0;  // in-range index for tail lanes
+        if (TOT % 32 == 0 || t0 < TOT) {
+            const int l = t / M, j = t - l * M;
+            const int k = j % Ns;
+            float2* q = p + l * ls;
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) q[(base + r * Ns) * es] = v[b][r];
+        }
+    }
+    __syncwarp();
+}
+
+template <int N, int L, bool INV, int S = 0>
+__device__ __forceinline__ void ct_fft(float2* p, int es, int ls, const float2* tw, int lane) {
+    if constexpr (S < ct_npasses(N)) {
+        ct_pass<N, S, L, INV>(p, es, ls, tw, lane);
+        ct_fft<N, L, INV, S + 1>(p, es, ls, tw, lane);
+    }
 }
 
 }  // namespace vdw

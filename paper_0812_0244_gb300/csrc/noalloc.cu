@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_delta_energy_blocks(const float*
         const long long i = base + (long long)r * NA_THREADS + threadIdx.x;
         if (i >= N) break;
         const float ni = n[i];
-        const QPoint qp = q_point(ni, grad[i], grad[N + i], grad[2 * N + i], P);
+        const QPoint qp = q_point(ni, grad[i], grad[N + i], grad[2 * N + i], P, P.qm);
         if (qp.k != K_INVALID) acc += (double)(0.5f * P.C_s * ni * ni / (qp.q * qp.q * qp.q));
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);

@@ -16,13 +16,22 @@
 // Layouts: real fields [N3][N2][N1] flat (x fastest); spectra
 // [field][N2][N3][Nh] with Nh = N1/2+1 (a y plane of the half spectrum is one
 // contiguous block, a pencil along y strides by N3 Nh).
+//
+// Every kernel is a template over the line lengths (CN1, CN2, CN3): the
+// grids 180 x 180 x 72 and 256 x 256 x 96 get compile-time transforms, any
+// other size (0) the runtime-length engine.
 #include "fft.cuh"
 #include "pointwise.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <string>
 #include <vector>
 
 namespace vdw {
+
+constexpr int CONTRACT_THREADS = 288;  // block size bound of the contraction kernel
 
 // ---------------------------------------------------------------------------
 // reductions
@@ -51,6 +60,40 @@ __device__ __forceinline__ void load_twiddles(float2* dst, const float2* src, in
 }
 
 // ---------------------------------------------------------------------------
+// line-transform dispatch: compile-time length when CN > 0
+// ---------------------------------------------------------------------------
+// rows of one plane (packed real pairs), one row per warp iteration
+template <int CN, bool INV>
+__device__ __forceinline__ void row_fft(float2* p, const LinePlan& pl, const float2* tw, int lane) {
+    if constexpr (CN > 0) ct_fft<CN, 1, INV>(p, 1, 0, tw, lane);
+    else line_fft<INV>(p, 1, pl, tw, lane);
+}
+
+// the Nh columns of a plane (element stride Nh), several columns per warp for short lines
+template <int CN, bool INV>
+__device__ __forceinline__ void columns_fft(float2* plane, int Nh, const LinePlan& pl, const float2* tw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if constexpr (CN > 0) {
+        constexpr int L = CN <= 72 ? 3 : (CN <= 128 ? 2 : 1);
+        const int full = (Nh / L) * L;
+        for (int col = warp * L; col < full; col += nw * L) ct_fft<CN, L, INV>(plane + col, Nh, 1, tw, lane);
+        for (int col = full + warp; col < Nh; col += nw) ct_fft<CN, 1, INV>(plane + col, Nh, 1, tw, lane);
+    } else {
+        for (int col = warp; col < Nh; col += nw) line_fft<INV>(plane + col, Nh, pl, tw, lane);
+    }
+}
+
+// contiguous lines of length N2 (pencils)
+template <int CN, bool INV>
+__device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, const LinePlan& pl, const float2* tw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int l = warp; l < nlines; l += nw) {
+        if constexpr (CN > 0) ct_fft<CN, 1, INV>(lines + l * N2, 1, 0, tw, lane);
+        else line_fft<INV>(lines + l * N2, 1, pl, tw, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // P0: pointwise
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, const float* __restrict__ grad,
@@ -58,12 +101,15 @@ __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, 
                                                    uint8_t* __restrict__ k_out, double* __restrict__ epart,
                                                    unsigned long long* __restrict__ invalid) {
     __shared__ double red[32];
+    __shared__ float qm[MAX_NQ];
+    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
+    __syncthreads();
     double acc = 0.0;
     unsigned int bad = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         const float ni = n[i];
         bad += (!(ni >= 0.f) || !isfinite(ni)) ? 1u : 0u;
-        const QPoint qp = q_point(ni, grad[i], grad[N + i], grad[2 * N + i], P);
+        const QPoint qp = q_point(ni, grad[i], grad[N + i], grad[2 * N + i], P, qm);
         t_out[i] = qp.t;
         k_out[i] = (uint8_t)qp.k;
         if (qp.k != K_INVALID) {
@@ -81,61 +127,71 @@ __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, 
 // ---------------------------------------------------------------------------
 // plane helpers (one y plane, N3 rows of N1 reals <-> N3 x Nh half spectrum)
 // ---------------------------------------------------------------------------
-// Real value of point (x, z) in the packed layout: rows 2j and 2j+1 share the
-// complex row at offset j (2 Nh), as real and imaginary parts.
-__device__ __forceinline__ int packed_index(int x, int z, int Nh) { return 2 * ((z >> 1) * 2 * Nh + x) + (z & 1); }
+// Real rows 2j and 2j+1 share the complex row at offset j (2 Nh), as real and
+// imaginary parts; this is the float offset of the start of real row z.
+__device__ __forceinline__ int packed_row(int z, int Nh) { return 2 * ((z >> 1) * 2 * Nh) + (z & 1); }
 
 // Forward: packed real rows -> half spectrum (x R2C, then z C2C).
+template <int CN1, int CN3>
 __device__ void plane_forward(float2* plane, const GridArgs& g, const float2* tw1, const float2* tw3) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int row = warp; row < g.N3 / 2; row += nw) {
         float2* p = plane + row * 2 * g.Nh;
-        line_fft<false>(p, 1, g.p1, tw1, lane);
+        row_fft<CN1, false>(p, g.p1, tw1, lane);
         r2c_untangle(p, g.N1, lane);
     }
     __syncthreads();
-    for (int col = warp; col < g.Nh; col += nw) line_fft<false>(plane + col, g.Nh, g.p3, tw3, lane);
+    columns_fft<CN3, false>(plane, g.Nh, g.p3, tw3);
     __syncthreads();
 }
 
 // Inverse: half spectrum -> packed real rows (z C2C inverse, then x C2R), unscaled.
+template <int CN1, int CN3>
 __device__ void plane_inverse(float2* plane, const GridArgs& g, const float2* tw1, const float2* tw3) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int col = warp; col < g.Nh; col += nw) line_fft<true>(plane + col, g.Nh, g.p3, tw3, lane);
+    columns_fft<CN3, true>(plane, g.Nh, g.p3, tw3);
     __syncthreads();
     for (int row = warp; row < g.N3 / 2; row += nw) {
         float2* p = plane + row * 2 * g.Nh;
         c2r_tangle(p, g.N1, lane);
-        line_fft<true>(p, 1, g.p1, tw1, lane);
+        row_fft<CN1, true>(p, g.p1, tw1, lane);
     }
     __syncthreads();
 }
 
+constexpr int PLANE_THREADS = 256;  // threads of the plane kernels (P1, P5)
+
 // ---------------------------------------------------------------------------
 // P1: theta_a planes, forward plane transform
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 2) k_theta_plane(const float* __restrict__ n, const float* __restrict__ tk,
-                                                     const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
-                                                     const float2* __restrict__ tw, float2* __restrict__ spec) {
+template <int CN1, int CN3>
+__global__ void __launch_bounds__(PLANE_THREADS, 2) k_theta_plane(const float* __restrict__ n, const float* __restrict__ tk,
+                                                        const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
+                                                        const float2* __restrict__ tw, float2* __restrict__ spec) {
     extern __shared__ float2 sm[];
+    __shared__ SplineSmem sp;
     float2* plane = sm;
     float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
     const int y = blockIdx.x, a = blockIdx.y;
     load_twiddles(tw1, tw, g.N1);
     load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    load_spline_smem(&sp, P);
+    __syncthreads();
     float* pf = reinterpret_cast<float*>(plane);
-    const int np = g.N1 * g.N3;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        const int x = i % g.N1, z = i / g.N1;
-        const long long gi = x + (long long)g.N1 * (y + (long long)g.N2 * z);
-        const int k = kk[gi];
-        float th = 0.f;
-        if (k != K_INVALID) th = n[gi] * cardinal_value(P, a, k, tk[gi]);
-        pf[packed_index(x, z, g.Nh)] = th;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int z = warp; z < g.N3; z += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+        float* dst = pf + packed_row(z, g.Nh);
+        for (int x = lane; x < g.N1; x += 32) {
+            const int k = kk[row + x];
+            float th = 0.f;
+            if (k != K_INVALID) th = n[row + x] * cardinal_value(&sp, a, k, tk[row + x]);
+            dst[2 * x] = th;
+        }
     }
     __syncthreads();
-    plane_forward(plane, g, tw1, tw3);
+    plane_forward<CN1, CN3>(plane, g, tw1, tw3);
     float2* dst = spec + ((long long)a * g.N2 + y) * g.ncols;
     for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
 }
@@ -143,15 +199,20 @@ __global__ void __launch_bounds__(256, 2) k_theta_plane(const float* __restrict_
 // ---------------------------------------------------------------------------
 // P2: pencils along y, contraction with the radial kernel table, energy
 // ---------------------------------------------------------------------------
-template <int NQ>
-__global__ void __launch_bounds__(256, 2) k_pencil_contract(float2* __restrict__ spec, GridArgs g,
-                                                         const float4* __restrict__ kcoef,
-                                                         const float2* __restrict__ tw, double* __restrict__ epart,
-                                                         int C, int write_back) {
+// G = (kx, ky, kz) and (kx, -ky, kz) have the same |G|: one thread takes both,
+// so each table row it fetches serves two points.  The thread keeps the two
+// points' u accumulators in registers and reads their theta values from the
+// block's shared lines (only it reads those two positions).
+template <int NQ, int CN2>
+__global__ void __launch_bounds__(CONTRACT_THREADS, 1) k_pencil_contract(float2* __restrict__ spec, GridArgs g,
+                                                                       const float4* __restrict__ kcoef,
+                                                                       const float2* __restrict__ tw,
+                                                                       double* __restrict__ epart, int C,
+                                                                       int write_back) {
     extern __shared__ float2 sm[];
     __shared__ double red[32];
-    const int N2 = g.N2;
-    float2* lines = sm;                  // [NQ][C][N2]
+    const int N2 = CN2 > 0 ? CN2 : g.N2;
+    float2* lines = sm;  // [NQ][C][N2]
     float2* tw2 = lines + NQ * C * N2;
     load_twiddles(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
@@ -164,60 +225,80 @@ __global__ void __launch_bounds__(256, 2) k_pencil_contract(float2* __restrict__
         lines[(a * C + cc) * N2 + yy] = val;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int l = warp; l < NQ * C; l += nw) line_fft<false>(lines + l * N2, 1, g.p2, tw2, lane);
+    pencils_fft<CN2, false>(lines, NQ * C, N2, g.p2, tw2);
     __syncthreads();
 
     constexpr int NP = NQ * (NQ + 1) / 2;
+    const int npy = N2 / 2 + 1;  // y = 0 .. N2/2, each with its partner N2 - y
+    const int LS = C * N2;       // stride between fields in lines
     double eacc = 0.0;
-    for (int pt = threadIdx.x; pt < C * N2; pt += blockDim.x) {
-        const int cc = pt / N2, yy = pt % N2;
+    for (int task = threadIdx.x; task < C * npy; task += blockDim.x) {
+        const int cc = task / npy, ya = task - cc * npy;
         const int col = c0 + cc;
         if (col >= g.ncols) continue;
+        const int yb0 = N2 - ya;
+        const bool two = (ya != 0) && (yb0 != ya);
+        const int yb = two ? yb0 : ya;  // self-paired: second point is a duplicate, dropped below
         const int kx = col % g.Nh, kz = col / g.Nh;
-        const int my = (2 * yy <= N2) ? yy : yy - N2;
         const int mz = (2 * kz <= g.N3) ? kz : kz - g.N3;
-        const float G2 = g.gx2 * (float)(kx * kx) + g.gy2 * (float)(my * my) + g.gz2 * (float)(mz * mz);
+        const float G2 = g.gx2 * (float)(kx * kx) + g.gy2 * (float)(ya * ya) + g.gz2 * (float)(mz * mz);
         const float s = sqrtf(G2) * g.inv_dk;
         const int j = min((int)s, g.Nk - 2);
         const float t = s - (float)j;
         const float4* cf = kcoef + (long long)j * NP;
-        float2 th[NQ], u[NQ];
+        const float2* la = lines + cc * N2 + ya;
+        const float2* lb = lines + cc * N2 + yb;
+        float2 ua[NQ], ub[NQ];
 #pragma unroll
         for (int a = 0; a < NQ; ++a) {
-            th[a] = lines[(a * C + cc) * N2 + yy];
-            u[a] = make_float2(0.f, 0.f);
+            ua[a] = make_float2(0.f, 0.f);
+            ub[a] = make_float2(0.f, 0.f);
         }
         int p = 0;
 #pragma unroll
         for (int a = 0; a < NQ; ++a) {
+            const float2 taa = la[a * LS], tba = lb[a * LS];
 #pragma unroll
             for (int b = a; b < NQ; ++b, ++p) {
                 const float4 c = __ldg(cf + p);
                 const float phi = fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
-                u[a].x = fmaf(phi, th[b].x, u[a].x);
-                u[a].y = fmaf(phi, th[b].y, u[a].y);
+                const float2 tab = la[b * LS], tbb = lb[b * LS];
+                ua[a].x = fmaf(phi, tab.x, ua[a].x);
+                ua[a].y = fmaf(phi, tab.y, ua[a].y);
+                ub[a].x = fmaf(phi, tbb.x, ub[a].x);
+                ub[a].y = fmaf(phi, tbb.y, ub[a].y);
                 if (b != a) {
-                    u[b].x = fmaf(phi, th[a].x, u[b].x);
-                    u[b].y = fmaf(phi, th[a].y, u[b].y);
+                    ua[b].x = fmaf(phi, taa.x, ua[b].x);
+                    ua[b].y = fmaf(phi, taa.y, ua[b].y);
+                    ub[b].x = fmaf(phi, tba.x, ub[b].x);
+                    ub[b].y = fmaf(phi, tba.y, ub[b].y);
                 }
             }
         }
-        float e = 0.f;
+        float ea = 0.f, eb = 0.f;
 #pragma unroll
-        for (int a = 0; a < NQ; ++a) e = fmaf(th[a].x, u[a].x, fmaf(th[a].y, u[a].y, e));
+        for (int a = 0; a < NQ; ++a) {
+            const float2 taa = la[a * LS], tba = lb[a * LS];
+            ea = fmaf(taa.x, ua[a].x, fmaf(taa.y, ua[a].y, ea));
+            eb = fmaf(tba.x, ub[a].x, fmaf(tba.y, ub[a].y, eb));
+        }
         const bool single = (kx == 0) || (2 * kx == g.N1);
-        eacc += (double)e * (single ? 1.0 : 2.0);
+        eacc += ((double)ea + (two ? (double)eb : 0.0)) * (single ? 1.0 : 2.0);
         if (write_back) {
+            float2* wa = lines + cc * N2 + ya;
+            float2* wb = lines + cc * N2 + yb;
 #pragma unroll
-            for (int a = 0; a < NQ; ++a) lines[(a * C + cc) * N2 + yy] = cscale(u[a], g.invN);
+            for (int a = 0; a < NQ; ++a) {
+                wa[a * LS] = cscale(ua[a], g.invN);
+                if (two) wb[a * LS] = cscale(ub[a], g.invN);
+            }
         }
     }
     const double es = block_sum(eacc, red);
     if (threadIdx.x == 0) epart[blockIdx.x] = es;
     if (!write_back) return;
     __syncthreads();
-    for (int l = warp; l < NQ * C; l += nw) line_fft<true>(lines + l * N2, 1, g.p2, tw2, lane);
+    pencils_fft<CN2, true>(lines, NQ * C, N2, g.p2, tw2);
     __syncthreads();
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
         const int cc = i % C, r = i / C, yy = r % N2, a = r / N2;
@@ -229,94 +310,149 @@ __global__ void __launch_bounds__(256, 2) k_pencil_contract(float2* __restrict__
 // ---------------------------------------------------------------------------
 // P3: inverse plane transforms of u_a and the assembly of Eq. (Vi)
 // ---------------------------------------------------------------------------
-// mode 0: v = v_loc (if v), w written to w_out; mode 1: v_loc to v, w(G) to wspec
-__global__ void __launch_bounds__(512) k_assemble(const float2* __restrict__ spec, const float* __restrict__ n,
-                                                  const float* __restrict__ grad, const float* __restrict__ tk,
-                                                  const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
-                                                  const float2* __restrict__ tw, float* __restrict__ v,
-                                                  float* __restrict__ w_out, float2* __restrict__ wspec, int mode,
-                                                  float* __restrict__ acc_global) {
+// A cluster of ASM_CTAS blocks shares one y plane: block r transforms the
+// fields a = r, r + ASM_CTAS, ... and accumulates S0 = sum_a u_a p_a and
+// S1 = sum_a u_a p_a' over its fields; after a cluster barrier, block r sums
+// the partials of every block for the rows z = r (mod ASM_CTAS) through
+// distributed shared memory and finishes those points (v_loc, g); after a
+// second barrier, blocks 0..2 each gather g for the whole plane and transform
+// one component of w = g grad n.
+// mode 0: v_loc to v (if v), w to w_out; mode 1: v_loc to v, w(G) to wspec.
+constexpr int ASM_CTAS = 4;
+constexpr int ASM_THREADS = 384;
+
+template <int CN1, int CN3>
+__global__ void __cluster_dims__(1, ASM_CTAS, 1) __launch_bounds__(ASM_THREADS, 1)
+    k_assemble(const float2* __restrict__ spec, const float* __restrict__ n, const float* __restrict__ grad,
+               const float* __restrict__ tk, const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
+               const float2* __restrict__ tw, float* __restrict__ v, float* __restrict__ w_out,
+               float2* __restrict__ wspec, int mode, float* __restrict__ acc_global, int tk_smem) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ float2 sm[];
+    __shared__ SplineSmem sp;
     const int np = g.N1 * g.N3;
     const int y = blockIdx.x;
+    const int rank = (int)cluster.block_rank();  // = blockIdx.y
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float2* plane = sm;
     float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
-    // per-point accumulators: shared memory when the plane leaves room for
-    // them, otherwise this block's slice of a global scratch buffer
-    float* S0 = acc_global ? acc_global + (long long)y * 2 * np : reinterpret_cast<float*>(tw3 + g.N3);
+    // per-point partial sums of this block: shared memory when the plane leaves
+    // room for them, otherwise this block's slice of a global scratch buffer
+    float* after = reinterpret_cast<float*>(tw3 + g.N3);
+    float* S0 = acc_global ? acc_global + ((long long)y * ASM_CTAS + rank) * 2 * np : after;
     float* S1 = S0 + np;
+    if (!acc_global) after += 2 * np;
+    // the plane's (t, k) in shared memory when there is room (tk_smem), read
+    // once instead of once per field
+    float* t_s = after;
+    uint8_t* k_s = reinterpret_cast<uint8_t*>(t_s + np);
+    load_spline_smem(&sp, P);
     load_twiddles(tw1, tw, g.N1);
     load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
     for (int i = threadIdx.x; i < np; i += blockDim.x) { S0[i] = 0.f; S1[i] = 0.f; }
+    if (tk_smem) {
+        for (int z = warp; z < g.N3; z += nw) {
+            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+            for (int x = lane; x < g.N1; x += 32) {
+                t_s[z * g.N1 + x] = tk[row + x];
+                k_s[z * g.N1 + x] = kk[row + x];
+            }
+        }
+    }
     const float* pf = reinterpret_cast<const float*>(plane);
-    for (int a = 0; a < P.Nq; ++a) {
+    for (int a = rank; a < P.Nq; a += ASM_CTAS) {
         const float2* src = spec + ((long long)a * g.N2 + y) * g.ncols;
         __syncthreads();
         for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
         __syncthreads();
-        plane_inverse(plane, g, tw1, tw3);
-        for (int i = threadIdx.x; i < np; i += blockDim.x) {
-            const int x = i % g.N1, z = i / g.N1;
-            const long long gi = x + (long long)g.N1 * (y + (long long)g.N2 * z);
-            const int k = kk[gi];
-            if (k == K_INVALID) continue;
-            float pa, dpa;
-            cardinal(P, a, k, tk[gi], pa, dpa);
-            const float u = pf[packed_index(x, z, g.Nh)];
-            S0[i] = fmaf(u, pa, S0[i]);
-            S1[i] = fmaf(u, dpa, S1[i]);
+        plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
+        for (int z = warp; z < g.N3; z += nw) {
+            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+            const float* srow = pf + packed_row(z, g.Nh);
+            for (int x = lane; x < g.N1; x += 32) {
+                const int i = z * g.N1 + x;
+                const int k = tk_smem ? k_s[i] : kk[row + x];
+                if (k == K_INVALID) continue;
+                float pa, dpa;
+                cardinal(&sp, a, k, tk_smem ? t_s[i] : tk[row + x], pa, dpa);
+                const float u = srow[2 * x];
+                S0[i] = fmaf(u, pa, S0[i]);
+                S1[i] = fmaf(u, dpa, S1[i]);
+            }
         }
     }
-    __syncthreads();
+    __threadfence_block();
+    cluster.sync();
+    // partial sums of every block of the cluster
+    const float* S0r[ASM_CTAS];
+    for (int r = 0; r < ASM_CTAS; ++r)
+        S0r[r] = acc_global ? acc_global + ((long long)y * ASM_CTAS + r) * 2 * np : cluster.map_shared_rank(S0, r);
     const long long N = g.N;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        const int x = i % g.N1, z = i / g.N1;
-        const long long gi = x + (long long)g.N1 * (y + (long long)g.N2 * z);
-        const float ni = n[gi];
-        const float gx = grad[gi], gy = grad[N + gi], gz = grad[2 * N + gi];
-        const QPoint qp = q_point(ni, gx, gy, gz, P);
-        float vl = 0.f, gg = 0.f;
-        if (qp.k != K_INVALID) {
-            const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
-            const float cn = 1.5f * P.C_s * ni * ni / q4;
-            vl = S0[i] + ni * qp.dq_dn * S1[i] + P.C_s * ni / q3 - cn * qp.dq_dn;
-            gg = ni * S1[i] * qp.dq_dg - cn * qp.dq_dg;
-        }
-        if (v) v[gi] = vl;
-        if (mode == 0) {
-            if (w_out) {
+    for (int z = rank + ASM_CTAS * warp; z < g.N3; z += ASM_CTAS * nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+        for (int x = lane; x < g.N1; x += 32) {
+            const int i = z * g.N1 + x;
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int r = 0; r < ASM_CTAS; ++r) {
+                s0 += S0r[r][i];
+                s1 += S0r[r][np + i];
+            }
+            const long long gi = row + x;
+            const float ni = n[gi];
+            const float gx = grad[gi], gy = grad[N + gi], gz = grad[2 * N + gi];
+            const QPoint qp = q_point(ni, gx, gy, gz, P, sp.qm);
+            float vl = 0.f, gg = 0.f;
+            if (qp.k != K_INVALID) {
+                const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
+                const float cn = 1.5f * P.C_s * ni * ni / q4;
+                vl = s0 + ni * qp.dq_dn * s1 + P.C_s * ni / q3 - cn * qp.dq_dn;
+                gg = ni * s1 * qp.dq_dg - cn * qp.dq_dg;
+            }
+            if (v) v[gi] = vl;
+            if (mode == 0 && w_out) {
                 w_out[gi] = gg * gx;
                 w_out[N + gi] = gg * gy;
                 w_out[2 * N + gi] = gg * gz;
             }
-        } else {
-            S1[i] = gg;
+            // g for this block's rows replaces its own S0 partials: other
+            // blocks read only their own rows of S0, which are untouched
+            S0[i] = gg;
         }
     }
-    if (mode == 0) return;
-    float* pw = reinterpret_cast<float*>(plane);
-    for (int c = 0; c < 3; ++c) {
+    __threadfence_block();
+    cluster.sync();
+    if (mode == 1 && rank < 3) {
+        const int c = rank;
+        float* pw = reinterpret_cast<float*>(plane);
         __syncthreads();
-        for (int i = threadIdx.x; i < np; i += blockDim.x) {
-            const int x = i % g.N1, z = i / g.N1;
-            const long long gi = x + (long long)g.N1 * (y + (long long)g.N2 * z);
-            pw[packed_index(x, z, g.Nh)] = S1[i] * grad[c * N + gi];
+        for (int z = warp; z < g.N3; z += nw) {
+            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+            const float* gsrc = S0r[z % ASM_CTAS] + z * g.N1;
+            float* dst = pw + packed_row(z, g.Nh);
+            for (int x = lane; x < g.N1; x += 32) dst[2 * x] = gsrc[x] * grad[c * N + row + x];
         }
         __syncthreads();
-        plane_forward(plane, g, tw1, tw3);
+        plane_forward<CN1, CN3>(plane, g, tw1, tw3);
         float2* dst = wspec + ((long long)c * g.N2 + y) * g.ncols;
         for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
     }
+    // keep this block's shared memory alive until every block is done reading it
+    cluster.sync();
 }
 
 // ---------------------------------------------------------------------------
 // P4: spectral divergence along pencils
 // ---------------------------------------------------------------------------
+constexpr int DIV_COLS_CT = 8;  // columns per divergence block
+
+template <int CN2>
 __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspec, GridArgs g,
-                                                    const float2* __restrict__ tw, int C) {
+                                                       const float2* __restrict__ tw, int C) {
     extern __shared__ float2 sm[];
-    const int N2 = g.N2;
+    const int N2 = CN2 > 0 ? CN2 : g.N2;
     float2* lines = sm;  // [3][C][N2]
     float2* tw2 = lines + 3 * C * N2;
     load_twiddles(tw2, tw + g.N1, N2);
@@ -330,12 +466,12 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
         lines[(c * C + cc) * N2 + yy] = val;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int l = warp; l < 3 * C; l += nw) line_fft<false>(lines + l * N2, 1, g.p2, tw2, lane);
+    pencils_fft<CN2, false>(lines, 3 * C, N2, g.p2, tw2);
     __syncthreads();
     for (int pt = threadIdx.x; pt < C * N2; pt += blockDim.x) {
         const int cc = pt / N2, yy = pt % N2;
         const int col = c0 + cc;
+        if (col >= g.ncols) continue;
         const int kx = col % g.Nh, kz = col / g.Nh;
         // derivative wave numbers with the Nyquist components removed
         const int mx = (2 * kx == g.N1) ? 0 : kx;
@@ -351,7 +487,7 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
         lines[(0 * C + cc) * N2 + yy] = make_float2(-im * g.invN, re * g.invN);
     }
     __syncthreads();
-    for (int l = warp; l < C; l += nw) line_fft<true>(lines + l * N2, 1, g.p2, tw2, lane);
+    pencils_fft<CN2, true>(lines, C, N2, g.p2, tw2);
     __syncthreads();
     for (int i = threadIdx.x; i < N2 * C; i += blockDim.x) {
         const int cc = i % C, yy = i / C;
@@ -363,8 +499,9 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
 // ---------------------------------------------------------------------------
 // P5: inverse plane transform of D.w, v = v_loc - D.w
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 2) k_div_final(const float2* __restrict__ wspec, GridArgs g,
-                                                   const float2* __restrict__ tw, float* __restrict__ v) {
+template <int CN1, int CN3>
+__global__ void __launch_bounds__(PLANE_THREADS, 2) k_div_final(const float2* __restrict__ wspec, GridArgs g,
+                                                      const float2* __restrict__ tw, float* __restrict__ v) {
     extern __shared__ float2 sm[];
     float2* plane = sm;
     float2* tw1 = plane + g.N3 * g.Nh;
@@ -375,13 +512,13 @@ __global__ void __launch_bounds__(256, 2) k_div_final(const float2* __restrict__
     const float2* src = wspec + (long long)y * g.ncols;
     for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     __syncthreads();
-    plane_inverse(plane, g, tw1, tw3);
+    plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
     const float* pf = reinterpret_cast<const float*>(plane);
-    const int np = g.N1 * g.N3;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        const int x = i % g.N1, z = i / g.N1;
-        const long long gi = x + (long long)g.N1 * (y + (long long)g.N2 * z);
-        v[gi] -= pf[packed_index(x, z, g.Nh)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int z = warp; z < g.N3; z += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+        const float* srow = pf + packed_row(z, g.Nh);
+        for (int x = lane; x < g.N1; x += 32) v[row + x] -= srow[2 * x];
     }
 }
 
@@ -428,26 +565,35 @@ int make_line_plan(int n, LinePlan* lp) {
 }
 
 static size_t smem_plane(const GridArgs& g) { return sizeof(float2) * ((size_t)g.N3 * g.Nh + g.N1 + g.N3); }
-static size_t smem_assemble(const GridArgs& g, bool acc_in_smem) {
+static size_t smem_assemble(const GridArgs& g, bool acc_in_smem, bool tk_in_smem) {
     return sizeof(float2) * ((size_t)g.N3 * g.Nh + g.N1 + g.N3) +
-           (acc_in_smem ? sizeof(float) * 2 * (size_t)g.N1 * g.N3 : 0);
+           (acc_in_smem ? sizeof(float) * 2 * (size_t)g.N1 * g.N3 : 0) + (tk_in_smem ? 5 * (size_t)g.N1 * g.N3 : 0);
 }
 static size_t smem_pencil(const GridArgs& g, int nq, int C) { return sizeof(float2) * ((size_t)nq * C * g.N2 + g.N2); }
+static size_t smem_pencil_run(const GridArgs& g, int nq, int C) { return smem_pencil(g, nq, C); }
 
-static const size_t SMEM_MAX = 227 * 1024;
+static int contract_threads(const GridArgs& g, int C) {
+    const int npy = g.N2 / 2 + 1;
+    return std::min(CONTRACT_THREADS, std::max(64, (C * npy + 31) / 32 * 32));
+}
+
+// dynamic shared memory per block, leaving room for the kernels' static arrays
+static const size_t SMEM_MAX = 227 * 1024 - 5 * 1024;
+static const int DIV_COLS = DIV_COLS_CT;
 
 int pipeline_plan_check(vdw_ctx* c, size_t* sp, size_t* spen, size_t* sa, size_t* sd) {
     const GridArgs& g = c->g;
     const int nq = c->p.Nq;
-    // columns per pencil block: as many as fit in ~110 KB (2 blocks per SM), at most 8
+    // columns per pencil block: as many as fit in ~110 KB, at most 8
     int C = 8;
     while (C > 1 && smem_pencil(g, nq, C) > 110 * 1024) --C;
     c->pencil_cols = C;
     *sp = smem_plane(g);
-    *spen = smem_pencil(g, nq, C);
-    c->acc_global = smem_assemble(g, true) > SMEM_MAX;
-    *sa = smem_assemble(g, !c->acc_global);
-    *sd = smem_pencil(g, 3, 8);
+    *spen = smem_pencil_run(g, nq, C);
+    c->acc_global = smem_assemble(g, true, false) > SMEM_MAX;
+    c->tk_smem = smem_assemble(g, !c->acc_global, true) <= SMEM_MAX;
+    *sa = smem_assemble(g, !c->acc_global, c->tk_smem);
+    *sd = smem_pencil_run(g, 3, DIV_COLS);
     if (*sp > SMEM_MAX || *spen > SMEM_MAX || *sa > SMEM_MAX || *sd > SMEM_MAX) return VDW_ERR_SIZE;
     return VDW_OK;
 }
@@ -462,17 +608,30 @@ int pipeline_make_twiddles(vdw_ctx* c) {
     return VDW_OK;
 }
 
-template <int NQ>
+template <int NQ, int CN2>
 static void launch_contract(vdw_ctx* c, cudaStream_t s, int write_back) {
     const GridArgs& g = c->g;
     const int C = c->pencil_cols;
-    const size_t sm = smem_pencil(g, NQ, C);
-    cudaFuncSetAttribute(k_pencil_contract<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_pencil_contract<NQ><<<c->nb_pencil, 256, sm, s>>>(c->d_spec, g, c->d_kcoef, c->d_tw,
-                                                        c->d_epart + c->nb_point, C, write_back);
+    const size_t sm = smem_pencil_run(g, NQ, C);
+    const int threads = contract_threads(g, C);
+    k_pencil_contract<NQ, CN2><<<c->nb_pencil, threads, sm, s>>>(c->d_spec, g, c->d_kcoef, c->d_tw,
+                                                                 c->d_epart + c->nb_point, C, write_back);
 }
 
-int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s) {
+template <int CN2>
+static int launch_contract_nq(vdw_ctx* c, cudaStream_t s, int write_back) {
+    switch (c->pp.Nq) {
+        case 20: launch_contract<20, CN2>(c, s, write_back); break;
+        case 8: launch_contract<8, CN2>(c, s, write_back); break;
+        case 12: launch_contract<12, CN2>(c, s, write_back); break;
+        case 16: launch_contract<16, CN2>(c, s, write_back); break;
+        default: set_error("Nq not compiled in"); return VDW_ERR_UNSUPPORTED;
+    }
+    return VDW_OK;
+}
+
+template <int CN1, int CN2, int CN3>
+static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s) {
     const GridArgs& g = c->g;
     const PointParams& P = c->pp;
     const bool want_pot = (v != nullptr) || (w != nullptr);
@@ -492,17 +651,11 @@ int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float
     mark(0);
 
     const size_t sp = smem_plane(g);
-    cudaFuncSetAttribute(k_theta_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp);
-    k_theta_plane<<<dim3(g.N2, P.Nq), 256, sp, s>>>(n, c->d_t, c->d_k, g, P, c->d_tw, c->d_spec);
+    k_theta_plane<CN1, CN3><<<dim3(g.N2, P.Nq), PLANE_THREADS, sp, s>>>(n, c->d_t, c->d_k, g, P, c->d_tw, c->d_spec);
     mark(1);
 
-    switch (P.Nq) {
-        case 20: launch_contract<20>(c, s, want_pot ? 1 : 0); break;
-        case 8: launch_contract<8>(c, s, want_pot ? 1 : 0); break;
-        case 12: launch_contract<12>(c, s, want_pot ? 1 : 0); break;
-        case 16: launch_contract<16>(c, s, want_pot ? 1 : 0); break;
-        default: set_error("Nq not compiled in"); return VDW_ERR_UNSUPPORTED;
-    }
+    int rc = launch_contract_nq<CN2>(c, s, want_pot ? 1 : 0);
+    if (rc) return rc;
     mark(2);
     if (E) {
         const double Omega = c->L[0] * c->L[1] * c->L[2];
@@ -512,25 +665,94 @@ int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float
         mark(3);
     }
     if (want_pot) {
-        const size_t sa = smem_assemble(g, !c->acc_global);
-        cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa);
+        const size_t sa = smem_assemble(g, !c->acc_global, c->tk_smem);
         const int mode = (w != nullptr) ? 0 : 1;
-        k_assemble<<<g.N2, 512, sa, s>>>(c->d_spec, n, grad, c->d_t, c->d_k, g, P, c->d_tw, v, w, c->d_wspec, mode,
-                                         c->acc_global ? c->d_acc : nullptr);
+        k_assemble<CN1, CN3><<<dim3(g.N2, ASM_CTAS), ASM_THREADS, sa, s>>>(c->d_spec, n, grad, c->d_t, c->d_k, g, P,
+                                                                   c->d_tw, v, w, c->d_wspec, mode,
+                                                                   c->acc_global ? c->d_acc : nullptr, c->tk_smem);
         mark(4);
         if (mode == 1) {
-            const int Cd = 8;
-            const size_t sd = smem_pencil(g, 3, Cd);
-            cudaFuncSetAttribute(k_pencil_div, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sd);
-            k_pencil_div<<<(g.ncols + Cd - 1) / Cd, 256, sd, s>>>(c->d_wspec, g, c->d_tw, Cd);
+            const size_t sd = smem_pencil_run(g, 3, DIV_COLS);
+            k_pencil_div<CN2><<<(g.ncols + DIV_COLS - 1) / DIV_COLS, 256, sd, s>>>(c->d_wspec, g, c->d_tw, DIV_COLS);
             mark(5);
-            cudaFuncSetAttribute(k_div_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp);
-            k_div_final<<<g.N2, 256, sp, s>>>(c->d_wspec, g, c->d_tw, v);
+            k_div_final<CN1, CN3><<<g.N2, PLANE_THREADS, sp, s>>>(c->d_wspec, g, c->d_tw, v);
             mark(6);
         }
     }
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
+}
+
+// Dynamic shared-memory limits of the kernels a plan uses (set once per plan).
+// Sets a kernel's dynamic shared-memory limit and checks that the block size
+// it will be launched with fits its register use.
+template <class K>
+static int set_and_check(K kernel, const char* name, int smem, int threads) {
+    VDW_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    cudaFuncAttributes fa;
+    VDW_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    if (fa.maxThreadsPerBlock < threads) {
+        set_error(std::string(name) + ": " + std::to_string(threads) + " threads requested, " +
+                  std::to_string(fa.maxThreadsPerBlock) + " possible with " + std::to_string(fa.numRegs) +
+                  " registers");
+        return VDW_ERR_UNSUPPORTED;
+    }
+    return VDW_OK;
+}
+
+template <int CN1, int CN2, int CN3>
+static int configure_sized(vdw_ctx* c) {
+    const GridArgs& g = c->g;
+    const int sp = (int)smem_plane(g), sa = (int)smem_assemble(g, !c->acc_global, c->tk_smem);
+    const int sd = (int)smem_pencil_run(g, 3, DIV_COLS), sc = (int)smem_pencil_run(g, c->p.Nq, c->pencil_cols);
+    const int tc = contract_threads(g, c->pencil_cols);
+    int rc = set_and_check(k_theta_plane<CN1, CN3>, "k_theta_plane", sp, PLANE_THREADS);
+    if (!rc) rc = set_and_check(k_assemble<CN1, CN3>, "k_assemble", sa, ASM_THREADS);
+    if (!rc) rc = set_and_check(k_pencil_div<CN2>, "k_pencil_div", sd, 256);
+    if (!rc) rc = set_and_check(k_div_final<CN1, CN3>, "k_div_final", sp, PLANE_THREADS);
+    if (rc) return rc;
+    switch (c->p.Nq) {
+        case 20: rc = set_and_check(k_pencil_contract<20, CN2>, "k_pencil_contract", sc, tc); break;
+        case 8: rc = set_and_check(k_pencil_contract<8, CN2>, "k_pencil_contract", sc, tc); break;
+        case 12: rc = set_and_check(k_pencil_contract<12, CN2>, "k_pencil_contract", sc, tc); break;
+        case 16: rc = set_and_check(k_pencil_contract<16, CN2>, "k_pencil_contract", sc, tc); break;
+        default: return VDW_ERR_UNSUPPORTED;
+    }
+    if (rc) return rc;
+    // the assembly clusters must fit on the device
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.N2, ASM_CTAS);
+    cfg.blockDim = dim3(ASM_THREADS);
+    cfg.dynamicSmemBytes = sa;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = 1;
+    at.val.clusterDim.y = ASM_CTAS;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    VDW_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, k_assemble<CN1, CN3>, &cfg));
+    if (nclusters < 1) {
+        set_error("k_assemble: a cluster of " + std::to_string(ASM_CTAS) + " blocks with " + std::to_string(sa) +
+                  " bytes of shared memory each does not fit");
+        return VDW_ERR_UNSUPPORTED;
+    }
+    return VDW_OK;
+}
+
+int pipeline_configure(vdw_ctx* c) {
+    const GridArgs& g = c->g;
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) return configure_sized<180, 180, 72>(c);
+    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) return configure_sized<256, 256, 96>(c);
+    return configure_sized<0, 0, 0>(c);
+}
+
+int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s) {
+    const GridArgs& g = c->g;
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) return run_sized<180, 180, 72>(c, n, grad, E, v, w, s);
+    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) return run_sized<256, 256, 96>(c, n, grad, E, v, w, s);
+    return run_sized<0, 0, 0>(c, n, grad, E, v, w, s);
 }
 
 }  // namespace vdw

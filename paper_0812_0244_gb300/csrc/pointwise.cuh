@@ -16,10 +16,13 @@ struct QPoint {
     int k;        // mesh interval, or K_INVALID when theta = 0
 };
 
-__device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz, const PointParams& P) {
+// qm: the q mesh (Nq values), normally a shared-memory copy of P.qm so that
+// the divergent interval search does not serialise on the constant bank.
+__device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz, const PointParams& P,
+                                          const float* qm) {
     QPoint r;
     if (!(n > P.n_min) || !isfinite(n)) {
-        r.q = P.qm[0]; r.dq_dn = 0.f; r.dq_dg = 0.f; r.t = 0.f; r.k = K_INVALID;
+        r.q = qm[0]; r.dq_dn = 0.f; r.dq_dg = 0.f; r.t = 0.f; r.k = K_INVALID;
         return r;
     }
     const float PI_F = 3.14159265358979f;
@@ -58,35 +61,48 @@ __device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz,
         h = -P.q_c * expm1f(-S);
         hp = expf(-S) * dS;
     }
-    float q = fminf(fmaxf(h, P.qm[0]), P.qm[P.Nq - 1]);
+    float q = fminf(fmaxf(h, qm[0]), qm[P.Nq - 1]);
     // interval: number of knots <= q, minus one, in [0, Nq-2]
     int lo = 0, hi = P.Nq - 1;  // invariant: qm[lo] <= q (or lo = 0), answer in [lo, hi)
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (P.qm[mid] <= q) lo = mid; else hi = mid;
+        if (qm[mid] <= q) lo = mid; else hi = mid;
     }
     r.k = lo;
-    r.t = (q - P.qm[lo]) / (P.qm[lo + 1] - P.qm[lo]);
+    r.t = (q - qm[lo]) / (qm[lo + 1] - qm[lo]);
     r.q = q;
     r.dq_dn = hp * dq0_dn;
     r.dq_dg = hp * dq0_dg;
     return r;
 }
 
+// Shared-memory copy of the spline tables: qm[MAX_NQ], Mq[a][k] as
+// Mq[a * MAX_NQ + k].  Indexing them by the per-point interval k from the
+// constant bank would serialise the warp.
+struct SplineSmem {
+    float qm[MAX_NQ];
+    float Mq[MAX_NQ * MAX_NQ];
+};
+
+__device__ __forceinline__ void load_spline_smem(SplineSmem* sp, const PointParams& P) {
+    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) sp->qm[i] = P.qm[i];
+    for (int i = threadIdx.x; i < MAX_NQ * MAX_NQ; i += blockDim.x) sp->Mq[i] = P.Mq[i / MAX_NQ][i % MAX_NQ];
+}
+
 // p_a and dp_a/dq on interval k at local position t.
-__device__ __forceinline__ void cardinal(const PointParams& P, int a, int k, float t, float& pa, float& dpa) {
-    const float h = P.qm[k + 1] - P.qm[k];
+__device__ __forceinline__ void cardinal(const SplineSmem* sp, int a, int k, float t, float& pa, float& dpa) {
+    const float h = sp->qm[k + 1] - sp->qm[k];
     const float A = 1.f - t, B = t;
-    const float M0 = P.Mq[a][k], M1 = P.Mq[a][k + 1];
+    const float M0 = sp->Mq[a * MAX_NQ + k], M1 = sp->Mq[a * MAX_NQ + k + 1];
     const float y0 = (a == k) ? 1.f : 0.f, y1 = (a == k + 1) ? 1.f : 0.f;
     pa = A * y0 + B * y1 + ((A * A * A - A) * M0 + (B * B * B - B) * M1) * (h * h * (1.f / 6.f));
     dpa = (y1 - y0) / h - (3.f * A * A - 1.f) * (1.f / 6.f) * h * M0 + (3.f * B * B - 1.f) * (1.f / 6.f) * h * M1;
 }
 
-__device__ __forceinline__ float cardinal_value(const PointParams& P, int a, int k, float t) {
-    const float h = P.qm[k + 1] - P.qm[k];
+__device__ __forceinline__ float cardinal_value(const SplineSmem* sp, int a, int k, float t) {
+    const float h = sp->qm[k + 1] - sp->qm[k];
     const float A = 1.f - t, B = t;
-    const float M0 = P.Mq[a][k], M1 = P.Mq[a][k + 1];
+    const float M0 = sp->Mq[a * MAX_NQ + k], M1 = sp->Mq[a * MAX_NQ + k + 1];
     const float y0 = (a == k) ? 1.f : 0.f, y1 = (a == k + 1) ? 1.f : 0.f;
     return A * y0 + B * y1 + ((A * A * A - A) * M0 + (B * B * B - B) * M1) * (h * h * (1.f / 6.f));
 }
