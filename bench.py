@@ -16,6 +16,7 @@ workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -60,6 +61,33 @@ def stage_bytes_per_point(Nq, N1):
         "pencil_div": 3 * 8 * h + 8 * h,           # w(G) in, D.w(G) out
         "div_final": 8 * h + 4 + 4,                # D.w(G), v_loc in; v out
     }
+
+
+def source_sha1():
+    """sha1 over the kernel sources (file name, then content, in name order)."""
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_0812_0244_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic(stage):
+    """DRAM bytes per launch of a stage from the committed ncu capture, or None
+    when there is none or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_dwnt_180x180x72_nq20.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 2 and not line.startswith("#"):
+            vals[parts[0]] = parts[1]
+    if vals.get("source_sha1") != source_sha1() or stage not in vals:
+        return None
+    return int(vals[stage])
 
 
 def b_alg(Nq):
@@ -277,13 +305,7 @@ def main():
     top = max((k2 for k2 in acc if k2 != "energy_final"), key=lambda k2: acc[k2])
     peak, peak_kind = measured_peaks()
     achieved = sb[top] * N / (acc[top] * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(top)
-        except Exception:
-            traffic = None
+    traffic = captured_traffic(top)
 
     # reference only: cuFFT (through torch.fft) on the transforms of one step:
     # Nq forward and Nq inverse real 3D transforms, plus 3 forward and 1
