@@ -12,5 +12,8 @@ Modules
 vdw_oracle   plain numpy FP64 statement of every step, in the paper's order.
 dion.c       the Dion kernel phi(d1, d2) by direct double quadrature (compiled
              on first use with gcc into ``oracle/_build``).
+learned      the learned reduced basis (a network's channel weights and a
+             learned pair kernel in place of the splines), its potential,
+             parameter gradients and training loss.
 """
 from .vdw_oracle import *  # noqa: F401,F403

@@ -21,6 +21,11 @@ Paper passages (Roman-Perez & Soler, arXiv:0812.0244):
 Definitions the paper takes from Dion et al. (PRL 92, 246401, 2004):
   q0(n, |grad n|), the kernel phi(d1, d2) and, through q0, the LDA
   correlation of Perdew and Wang (PRB 45, 13244, 1992).
+
+Parity unpinned: the Perdew-Wang constants alpha1, beta2, beta3, beta4 and
+Dion's gradient coefficient Z_ab are restated from the published papers, which
+are not at hand; no test fixes their values (A is pinned through the
+high-density limit, and every derivative is pinned by finite differences).
 """
 from __future__ import annotations
 
@@ -91,7 +96,8 @@ Z_AB = -0.8491  # Dion et al. gradient coefficient in q0
 
 
 def pw92_eps_c(rs):
-    """eps_c(rs) in Hartree and d eps_c / d rs (Perdew-Wang 1992, p = 1)."""
+    """eps_c(rs) in Hartree and d eps_c / d rs (Perdew-Wang 1992, p = 1).
+    Parity unpinned for alpha1 and beta2..beta4 (restated constants)."""
     rs = np.asarray(rs, dtype=np.float64)
     b1, b2, b3, b4 = PW_BETA
     srs = np.sqrt(rs)
@@ -109,6 +115,7 @@ def q0_unsaturated(n, gmod):
     q0 = k_F (1 - (Z_ab/9) s^2) - (4 pi/3) eps_c^LDA(r_s),
     k_F = (3 pi^2 n)^(1/3), s = |grad n| / (2 k_F n), r_s = (3/(4 pi n))^(1/3).
     Returns q0, d q0/d n, and (d q0/d|grad n|) / |grad n| (finite at grad = 0).
+    Parity unpinned for Z_ab (restated constant).
     """
     n = np.asarray(n, dtype=np.float64)
     gmod = np.asarray(gmod, dtype=np.float64)
