@@ -113,7 +113,10 @@ int vdw_plan(vdw_handle h, int n1, int n2, int n3, const double L[3]);
 
 /* E_c^nl and, on request, its potential (device pointers, caller-owned).
  *   n        [N]    density (FP32)
- *   grad     [3][N] its gradient, components x, y, z (FP32)
+ *   grad     [3][N] its gradient, components x, y, z (FP32), or NULL: the
+ *                   library then computes grad n = D n with its spectral
+ *                   derivative (vdw_spectral_gradient) into a context-owned
+ *                   buffer (allocated on first use)
  *   E        [3]    FP64 device output {E_c^nl, E_soft, Delta E} (Hartree);
  *                   E_soft is Eq. (Eoffk) with the soft kernel, Delta E the
  *                   local correction of Eqs. (DEnl, Depsnl); may be NULL.
@@ -180,6 +183,87 @@ int vdw_profile_read(vdw_handle h, float* ms);
 #define VDW_NOALLOC_MAX_POINTS 16777216LL
 int vdw_delta_energy_noalloc(vdw_handle h, const float* n, const float* grad, long long npoints,
                              double dOmega, double* dE, void* stream);
+
+/* ---- spectral gradient --------------------------------------------------
+ * grad[3][N] = D f for a real field f[N] (device, FP32): grad_c f =
+ * IFFT(i G_c f(G)) with the Nyquist component of every even axis removed, the
+ * derivative whose transpose is -D (the operator in Eq. (Vi)'s gradient
+ * term, spectral form of the finite differences the paper uses).  Uses the
+ * context's transform workspace; needs vdw_plan.  Asynchronous on stream. */
+int vdw_spectral_gradient(vdw_handle h, const float* f, float* grad, void* stream);
+
+/* ---- learned reduced basis ------------------------------------------------
+ * The paper has no learned part.  These entry points replace the Nq
+ * cardinal-spline channels theta_a = n p_a(q) (Eq. fofx) and the radial table
+ * phi_ab(k) (Eq. Eoffk) by VDW_LEARNED_M = 8 channels theta_m = n w_m whose
+ * weights w come from a 2-64-64-8 SiLU network of two features, and by a
+ * learned symmetric pair kernel K_mn(k), piecewise linear on J uniform knots
+ * k_j = j k_max/(J-1).  The local correction Delta E of Eqs. (DEnl, Depsnl)
+ * is kept unchanged.  The contraction, transforms and assembly are those of
+ * the plain method (Eqs. Eoffk, epsilon, epsofk, Vi) with M channels.
+ *
+ * Features (s2 = |grad n|^2 n^(-8/3), a smooth form of |grad n| / n^(4/3)):
+ *   x1 = (ln n - feat[0]) / feat[1],  x2 = (1/2 ln(s2 + feat[4]^2) - feat[2]) / feat[3]
+ * Network: h1 = bf16(silu(W1 x + b1)), h2 = bf16(silu(W2 h1 + b2)),
+ *   w = W3 h2 + b3; the weights are rounded to bf16, layers 2 and 3 (and the
+ *   potential's Jacobian-vector product) run on the tensor cores with FP32
+ *   accumulation.  Points with n <= n_min carry theta = 0.
+ * Parameters: one flat FP32 vector of vdw_learned_param_count(J) values, in
+ *   the order W1[64][2], b1[64], W2[64][64], b2[64], W3[8][64], b3[8],
+ *   K[36][J] (pairs m <= n, row-major), W[out][in].
+ * Errors: VDW_ERR_STATE before vdw_plan or vdw_learned_load; VDW_ERR_SIZE if
+ *   the grid's largest |G| exceeds k_max or shared memory does not suffice. */
+#define VDW_LEARNED_M 8
+#define VDW_LEARNED_H 64
+long long vdw_learned_param_count(int J);
+
+/* Load (or reload, e.g. after a training step) a model for the planned grid.
+ *   J       knots, 2 <= J <= 256;  k_max  last knot (bohr^-1)
+ *   feat    host [5]: mu1, sig1, mu2, sig2, eps of the features
+ *   params  device [vdw_learned_param_count(J)] FP32; read by a kernel on
+ *           stream, so it may be updated right after on the same stream.
+ * The context derives its own copies (bf16 operands, knot intervals); the
+ * first call allocates them (synchronous), later calls only enqueue. */
+int vdw_learned_load(vdw_handle h, int J, double k_max, const double feat[5], const float* params,
+                     void* stream);
+
+/* E and v of the learned model; arguments and outputs exactly as
+ * vdw_energy_potential (E[1] holds the learned soft part, E[2] Delta E).
+ * grad must be given.  Asynchronous on stream. */
+int vdw_learned_energy_potential(vdw_handle h, const float* n, const float* grad, double* E, float* v,
+                                 float* w, void* stream);
+
+/* Adds coef * dE/dparams of the learned energy at (n, grad) to g_params
+ * (device FP64 [vdw_learned_param_count(J)]); E (device FP64 [3]) receives
+ * the energy, or NULL.  The gradient treats every bf16 rounding as the
+ * identity.  Allocates an [8][N] FP32 buffer on first use.  Asynchronous. */
+int vdw_learned_param_grad(vdw_handle h, const float* n, const float* grad, double coef, double* g_params,
+                           double* E, void* stream);
+
+/* Adds coef * d/dparams sum_i weight_i sum_m (w_m(x_i) - target[m][i])^2 to
+ * g_params (network part only): fitting the channel weights to targets such
+ * as vdw_basis_weights.  target [8][N], weight [N] device FP32.  Asynchronous. */
+int vdw_learned_fit_grad(vdw_handle h, const float* n, const float* grad, const float* target,
+                         const float* weight, double coef, double* g_params, void* stream);
+
+/* Network outputs w_m at every point (0 where n <= n_min): w_out [8][N].
+ * Asynchronous. */
+int vdw_learned_channels(vdw_handle h, const float* n, const float* grad, float* w_out, void* stream);
+
+/* *tc_error = 1 if a tensor-core wait in a learned kernel gave up (the
+ * kernel then skipped its remaining tiles), else 0.  Synchronous. */
+int vdw_learned_status(vdw_handle h, int* tc_error);
+
+/* The plain method's cardinal weights p_a(q(n, |grad n|)) (Eq. fofx, with
+ * Eq. (Sat)) for the context's Nq mesh: p_out [Nq][N], 0 where n <= n_min.
+ * Needs vdw_plan.  Asynchronous. */
+int vdw_basis_weights(vdw_handle h, const float* n, const float* grad, float* p_out, void* stream);
+
+/* One Adam step (Kingma and Ba) on count FP32 parameters p with FP64
+ * gradients g and FP32 moment buffers m, v (all device); step >= 1 is the
+ * 1-based step number for the bias corrections.  Asynchronous. */
+int vdw_adam_step(float* p, const double* g, float* m, float* v, long long count, double lr, double beta1,
+                  double beta2, double eps, int step, void* stream);
 
 /* Bytes of device memory the context holds. */
 int vdw_workspace_bytes(vdw_handle h, size_t* bytes);

@@ -338,3 +338,22 @@ def loss_grad(n, cell, mdl, T, E_ref, v_ref, natoms, a=1.0, b=1.0, rel_step=1e-3
         dd = np.zeros_like(r["grad"])
     g = 2.0 * a * (r["E"] - E_ref) / natoms ** 2 * r["grad"] + (2.0 * b / np.sum(n)) * dd / dOmega
     return g
+
+
+def fit_grad(n, grad, mdl: LearnedModel, target, weight, n_min):
+    """d/dparams of sum_i weight_i sum_m (w_m(x_i) - target_m,i)^2 over the
+    points with n > n_min (network part of the flat vector; knots get zero)."""
+    ft = features(n, grad, mdl, n_min)
+    ok = ft["ok"].ravel()
+    f = mlp_forward(ft["x1"].ravel(), ft["x2"].ravel(), mdl)
+    M = mdl.M
+    do = 2.0 * (np.asarray(weight, np.float64).ravel() * ok)[None] * (f["w"] - np.asarray(target).reshape(M, -1))
+    gb3 = do.sum(axis=1)
+    gW3 = do @ f["h2"].T
+    dz2 = (f["W3"].T @ do) * silu_prime(f["z2"])
+    gb2 = dz2.sum(axis=1)
+    gW2 = dz2 @ f["h1"].T
+    dz1 = (f["W2"].T @ dz2) * silu_prime(f["z1"])
+    gb1 = dz1.sum(axis=1)
+    gW1 = dz1 @ f["X"].T
+    return np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3, np.zeros(mdl.K.size)])

@@ -45,6 +45,9 @@ static void free_plan(vdw_ctx* c) {
     c->d_acc = nullptr;
     c->d_in = c->d_v = nullptr;
     c->d_E = nullptr;
+    cudaFree(c->d_gtmp);
+    c->d_gtmp = nullptr;
+    learned_free(c);
     c->planned = 0;
 }
 
@@ -187,8 +190,15 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
 
 int vdw_energy_potential(vdw_handle c, const float* n, const float* grad, double* E, float* v, float* w,
                          void* stream) {
-    if (!c || !n || !grad) return VDW_ERR_ARG;
+    if (!c || !n) return VDW_ERR_ARG;
     if (!c->planned) return VDW_ERR_STATE;
+    if (!grad) {
+        // grad n = D n with the library's spectral derivative
+        if (!c->d_gtmp) VDW_CUDA(cudaMalloc(&c->d_gtmp, sizeof(float) * 3 * (size_t)c->g.N));
+        const int rc = vdw_spectral_gradient(c, n, c->d_gtmp, stream);
+        if (rc) return rc;
+        grad = c->d_gtmp;
+    }
     return pipeline_run(c, n, grad, E, v, w, (cudaStream_t)stream);
 }
 

@@ -45,6 +45,40 @@ struct GridArgs {
     LinePlan p1, p2, p3;   // line transforms along x, y, z
 };
 
+// Learned reduced basis: sizes fixed at compile time.
+constexpr int LRN_H = 64;                          // hidden units of the channel network
+constexpr int LRN_M = 8;                           // channels
+constexpr int LRN_P = LRN_M * (LRN_M + 1) / 2;     // learned pair kernels m <= n
+constexpr int LRN_N3 = 16;                         // last layer padded to a legal MMA width
+// offsets in the flat parameter vector: W1 [H][2], b1, W2 [H][H], b2, W3 [M][H], b3, K [P][J]
+constexpr int LRN_OFF_W1 = 0;
+constexpr int LRN_OFF_B1 = LRN_OFF_W1 + LRN_H * 2;
+constexpr int LRN_OFF_W2 = LRN_OFF_B1 + LRN_H;
+constexpr int LRN_OFF_B2 = LRN_OFF_W2 + LRN_H * LRN_H;
+constexpr int LRN_OFF_W3 = LRN_OFF_B2 + LRN_H;
+constexpr int LRN_OFF_B3 = LRN_OFF_W3 + LRN_M * LRN_H;
+constexpr int LRN_OFF_K = LRN_OFF_B3 + LRN_M;
+
+// Device view of a loaded learned model (kernel parameter).  The bf16
+// operands are stored in the tensor-core layout (tc.cuh) as raw 16-bit words.
+struct LearnedArgs {
+    int J;                  // knots
+    float dk, inv_dk;       // knot spacing and its inverse
+    float mu1, inv_sig1, mu2, inv_sig2, eps2;  // feature standardisation, eps^2
+    const float* w1;        // [H][2] bf16-rounded values
+    const float* b1;        // [H]
+    const float* b2;        // [H]
+    const float* b3;        // [M]
+    const uint16_t* w2f;    // forward operand W2 [H out][H in]
+    const uint16_t* w3f;    // forward operand W3 [16 (M padded)][H]
+    const uint16_t* w3t;    // transposed-product operand W3^T [H][16]
+    const uint16_t* w2t;    // transposed-product operand W2^T [H][H]
+    const float* w2r;       // W2 bf16-rounded values, row-major [H][H] (CUDA-core kernels)
+    const float* w3r;       // W3 bf16-rounded values, row-major [M][H]
+    const float2* knots;    // [J-1][P]: (K[j], K[j+1] - K[j]) per interval
+    int* err;               // set when a tensor-core wait gives up
+};
+
 }  // namespace vdw
 
 // The context behind the opaque vdw_handle.
@@ -75,7 +109,16 @@ struct vdw_ctx {
     float* d_in;                // [4N]
     float* d_v;                 // [N]
     double* d_E;                // [3]
+    float* d_gtmp;              // [3N] spectral gradient when the caller passes none
     size_t bytes;
+    // learned reduced basis (vdw_learned_load)
+    int lrn_loaded;
+    int lrn_J;
+    double lrn_kmax;
+    void* d_lrn;                // one allocation behind the LearnedArgs pointers
+    vdw::LearnedArgs la;
+    float* d_U;                 // [M][N] real-space u_m for the parameter gradient (on first use)
+    double* d_gK;               // [P][J] knot-gradient accumulator (on first use)
     // per-stage timing (vdw_profile_enable)
     int prof;
     cudaEvent_t ev[VDW_NSTAGES + 1];
@@ -100,6 +143,13 @@ int pipeline_plan_check(vdw_ctx* c, size_t* smem_plane, size_t* smem_pencil, siz
                         size_t* smem_div);
 int pipeline_make_twiddles(vdw_ctx* c);
 int pipeline_configure(vdw_ctx* c);
+// the divergence term of a potential (w(G) in d_wspec) and the energy reduction
+int pipeline_divergence(vdw_ctx* c, float* v, cudaStream_t s);
+int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, double* E, cudaStream_t s);
+
+// learned reduced basis (learned.cu)
+int learned_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s);
+void learned_free(vdw_ctx* c);
 
 // table launchers (table.cu)
 int table_build(const vdw_params* p, double* h_qmesh, double* h_phik, double* phi0, double* C_s);

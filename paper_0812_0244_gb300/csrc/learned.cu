@@ -1,0 +1,1339 @@
+// Learned reduced basis: M = 8 channels theta_m = n w_m(x(n, |grad n|)) whose
+// weights come from a 2-64-64-8 SiLU network (bf16 operands on the tensor
+// cores, FP32 accumulation in tensor memory), contracted with a learned
+// piecewise-linear pair kernel K_mn(|G|) on uniform knots, plus the paper's
+// local correction Delta E (Eqs. DEnl, Depsnl).  The transform structure is
+// the plain method's (Eqs. Eoffk, epsilon, epsofk, Vi) with M channels:
+//
+//   L1 k_learned_theta     a cluster of 8 blocks per y plane: the network on
+//                          the plane's points (tiles of 128 points, one per
+//                          warpgroup), theta_m sent to block m's plane through
+//                          distributed shared memory, then block m's forward
+//                          plane transform; Delta E partial sums
+//   L2 k_learned_contract  y pencils of the 8 channels, u_m(G) = sum_n
+//                          K_mn(|G|) theta_n(G), FP64 energy, inverse y; in
+//                          training also dE/dK at the knots
+//   L3 k_learned_assemble  a cluster of 8 blocks per y plane: inverse plane
+//                          transform of u_m in block m; then per point the
+//                          network again and its Jacobian-vector product with
+//                          u (tensor cores), v_loc and w = g grad n (Eq. Vi);
+//                          forward plane transforms of w by blocks 0..2
+//   then the plain method's divergence kernels (P4, P5).
+//
+// Training kernels: the parameter gradient of E through the network
+// (k_learned_param_grad, CUDA cores, FP32 sums into FP64), a regression
+// gradient for fitting the channel weights to targets, and an Adam step.
+// Utilities: the plain cardinal weights p_a(q) and the spectral gradient.
+#include "plane.cuh"
+#include "pointwise.cuh"
+#include "tc.cuh"
+
+#include <cooperative_groups.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+namespace vdw {
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int L_CTAS = 8;         // blocks per cluster = channels
+constexpr int L_THREADS = 256;    // two warpgroups
+constexpr int L_TILE = 128;       // points per warpgroup tile
+constexpr int L_MAXJ = 256;       // knots held in shared memory by the knot-gradient bins
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float silu_prime(float z) {
+    const float s = 1.f / (1.f + __expf(-z));
+    return s * (1.f + z * (1.f - s));
+}
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+    const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+    return lo | (hi << 16);
+}
+// 8 values -> one 16-byte core-matrix row
+__device__ __forceinline__ void store8_bf16(uint16_t* dst, const float* v) {
+    uint4 q;
+    q.x = pack_bf16(v[0], v[1]);
+    q.y = pack_bf16(v[2], v[3]);
+    q.z = pack_bf16(v[4], v[5]);
+    q.w = pack_bf16(v[6], v[7]);
+    *reinterpret_cast<uint4*>(dst) = q;
+}
+
+__device__ __forceinline__ void wg_bar(int wg) { asm volatile("bar.sync %0, %1;" ::"r"(1 + wg), "r"(128) : "memory"); }
+
+// Network features of Eq.-free form (no counterpart in the paper):
+// x1 = (ln n - mu1)/sig1, x2 = (1/2 ln(s2 + eps^2) - mu2)/sig2,
+// s2 = |grad n|^2 n^(-8/3), and the derivatives the potential needs.
+struct Feat {
+    float x1, x2;
+    float dx1_dn, dx2_dn;  // d x / d n
+    float gx2;             // (d x2 / d grad_c) / grad_c
+    bool ok;
+};
+__device__ __forceinline__ Feat features(float n, float gx, float gy, float gz, const LearnedArgs& la, float n_min) {
+    Feat f;
+    f.ok = (n > n_min) && isfinite(n);
+    const float ns = f.ok ? n : 1.f;
+    const float cb = cbrtf(ns);
+    const float n83 = 1.f / (ns * ns * cb * cb);
+    const float s2 = (gx * gx + gy * gy + gz * gz) * n83;
+    const float den = s2 + la.eps2;
+    f.x1 = (logf(ns) - la.mu1) * la.inv_sig1;
+    f.x2 = (0.5f * logf(den) - la.mu2) * la.inv_sig2;
+    f.dx1_dn = la.inv_sig1 / ns;
+    f.dx2_dn = -(4.f / 3.f) * s2 / (ns * den) * la.inv_sig2;
+    f.gx2 = n83 / den * la.inv_sig2;
+    return f;
+}
+
+// ---------------------------------------------------------------------------
+// shared memory of the tensor-core network
+// ---------------------------------------------------------------------------
+struct __align__(128) MlpShared {
+    uint16_t w2f[LRN_H * LRN_H];
+    uint16_t w3f[LRN_N3 * LRN_H];
+    uint16_t w3t[LRN_H * LRN_N3];
+    uint16_t w2t[LRN_H * LRN_H];
+    float w1[2 * LRN_H], b1[LRN_H], b2[LRN_H], b3[LRN_M];
+};
+struct __align__(128) MlpWG {
+    uint16_t A[L_TILE * LRN_H];   // activation operand of the tile
+    uint16_t U[L_TILE * LRN_N3];  // cotangent operand (Jacobian-vector product)
+};
+struct MlpCtl {
+    uint64_t bar[2];
+    uint32_t tmem;
+    int abort[2];  // per warpgroup: a wait gave up
+};
+
+__device__ void mlp_load_weights(MlpShared* S, const LearnedArgs& la, bool transposed) {
+    const uint4* s1 = reinterpret_cast<const uint4*>(la.w2f);
+    uint4* d1 = reinterpret_cast<uint4*>(S->w2f);
+    for (int i = threadIdx.x; i < LRN_H * LRN_H / 8; i += blockDim.x) d1[i] = s1[i];
+    const uint4* s2 = reinterpret_cast<const uint4*>(la.w3f);
+    uint4* d2 = reinterpret_cast<uint4*>(S->w3f);
+    for (int i = threadIdx.x; i < LRN_N3 * LRN_H / 8; i += blockDim.x) d2[i] = s2[i];
+    if (transposed) {
+        const uint4* s3 = reinterpret_cast<const uint4*>(la.w3t);
+        uint4* d3 = reinterpret_cast<uint4*>(S->w3t);
+        for (int i = threadIdx.x; i < LRN_H * LRN_N3 / 8; i += blockDim.x) d3[i] = s3[i];
+        const uint4* s4 = reinterpret_cast<const uint4*>(la.w2t);
+        uint4* d4 = reinterpret_cast<uint4*>(S->w2t);
+        for (int i = threadIdx.x; i < LRN_H * LRN_H / 8; i += blockDim.x) d4[i] = s4[i];
+    }
+    for (int i = threadIdx.x; i < 2 * LRN_H; i += blockDim.x) S->w1[i] = la.w1[i];
+    for (int i = threadIdx.x; i < LRN_H; i += blockDim.x) {
+        S->b1[i] = la.b1[i];
+        S->b2[i] = la.b2[i];
+    }
+    for (int i = threadIdx.x; i < LRN_M; i += blockDim.x) S->b3[i] = la.b3[i];
+}
+
+// Block setup: barriers, tensor memory (256 columns: 128 per warpgroup).
+__device__ void mlp_setup(MlpCtl* ctl) {
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&ctl->bar[0], 1);
+        tc::mbar_init(&ctl->bar[1], 1);
+        ctl->abort[0] = ctl->abort[1] = 0;
+    }
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&ctl->tmem, 256);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__device__ void mlp_teardown(MlpCtl* ctl) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_free(ctl->tmem, 256);
+}
+
+// Issue K/16 MMAs of A (K-wide) x B^T into column col of this warpgroup's
+// tensor memory, wait for them, and agree across the warpgroup on success.
+__device__ __forceinline__ bool wg_mma(MlpCtl* ctl, int wg, int r, uint32_t& phase, const uint16_t* A,
+                                       const uint16_t* B, int K, int N, uint32_t col, int* err) {
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    wg_bar(wg);
+    if (r == 0) {
+        tc::fence_after_sync();
+        const uint32_t a = tc::smem_u32(A), b = tc::smem_u32(B);
+        const uint32_t d = ctl->tmem + (uint32_t)(wg * 128) + col;
+        for (int k = 0; k < K / 16; ++k)
+            tc::mma_bf16(d, tc::operand_desc(a, K, k), tc::operand_desc(b, K, k), tc::idesc_bf16(128, N), k > 0);
+        tc::mma_commit(&ctl->bar[wg]);
+    }
+    const bool ok = tc::mbar_wait(&ctl->bar[wg], phase);
+    phase ^= 1u;
+    if (!ok) {
+        atomicExch(&ctl->abort[wg], 1);
+        atomicExch(err, 1);
+    }
+    wg_bar(wg);
+    tc::fence_after_sync();
+    return ctl->abort[wg] == 0;
+}
+
+// tensor-memory address of this thread's lane, column col of its warpgroup
+__device__ __forceinline__ uint32_t lane_addr(const MlpCtl* ctl, int wg, uint32_t col) {
+    const int warp = threadIdx.x >> 5;
+    return ctl->tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(wg * 128) + col;
+}
+
+// Forward network on the warpgroup's tile (row r = this thread's point):
+// layer 1 on the CUDA cores, layers 2 and 3 on the tensor cores.  Leaves the
+// layer-2 accumulator in columns [0, 64) and returns the 8 outputs in o.
+__device__ bool mlp_forward(MlpShared* S, MlpWG* W, MlpCtl* ctl, int wg, int r, uint32_t& phase, float x1,
+                            float x2, float* o, int* err) {
+#pragma unroll
+    for (int c = 0; c < LRN_H / 8; ++c) {
+        float h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = 8 * c + q;
+            h[q] = silu(fmaf(S->w1[2 * j], x1, fmaf(S->w1[2 * j + 1], x2, S->b1[j])));
+        }
+        store8_bf16(W->A + tc::kmaj(r, 8 * c, LRN_H), h);
+    }
+    if (!wg_mma(ctl, wg, r, phase, W->A, S->w2f, LRN_H, LRN_H, 0, err)) return false;
+#pragma unroll
+    for (int c = 0; c < LRN_H / 16; ++c) {
+        float v[16];
+        tc::tmem_ld16(lane_addr(ctl, wg, 16 * c), v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = silu(v[q] + S->b2[16 * c + q]);
+        store8_bf16(W->A + tc::kmaj(r, 16 * c, LRN_H), v);
+        store8_bf16(W->A + tc::kmaj(r, 16 * c + 8, LRN_H), v + 8);
+    }
+    if (!wg_mma(ctl, wg, r, phase, W->A, S->w3f, LRN_H, LRN_N3, 64, err)) return false;
+    float v[16];
+    tc::tmem_ld16(lane_addr(ctl, wg, 64), v);
+#pragma unroll
+    for (int m = 0; m < LRN_M; ++m) o[m] = v[m] + S->b3[m];
+    return true;
+}
+
+// Jacobian-vector product of the network with the cotangent u (8 values):
+// c_j = sum_m u_m d w_m / d x_j.  Needs the forward's layer-2 accumulator in
+// columns [0, 64); uses [64, 128) and then [0, 64) again.
+__device__ bool mlp_vjp(MlpShared* S, MlpWG* W, MlpCtl* ctl, int wg, int r, uint32_t& phase, float x1, float x2,
+                        const float* u, float& c1, float& c2, int* err) {
+    float uu[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) uu[m] = m < LRN_M ? u[m] : 0.f;
+    store8_bf16(W->U + tc::kmaj(r, 0, LRN_N3), uu);
+    store8_bf16(W->U + tc::kmaj(r, 8, LRN_N3), uu + 8);
+    // G2 = U W3 (tile x 64) into columns [64, 128)
+    if (!wg_mma(ctl, wg, r, phase, W->U, S->w3t, LRN_N3, LRN_H, 64, err)) return false;
+#pragma unroll
+    for (int c = 0; c < LRN_H / 16; ++c) {
+        float z[16], g[16];
+        tc::tmem_ld16(lane_addr(ctl, wg, 16 * c), z);
+        tc::tmem_ld16(lane_addr(ctl, wg, 64 + 16 * c), g);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) g[q] *= silu_prime(z[q] + S->b2[16 * c + q]);
+        store8_bf16(W->A + tc::kmaj(r, 16 * c, LRN_H), g);
+        store8_bf16(W->A + tc::kmaj(r, 16 * c + 8, LRN_H), g + 8);
+    }
+    // G1 = delta2 W2 (tile x 64) into columns [0, 64)
+    if (!wg_mma(ctl, wg, r, phase, W->A, S->w2t, LRN_H, LRN_H, 0, err)) return false;
+    c1 = 0.f;
+    c2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < LRN_H / 16; ++c) {
+        float g[16];
+        tc::tmem_ld16(lane_addr(ctl, wg, 16 * c), g);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int j = 16 * c + q;
+            const float z1 = fmaf(S->w1[2 * j], x1, fmaf(S->w1[2 * j + 1], x2, S->b1[j]));
+            const float d1 = g[q] * silu_prime(z1);
+            c1 = fmaf(S->w1[2 * j], d1, c1);
+            c2 = fmaf(S->w1[2 * j + 1], d1, c2);
+        }
+    }
+    return true;
+}
+
+// dynamic shared memory of the cluster kernels: plane, twiddles, then the
+// network's shared block (128-byte aligned)
+__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
+__host__ __device__ inline size_t plane_bytes(int N3, int Nh, int N1) {
+    return align128(sizeof(float2) * ((size_t)N3 * Nh + N1 + N3));
+}
+
+// ---------------------------------------------------------------------------
+// L0: model preparation (flat FP32 parameters -> device operands)
+// ---------------------------------------------------------------------------
+__global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la) {
+    float* w1 = const_cast<float*>(la.w1);
+    float* b1 = const_cast<float*>(la.b1);
+    float* b2 = const_cast<float*>(la.b2);
+    float* b3 = const_cast<float*>(la.b3);
+    float* w2r = const_cast<float*>(la.w2r);
+    float* w3r = const_cast<float*>(la.w3r);
+    uint16_t* w2f = const_cast<uint16_t*>(la.w2f);
+    uint16_t* w3f = const_cast<uint16_t*>(la.w3f);
+    uint16_t* w3t = const_cast<uint16_t*>(la.w3t);
+    uint16_t* w2t = const_cast<uint16_t*>(la.w2t);
+    float2* kn = const_cast<float2*>(la.knots);
+    const int t = threadIdx.x + blockIdx.x * blockDim.x, nt = blockDim.x * gridDim.x;
+    auto bfu = [](float x) { return (uint16_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)); };
+    for (int i = t; i < 2 * LRN_H; i += nt) w1[i] = bf16r(flat[LRN_OFF_W1 + i]);
+    for (int i = t; i < LRN_H; i += nt) {
+        b1[i] = flat[LRN_OFF_B1 + i];
+        b2[i] = flat[LRN_OFF_B2 + i];
+    }
+    for (int i = t; i < LRN_M; i += nt) b3[i] = flat[LRN_OFF_B3 + i];
+    for (int i = t; i < LRN_H * LRN_H; i += nt) {
+        const int o = i / LRN_H, j = i % LRN_H;  // W2[o][j]: output o, input j
+        const float x = flat[LRN_OFF_W2 + i];
+        w2r[i] = bf16r(x);
+        w2f[tc::kmaj(o, j, LRN_H)] = bfu(x);
+        w2t[tc::kmaj(j, o, LRN_H)] = bfu(x);
+    }
+    for (int i = t; i < LRN_N3 * LRN_H; i += nt) {
+        const int m = i / LRN_H, j = i % LRN_H;  // W3[m][j], rows m >= M are zero
+        const float x = m < LRN_M ? flat[LRN_OFF_W3 + m * LRN_H + j] : 0.f;
+        if (m < LRN_M) w3r[m * LRN_H + j] = bf16r(x);
+        w3f[tc::kmaj(m, j, LRN_H)] = bfu(x);
+        w3t[tc::kmaj(j, m, LRN_N3)] = bfu(x);
+    }
+    const float* K = flat + LRN_OFF_K;
+    for (int i = t; i < (la.J - 1) * LRN_P; i += nt) {
+        const int j = i / LRN_P, p = i % LRN_P;
+        const float k0 = K[p * la.J + j], k1 = K[p * la.J + j + 1];
+        kn[i] = make_float2(k0, k1 - k0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L1: network, channels, forward plane transforms
+// ---------------------------------------------------------------------------
+// Tile T (128 consecutive points of the plane, index i = z N1 + x) belongs to
+// block (T / 2) mod 8, warpgroup T mod 2.
+template <int CN1, int CN3>
+__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
+    k_learned_theta(const float* __restrict__ n, const float* __restrict__ grad, GridArgs g, PointParams P,
+                    LearnedArgs la, const float2* __restrict__ tw, float2* __restrict__ spec,
+                    double* __restrict__ epart, unsigned long long* __restrict__ invalid) {
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ MlpCtl ctl;
+    __shared__ double red[32];
+    __shared__ float qm[MAX_NQ];
+    float2* plane = reinterpret_cast<float2*>(smraw);
+    float2* tw1 = plane + g.N3 * g.Nh;
+    float2* tw3 = tw1 + g.N1;
+    MlpShared* S = reinterpret_cast<MlpShared*>(smraw + plane_bytes(g.N3, g.Nh, g.N1));
+    MlpWG* Wb = reinterpret_cast<MlpWG*>(reinterpret_cast<unsigned char*>(S) + sizeof(MlpShared));
+    const int y = blockIdx.x;
+    const int rank = (int)cluster.block_rank();
+    const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
+    MlpWG* W = Wb + wg;
+    load_twiddles(tw1, tw, g.N1);
+    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    mlp_load_weights(S, la, false);
+    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
+    mlp_setup(&ctl);
+    float* pf = reinterpret_cast<float*>(plane);
+    float* rem[L_CTAS];
+#pragma unroll
+    for (int m = 0; m < L_CTAS; ++m) rem[m] = cluster.map_shared_rank(pf, m);
+    cluster.sync();  // every block of the cluster is running before remote stores
+    const int np = g.N1 * g.N3;
+    const int ntiles = (np + L_TILE - 1) / L_TILE;
+    const long long N = g.N;
+    uint32_t phase = 0;
+    double eacc = 0.0;
+    unsigned int bad = 0;
+    for (int T = 2 * rank + wg; T < ntiles; T += 2 * L_CTAS) {
+        const int i = T * L_TILE + r;
+        const bool in = i < np;
+        const int z = in ? i / g.N1 : 0, x = in ? i - z * g.N1 : 0;
+        const long long gi = (long long)g.N1 * (y + (long long)g.N2 * z) + x;
+        float ni = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        if (in) {
+            ni = n[gi];
+            gx = grad[gi];
+            gy = grad[N + gi];
+            gz = grad[2 * N + gi];
+        }
+        const Feat f = features(ni, gx, gy, gz, la, P.n_min);
+        const bool ok = in && f.ok;
+        if (in) {
+            bad += (!(ni >= 0.f) || !isfinite(ni)) ? 1u : 0u;
+            const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
+            if (qp.k != K_INVALID) eacc += (double)(0.5f * P.C_s * ni * ni / (qp.q * qp.q * qp.q));
+        }
+        float o[LRN_M];
+        if (!mlp_forward(S, W, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, la.err)) break;
+        if (in) {
+            const int off = packed_row(z, g.Nh) + 2 * x;
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) rem[m][off] = ok ? ni * o[m] : 0.f;
+        }
+    }
+    mlp_teardown(&ctl);
+    const double es = block_sum(eacc, red);
+    if (threadIdx.x == 0) epart[y * L_CTAS + rank] = es;
+    __syncthreads();
+    const double b = block_sum((double)bad, red);
+    if (threadIdx.x == 0 && b > 0.0) atomicAdd(invalid, (unsigned long long)b);
+    cluster.sync();  // all channels of the plane have arrived
+    plane_forward<CN1, CN3>(plane, g, tw1, tw3);
+    float2* dst = spec + ((long long)rank * g.N2 + y) * g.ncols;
+    for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
+}
+
+// ---------------------------------------------------------------------------
+// L2: pencils, learned kernel, energy (and dE/dK at the knots)
+// ---------------------------------------------------------------------------
+template <int CN2, bool GRADK>
+__global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ spec, GridArgs g, LearnedArgs la,
+                                                          const float2* __restrict__ tw, double* __restrict__ epart,
+                                                          int C, int write_back, double* __restrict__ gK,
+                                                          float halfOmega) {
+    constexpr int NQ = LRN_M;
+    extern __shared__ float2 sm[];
+    __shared__ double red[32];
+    const int N2 = CN2 > 0 ? CN2 : g.N2;
+    float2* lines = sm;  // [NQ][C][N2]
+    float2* tw2 = lines + NQ * C * N2;
+    float* bins = reinterpret_cast<float*>(tw2 + N2);  // [P][J] (GRADK)
+    load_twiddles(tw2, tw + g.N1, N2);
+    if (GRADK)
+        for (int i = threadIdx.x; i < LRN_P * la.J; i += blockDim.x) bins[i] = 0.f;
+    const int c0 = blockIdx.x * C;
+    const int tot = NQ * N2 * C;
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+        const int cc = i % C, rr = i / C, yy = rr % N2, a = rr / N2;
+        const int col = c0 + cc;
+        float2 val = make_float2(0.f, 0.f);
+        if (col < g.ncols) val = spec[((long long)a * N2 + yy) * g.ncols + col];
+        lines[(a * C + cc) * N2 + yy] = val;
+    }
+    __syncthreads();
+    pencils_fft<CN2, false>(lines, NQ * C, N2, g.p2, tw2);
+    __syncthreads();
+    const int npy = N2 / 2 + 1;
+    const int LS = C * N2;
+    double eacc = 0.0;
+    for (int task = threadIdx.x; task < C * npy; task += blockDim.x) {
+        const int cc = task / npy, ya = task - cc * npy;
+        const int col = c0 + cc;
+        if (col >= g.ncols) continue;
+        const int yb0 = N2 - ya;
+        const bool two = (ya != 0) && (yb0 != ya);
+        const int yb = two ? yb0 : ya;
+        const int kx = col % g.Nh, kz = col / g.Nh;
+        const int mz = (2 * kz <= g.N3) ? kz : kz - g.N3;
+        const float G2 = g.gx2 * (float)(kx * kx) + g.gy2 * (float)(ya * ya) + g.gz2 * (float)(mz * mz);
+        const float s = sqrtf(G2) * la.inv_dk;
+        const int j = min((int)s, la.J - 2);
+        const float t = s - (float)j;
+        const float2* cf = la.knots + (long long)j * LRN_P;
+        const float2* pa = lines + cc * N2 + ya;
+        const float2* pb = lines + cc * N2 + yb;
+        float2 ua[NQ], ub[NQ];
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) {
+            ua[a] = make_float2(0.f, 0.f);
+            ub[a] = make_float2(0.f, 0.f);
+        }
+        const bool single = (kx == 0) || (2 * kx == g.N1);
+        const float wgt = single ? 1.f : 2.f;
+        int p = 0;
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) {
+            const float2 taa = pa[a * LS], tba = pb[a * LS];
+#pragma unroll
+            for (int b = a; b < NQ; ++b, ++p) {
+                const float2 c = cf[p];
+                const float phi = fmaf(t, c.y, c.x);
+                const float2 tab = pa[b * LS], tbb = pb[b * LS];
+                ua[a].x = fmaf(phi, tab.x, ua[a].x);
+                ua[a].y = fmaf(phi, tab.y, ua[a].y);
+                ub[a].x = fmaf(phi, tbb.x, ub[a].x);
+                ub[a].y = fmaf(phi, tbb.y, ub[a].y);
+                if (b != a) {
+                    ua[b].x = fmaf(phi, taa.x, ua[b].x);
+                    ua[b].y = fmaf(phi, taa.y, ua[b].y);
+                    ub[b].x = fmaf(phi, tba.x, ub[b].x);
+                    ub[b].y = fmaf(phi, tba.y, ub[b].y);
+                }
+                if (GRADK) {
+                    // d E / d K_p at the two knots of |G|: 1/2 Omega w_G (2 - delta_ab) Re(conj th_a th_b)
+                    float rr2 = taa.x * tab.x + taa.y * tab.y;
+                    if (two) rr2 += tba.x * tbb.x + tba.y * tbb.y;
+                    const float rv = halfOmega * wgt * (b != a ? 2.f : 1.f) * rr2;
+                    atomicAdd(&bins[p * la.J + j], (1.f - t) * rv);
+                    atomicAdd(&bins[p * la.J + j + 1], t * rv);
+                }
+            }
+        }
+        float ea = 0.f, eb = 0.f;
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) {
+            const float2 taa = pa[a * LS], tba = pb[a * LS];
+            ea = fmaf(taa.x, ua[a].x, fmaf(taa.y, ua[a].y, ea));
+            eb = fmaf(tba.x, ub[a].x, fmaf(tba.y, ub[a].y, eb));
+        }
+        eacc += ((double)ea + (two ? (double)eb : 0.0)) * (double)wgt;
+        if (write_back) {
+            float2* wa = lines + cc * N2 + ya;
+            float2* wb = lines + cc * N2 + yb;
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) {
+                wa[a * LS] = cscale(ua[a], g.invN);
+                if (two) wb[a * LS] = cscale(ub[a], g.invN);
+            }
+        }
+    }
+    const double es = block_sum(eacc, red);
+    if (threadIdx.x == 0) epart[blockIdx.x] = es;
+    if (GRADK) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < LRN_P * la.J; i += blockDim.x)
+            if (bins[i] != 0.f) atomicAdd(&gK[i], (double)bins[i]);
+    }
+    if (!write_back) return;
+    __syncthreads();
+    pencils_fft<CN2, true>(lines, NQ * C, N2, g.p2, tw2);
+    __syncthreads();
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+        const int cc = i % C, rr = i / C, yy = rr % N2, a = rr / N2;
+        const int col = c0 + cc;
+        if (col < g.ncols) spec[((long long)a * N2 + yy) * g.ncols + col] = lines[(a * C + cc) * N2 + yy];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L3: inverse plane transforms of u_m, network Jacobian, assembly of Eq. (Vi)
+// ---------------------------------------------------------------------------
+// mode 0: v_loc to v, w = g grad n to w_out; mode 1: v_loc to v, w(G) to wspec;
+// mode 2: only the real-space u_m to U (parameter gradient).
+template <int CN1, int CN3>
+__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
+    k_learned_assemble(const float2* __restrict__ spec, const float* __restrict__ n, const float* __restrict__ grad,
+                       GridArgs g, PointParams P, LearnedArgs la, const float2* __restrict__ tw,
+                       float* __restrict__ v, float* __restrict__ w_out, float2* __restrict__ wspec,
+                       float* __restrict__ U, int mode) {
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ MlpCtl ctl;
+    __shared__ float qm[MAX_NQ];
+    float2* plane = reinterpret_cast<float2*>(smraw);
+    float2* tw1 = plane + g.N3 * g.Nh;
+    float2* tw3 = tw1 + g.N1;
+    MlpShared* S = reinterpret_cast<MlpShared*>(smraw + plane_bytes(g.N3, g.Nh, g.N1));
+    MlpWG* Wb = reinterpret_cast<MlpWG*>(reinterpret_cast<unsigned char*>(S) + sizeof(MlpShared));
+    float* gg_s = reinterpret_cast<float*>(Wb + 2);  // g of this block's tiles
+    const int y = blockIdx.x;
+    const int rank = (int)cluster.block_rank();
+    const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    MlpWG* W = Wb + wg;
+    const long long N = g.N;
+    load_twiddles(tw1, tw, g.N1);
+    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    if (mode != 2) mlp_load_weights(S, la, true);
+    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
+    // u_m of this block's channel
+    const float2* src = spec + ((long long)rank * g.N2 + y) * g.ncols;
+    for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
+    __syncthreads();
+    plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
+    float* pf = reinterpret_cast<float*>(plane);
+    if (mode == 2) {
+        for (int z = warp; z < g.N3; z += nw) {
+            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+            const float* srow = pf + packed_row(z, g.Nh);
+            for (int x = lane; x < g.N1; x += 32) U[(long long)rank * N + row + x] = srow[2 * x];
+        }
+        return;
+    }
+    mlp_setup(&ctl);
+    const float* rem[L_CTAS];
+#pragma unroll
+    for (int m = 0; m < L_CTAS; ++m) rem[m] = cluster.map_shared_rank(pf, m);
+    cluster.sync();  // every channel's u is in place
+    const int np = g.N1 * g.N3;
+    const int ntiles = (np + L_TILE - 1) / L_TILE;
+    uint32_t phase = 0;
+    for (int T = 2 * rank + wg; T < ntiles; T += 2 * L_CTAS) {
+        const int i = T * L_TILE + r;
+        const bool in = i < np;
+        const int z = in ? i / g.N1 : 0, x = in ? i - z * g.N1 : 0;
+        const long long gi = (long long)g.N1 * (y + (long long)g.N2 * z) + x;
+        float ni = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        float u[LRN_M];
+        if (in) {
+            ni = n[gi];
+            gx = grad[gi];
+            gy = grad[N + gi];
+            gz = grad[2 * N + gi];
+            const int off = packed_row(z, g.Nh) + 2 * x;
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) u[m] = rem[m][off];
+        } else {
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) u[m] = 0.f;
+        }
+        const Feat f = features(ni, gx, gy, gz, la, P.n_min);
+        const bool ok = in && f.ok;
+        const float x1 = ok ? f.x1 : 0.f, x2 = ok ? f.x2 : 0.f;
+        float o[LRN_M];
+        if (!mlp_forward(S, W, &ctl, wg, r, phase, x1, x2, o, la.err)) break;
+        float c1 = 0.f, c2 = 0.f;
+        if (!mlp_vjp(S, W, &ctl, wg, r, phase, x1, x2, u, c1, c2, la.err)) break;
+        float vl = 0.f, gg = 0.f;
+        if (ok) {
+            float s0 = 0.f;
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) s0 = fmaf(u[m], o[m], s0);
+            const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
+            float dEn = 0.f, dEg = 0.f;
+            if (qp.k != K_INVALID) {
+                const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
+                const float cn = 1.5f * P.C_s * ni * ni / q4;
+                dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
+                dEg = -cn * qp.dq_dg;
+            }
+            vl = s0 + ni * (c1 * f.dx1_dn + c2 * f.dx2_dn) + dEn;
+            gg = ni * c2 * f.gx2 + dEg;
+        }
+        if (in) {
+            if (v) v[gi] = vl;
+            if (mode == 0 && w_out) {
+                w_out[gi] = gg * gx;
+                w_out[N + gi] = gg * gy;
+                w_out[2 * N + gi] = gg * gz;
+            }
+        }
+        gg_s[(T >> 4) * 2 * L_TILE + (T & 1) * L_TILE + r] = gg;
+    }
+    mlp_teardown(&ctl);
+    cluster.sync();  // g of every tile is in place; u planes no longer read
+    if (mode == 1 && rank < 3) {
+        const int c = rank;
+        const float* ggr[L_CTAS];
+#pragma unroll
+        for (int m = 0; m < L_CTAS; ++m) ggr[m] = cluster.map_shared_rank(gg_s, m);
+        for (int z = warp; z < g.N3; z += nw) {
+            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+            float* dst = pf + packed_row(z, g.Nh);
+            for (int x = lane; x < g.N1; x += 32) {
+                const int i = z * g.N1 + x;
+                const int T = i / L_TILE, rr = i - T * L_TILE;
+                const float ggv = ggr[(T >> 1) & (L_CTAS - 1)][(T >> 4) * 2 * L_TILE + (T & 1) * L_TILE + rr];
+                dst[2 * x] = ggv * grad[c * N + row + x];
+            }
+        }
+        __syncthreads();
+        plane_forward<CN1, CN3>(plane, g, tw1, tw3);
+        float2* dst = wspec + ((long long)c * g.N2 + y) * g.ncols;
+        for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
+    }
+    cluster.sync();  // keep g alive until every block is done reading it
+}
+
+// ---------------------------------------------------------------------------
+// network outputs alone (tests, fitting): w_m at every point
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(L_THREADS, 1) k_learned_channels(const float* __restrict__ n,
+                                                                   const float* __restrict__ grad, long long N,
+                                                                   float n_min, LearnedArgs la,
+                                                                   float* __restrict__ wout) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ MlpCtl ctl;
+    MlpShared* S = reinterpret_cast<MlpShared*>(smraw);
+    MlpWG* Wb = reinterpret_cast<MlpWG*>(smraw + sizeof(MlpShared));
+    const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
+    mlp_load_weights(S, la, false);
+    mlp_setup(&ctl);
+    uint32_t phase = 0;
+    const long long ntiles = (N + L_TILE - 1) / L_TILE;
+    for (long long T = 2 * (long long)blockIdx.x + wg; T < ntiles; T += 2 * (long long)gridDim.x) {
+        const long long i = T * L_TILE + r;
+        const bool in = i < N;
+        float ni = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        if (in) {
+            ni = n[i];
+            gx = grad[i];
+            gy = grad[N + i];
+            gz = grad[2 * N + i];
+        }
+        const Feat f = features(ni, gx, gy, gz, la, n_min);
+        const bool ok = in && f.ok;
+        float o[LRN_M];
+        if (!mlp_forward(S, Wb + wg, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, la.err)) break;
+        if (in)
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) wout[m * N + i] = ok ? o[m] : 0.f;
+    }
+    mlp_teardown(&ctl);
+}
+
+// ---------------------------------------------------------------------------
+// parameter gradient through the network (CUDA cores, FP32, FP64 totals)
+// ---------------------------------------------------------------------------
+// mode 0 (energy): cotangent of w_m at point i is coef dOmega n_i U[m][i];
+// mode 1 (fit):    coef 2 wt_i (w_m - T[m][i]) for the loss sum_i wt_i |w - T|^2.
+constexpr int PG_TILE = 128;
+constexpr int PG_THREADS = 256;
+constexpr int PG_LD = LRN_H + 1;  // padded row of the per-point tiles
+
+__global__ void __launch_bounds__(PG_THREADS, 1) k_learned_param_grad(
+    const float* __restrict__ n, const float* __restrict__ grad, long long N, float n_min, LearnedArgs la,
+    const float* __restrict__ cot, const float* __restrict__ wt, int mode, float coef, double* __restrict__ gout) {
+    extern __shared__ float smf[];
+    float* W2 = smf;                          // [H][H]
+    float* W3 = W2 + LRN_H * LRN_H;           // [M][H]
+    float* w1 = W3 + LRN_M * LRN_H;           // [H][2]
+    float* b1 = w1 + 2 * LRN_H;
+    float* b2 = b1 + LRN_H;
+    float* b3 = b2 + LRN_H;                   // [M] (padded to 8)
+    float* H1 = b3 + LRN_M;                   // [TILE][LD]
+    float* H2 = H1 + PG_TILE * PG_LD;         // [TILE][LD]; later delta z1
+    float* DZ2 = H2 + PG_TILE * PG_LD;        // [TILE][LD]
+    float* DO = DZ2 + PG_TILE * PG_LD;        // [TILE][M]
+    float* X = DO + PG_TILE * LRN_M;          // [TILE][2]
+    const int t = threadIdx.x;
+    for (int i = t; i < LRN_H * LRN_H; i += PG_THREADS) W2[i] = la.w2r[i];
+    for (int i = t; i < LRN_M * LRN_H; i += PG_THREADS) W3[i] = la.w3r[i];
+    for (int i = t; i < 2 * LRN_H; i += PG_THREADS) w1[i] = la.w1[i];
+    for (int i = t; i < LRN_H; i += PG_THREADS) {
+        b1[i] = la.b1[i];
+        b2[i] = la.b2[i];
+    }
+    if (t < LRN_M) b3[t] = la.b3[t];
+    // accumulators: dW2[o][i0..i0+15] (o = t / 4, i0 = 16 (t % 4)), dW3[m][j0, j0+1]
+    // (m = t / 32, j0 = 2 (t % 32)), db2[o] (t % 4 == 0), db3 (t < M),
+    // dW1[j][c] and db1[j] for t < 64 (j = t)
+    float aW2[16], aW3[2], ab2 = 0.f, ab3 = 0.f, aW1[2] = {0.f, 0.f}, ab1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) aW2[q] = 0.f;
+    aW3[0] = aW3[1] = 0.f;
+    const float dOmegaCoef = coef;
+    const long long ntiles = (N + PG_TILE - 1) / PG_TILE;
+    for (long long T = blockIdx.x; T < ntiles; T += gridDim.x) {
+        __syncthreads();
+        if (t < PG_TILE) {
+            const long long i = T * PG_TILE + t;
+            const bool in = i < N;
+            float ni = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+            if (in) {
+                ni = n[i];
+                gx = grad[i];
+                gy = grad[N + i];
+                gz = grad[2 * N + i];
+            }
+            const Feat f = features(ni, gx, gy, gz, la, n_min);
+            const bool ok = in && f.ok;
+            const float x1 = ok ? f.x1 : 0.f, x2 = ok ? f.x2 : 0.f;
+            X[2 * t] = x1;
+            X[2 * t + 1] = x2;
+            float* h1 = H1 + t * PG_LD;
+            for (int j = 0; j < LRN_H; ++j)
+                h1[j] = bf16r(silu(fmaf(w1[2 * j], x1, fmaf(w1[2 * j + 1], x2, b1[j]))));
+            float* h2 = H2 + t * PG_LD;
+            float* dz2 = DZ2 + t * PG_LD;
+            for (int o = 0; o < LRN_H; ++o) {
+                float z = b2[o];
+                for (int j = 0; j < LRN_H; ++j) z = fmaf(W2[o * LRN_H + j], h1[j], z);
+                dz2[o] = z;  // pre-activation, replaced by its delta below
+                h2[o] = bf16r(silu(z));
+            }
+            float dout[LRN_M];
+            for (int m = 0; m < LRN_M; ++m) {
+                float d = 0.f;
+                if (ok) {
+                    if (mode == 0) {
+                        d = dOmegaCoef * ni * cot[m * N + i];
+                    } else {
+                        float om = b3[m];
+                        for (int j = 0; j < LRN_H; ++j) om = fmaf(W3[m * LRN_H + j], h2[j], om);
+                        d = dOmegaCoef * 2.f * wt[i] * (om - cot[m * N + i]);
+                    }
+                }
+                dout[m] = d;
+                DO[t * LRN_M + m] = d;
+            }
+            for (int o = 0; o < LRN_H; ++o) {
+                float dh = 0.f;
+                for (int m = 0; m < LRN_M; ++m) dh = fmaf(W3[m * LRN_H + o], dout[m], dh);
+                dz2[o] = dh * silu_prime(dz2[o]);
+            }
+        }
+        __syncthreads();
+        {
+            const int o = t >> 2, i0 = 16 * (t & 3);
+            for (int p = 0; p < PG_TILE; ++p) {
+                const float d = DZ2[p * PG_LD + o];
+                const float* h1 = H1 + p * PG_LD + i0;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) aW2[q] = fmaf(d, h1[q], aW2[q]);
+                if ((t & 3) == 0) ab2 += d;
+            }
+            const int m = t >> 5, j0 = 2 * (t & 31);
+            for (int p = 0; p < PG_TILE; ++p) {
+                const float d = DO[p * LRN_M + m];
+                aW3[0] = fmaf(d, H2[p * PG_LD + j0], aW3[0]);
+                aW3[1] = fmaf(d, H2[p * PG_LD + j0 + 1], aW3[1]);
+                if (t < LRN_M) ab3 += DO[p * LRN_M + t];
+            }
+        }
+        __syncthreads();
+        if (t < PG_TILE) {
+            // delta z1 = (W2^T delta z2) * silu'(z1), into this point's H2 row
+            const float x1 = X[2 * t], x2 = X[2 * t + 1];
+            const float* dz2 = DZ2 + t * PG_LD;
+            float* dz1 = H2 + t * PG_LD;
+            for (int j = 0; j < LRN_H; ++j) {
+                float dh = 0.f;
+                for (int o = 0; o < LRN_H; ++o) dh = fmaf(W2[o * LRN_H + j], dz2[o], dh);
+                dz1[j] = dh * silu_prime(fmaf(w1[2 * j], x1, fmaf(w1[2 * j + 1], x2, b1[j])));
+            }
+        }
+        __syncthreads();
+        if (t < LRN_H) {
+            for (int p = 0; p < PG_TILE; ++p) {
+                const float d = H2[p * PG_LD + t];
+                aW1[0] = fmaf(d, X[2 * p], aW1[0]);
+                aW1[1] = fmaf(d, X[2 * p + 1], aW1[1]);
+                ab1 += d;
+            }
+        }
+    }
+    {
+        const int o = t >> 2, i0 = 16 * (t & 3);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) atomicAdd(&gout[LRN_OFF_W2 + o * LRN_H + i0 + q], (double)aW2[q]);
+        if ((t & 3) == 0) atomicAdd(&gout[LRN_OFF_B2 + o], (double)ab2);
+        const int m = t >> 5, j0 = 2 * (t & 31);
+        atomicAdd(&gout[LRN_OFF_W3 + m * LRN_H + j0], (double)aW3[0]);
+        atomicAdd(&gout[LRN_OFF_W3 + m * LRN_H + j0 + 1], (double)aW3[1]);
+        if (t < LRN_M) atomicAdd(&gout[LRN_OFF_B3 + t], (double)ab3);
+        if (t < LRN_H) {
+            atomicAdd(&gout[LRN_OFF_W1 + 2 * t], (double)aW1[0]);
+            atomicAdd(&gout[LRN_OFF_W1 + 2 * t + 1], (double)aW1[1]);
+            atomicAdd(&gout[LRN_OFF_B1 + t], (double)ab1);
+        }
+    }
+}
+
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, double a, int n) {
+    for (int i = threadIdx.x + blockIdx.x * blockDim.x; i < n; i += blockDim.x * gridDim.x) y[i] += a * x[i];
+}
+
+// ---------------------------------------------------------------------------
+// plain cardinal weights p_a(q(n, |grad n|)) at every point (fitting targets)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_basis_weights(const float* __restrict__ n, const float* __restrict__ grad,
+                                                       long long N, PointParams P, float* __restrict__ out) {
+    __shared__ SplineSmem sp;
+    load_spline_smem(&sp, P);
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const QPoint qp = q_point(n[i], grad[i], grad[N + i], grad[2 * N + i], P, sp.qm);
+        for (int a = 0; a < P.Nq; ++a) out[a * N + i] = qp.k == K_INVALID ? 0.f : cardinal_value(&sp, a, qp.k, qp.t);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// spectral gradient: grad f = IFFT(i G f(G)), Nyquist components removed
+// ---------------------------------------------------------------------------
+template <int CN1, int CN3>
+__global__ void __launch_bounds__(PLANE_THREADS, 2) k_field_plane(const float* __restrict__ f, GridArgs g,
+                                                                   const float2* __restrict__ tw,
+                                                                   float2* __restrict__ spec) {
+    extern __shared__ float2 sm[];
+    float2* plane = sm;
+    float2* tw1 = plane + g.N3 * g.Nh;
+    float2* tw3 = tw1 + g.N1;
+    const int y = blockIdx.x;
+    load_twiddles(tw1, tw, g.N1);
+    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    float* pf = reinterpret_cast<float*>(plane);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int z = warp; z < g.N3; z += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+        float* dst = pf + packed_row(z, g.Nh);
+        for (int x = lane; x < g.N1; x += 32) dst[2 * x] = f[row + x];
+    }
+    __syncthreads();
+    plane_forward<CN1, CN3>(plane, g, tw1, tw3);
+    float2* dst = spec + (long long)y * g.ncols;
+    for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
+}
+
+template <int CN2>
+__global__ void __launch_bounds__(256, 2) k_pencil_grad(const float2* __restrict__ spec, float2* __restrict__ wspec,
+                                                        GridArgs g, const float2* __restrict__ tw, int C) {
+    extern __shared__ float2 sm[];
+    const int N2 = CN2 > 0 ? CN2 : g.N2;
+    float2* lines = sm;  // [4][C][N2]: the field, then its three derivatives
+    float2* tw2 = lines + 4 * C * N2;
+    load_twiddles(tw2, tw + g.N1, N2);
+    const int c0 = blockIdx.x * C;
+    for (int i = threadIdx.x; i < N2 * C; i += blockDim.x) {
+        const int cc = i % C, yy = i / C;
+        const int col = c0 + cc;
+        lines[cc * N2 + yy] = col < g.ncols ? spec[(long long)yy * g.ncols + col] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    pencils_fft<CN2, false>(lines, C, N2, g.p2, tw2);
+    __syncthreads();
+    for (int pt = threadIdx.x; pt < C * N2; pt += blockDim.x) {
+        const int cc = pt / N2, yy = pt % N2;
+        const int col = c0 + cc;
+        const int kx = col % g.Nh, kz = col / g.Nh;
+        const int mx = (2 * kx == g.N1) ? 0 : kx;
+        const int my = (2 * yy == N2) ? 0 : ((2 * yy < N2) ? yy : yy - N2);
+        const int mz = (2 * kz == g.N3) ? 0 : ((2 * kz < g.N3) ? kz : kz - g.N3);
+        const float2 fv = lines[cc * N2 + yy];
+        const float G[3] = {g.gx * mx, g.gy * my, g.gz * mz};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)  // i G f / N
+            lines[((1 + c) * C + cc) * N2 + yy] = make_float2(-G[c] * fv.y * g.invN, G[c] * fv.x * g.invN);
+    }
+    __syncthreads();
+    pencils_fft<CN2, true>(lines + C * N2, 3 * C, N2, g.p2, tw2);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * N2 * C; i += blockDim.x) {
+        const int cc = i % C, rr = i / C, yy = rr % N2, c = rr / N2;
+        const int col = c0 + cc;
+        if (col < g.ncols) wspec[((long long)c * N2 + yy) * g.ncols + col] = lines[((1 + c) * C + cc) * N2 + yy];
+    }
+}
+
+template <int CN1, int CN3>
+__global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_inv3(const float2* __restrict__ wspec, GridArgs g,
+                                                                  const float2* __restrict__ tw,
+                                                                  float* __restrict__ out) {
+    extern __shared__ float2 sm[];
+    float2* plane = sm;
+    float2* tw1 = plane + g.N3 * g.Nh;
+    float2* tw3 = tw1 + g.N1;
+    const int y = blockIdx.x, c = blockIdx.y;
+    load_twiddles(tw1, tw, g.N1);
+    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    const float2* src = wspec + ((long long)c * g.N2 + y) * g.ncols;
+    for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
+    __syncthreads();
+    plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
+    const float* pf = reinterpret_cast<const float*>(plane);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int z = warp; z < g.N3; z += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+        const float* srow = pf + packed_row(z, g.Nh);
+        for (int x = lane; x < g.N1; x += 32) out[c * g.N + row + x] = srow[2 * x];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma & Ba) on FP32 parameters with FP64 gradients
+// ---------------------------------------------------------------------------
+__global__ void k_adam(float* __restrict__ p, const double* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float bc1,
+                       float bc2) {
+    for (long long i = threadIdx.x + blockIdx.x * (long long)blockDim.x; i < n; i += (long long)blockDim.x * gridDim.x) {
+        const float gi = (float)g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+size_t smem_cluster(const GridArgs& g, bool assemble) {
+    const int np = g.N1 * g.N3;
+    const int ntiles = (np + L_TILE - 1) / L_TILE;
+    const size_t gg = assemble ? sizeof(float) * (size_t)((ntiles + 2 * L_CTAS - 1) / (2 * L_CTAS)) * 2 * L_TILE : 0;
+    return plane_bytes(g.N3, g.Nh, g.N1) + sizeof(MlpShared) + 2 * sizeof(MlpWG) + gg;
+}
+int contract_cols(const GridArgs& g) {
+    int C = 8;
+    while (C > 1 && sizeof(float2) * ((size_t)LRN_M * C * g.N2 + g.N2) > 100 * 1024) --C;
+    return C;
+}
+size_t smem_contract(const GridArgs& g, int C, bool gradk, int J) {
+    return sizeof(float2) * ((size_t)LRN_M * C * g.N2 + g.N2) + (gradk ? sizeof(float) * (size_t)LRN_P * J : 0);
+}
+size_t smem_plane1(const GridArgs& g) { return sizeof(float2) * ((size_t)g.N3 * g.Nh + g.N1 + g.N3); }
+size_t smem_pgrad() {
+    return sizeof(float) * ((size_t)LRN_H * LRN_H + LRN_M * LRN_H + 2 * LRN_H + 2 * LRN_H + LRN_M +
+                            3 * (size_t)PG_TILE * PG_LD + PG_TILE * LRN_M + 2 * PG_TILE);
+}
+constexpr int GRAD_COLS = 8;
+size_t smem_pgrad_pencil(const GridArgs& g) { return sizeof(float2) * ((size_t)4 * GRAD_COLS * g.N2 + g.N2); }
+const size_t SMEM_LIMIT = 227 * 1024 - 4 * 1024;
+
+template <class K>
+int set_smem(K kernel, size_t bytes, const char* name) {
+    if (bytes > SMEM_LIMIT) {
+        set_error(std::string(name) + ": shared memory beyond the limit");
+        return VDW_ERR_SIZE;
+    }
+    VDW_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    return VDW_OK;
+}
+
+template <class K>
+int cluster_fits(K kernel, const GridArgs& g, size_t smem, const char* name) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.N2, L_CTAS);
+    cfg.blockDim = dim3(L_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = 1;
+    at.val.clusterDim.y = L_CTAS;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    VDW_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg));
+    if (nclusters < 1) {
+        set_error(std::string(name) + ": a cluster of 8 blocks does not fit");
+        return VDW_ERR_UNSUPPORTED;
+    }
+    return VDW_OK;
+}
+
+template <int CN1, int CN2, int CN3>
+int configure(vdw_ctx* c) {
+    const GridArgs& g = c->g;
+    const int C = contract_cols(g);
+    int rc = set_smem(k_learned_theta<CN1, CN3>, smem_cluster(g, false), "k_learned_theta");
+    if (!rc) rc = set_smem(k_learned_assemble<CN1, CN3>, smem_cluster(g, true), "k_learned_assemble");
+    if (!rc) rc = set_smem(k_learned_contract<CN2, false>, smem_contract(g, C, false, c->lrn_J), "k_learned_contract");
+    if (!rc) rc = set_smem(k_learned_contract<CN2, true>, smem_contract(g, C, true, c->lrn_J), "k_learned_contract");
+    if (!rc) rc = set_smem(k_field_plane<CN1, CN3>, smem_plane1(g), "k_field_plane");
+    if (!rc) rc = set_smem(k_plane_inv3<CN1, CN3>, smem_plane1(g), "k_plane_inv3");
+    if (!rc) rc = set_smem(k_pencil_grad<CN2>, smem_pgrad_pencil(g), "k_pencil_grad");
+    if (!rc) rc = set_smem(k_learned_param_grad, smem_pgrad(), "k_learned_param_grad");
+    if (!rc) rc = cluster_fits(k_learned_theta<CN1, CN3>, g, smem_cluster(g, false), "k_learned_theta");
+    if (!rc) rc = cluster_fits(k_learned_assemble<CN1, CN3>, g, smem_cluster(g, true), "k_learned_assemble");
+    return rc;
+}
+
+int configure_all(vdw_ctx* c) {
+    const GridArgs& g = c->g;
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) return configure<180, 180, 72>(c);
+    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) return configure<256, 256, 96>(c);
+    return configure<0, 0, 0>(c);
+}
+
+// learned scratch: partial sums [N2 * 8 + ncols]
+double* lrn_epart(vdw_ctx* c) {
+    return reinterpret_cast<double*>(static_cast<unsigned char*>(c->d_lrn) + 0);
+}
+
+enum RunKind { RUN_ENERGY = 0, RUN_GRAD = 1 };
+
+template <int CN1, int CN2, int CN3>
+int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, int kind, double coef,
+        double* gout, cudaStream_t s) {
+    const GridArgs& g = c->g;
+    const PointParams& P = c->pp;
+    const LearnedArgs& la = c->la;
+    const int C = contract_cols(g);
+    const int nb_c = (g.ncols + C - 1) / C;
+    const int nb0 = g.N2 * L_CTAS;
+    double* ep = lrn_epart(c);
+    const double Omega = c->L[0] * c->L[1] * c->L[2];
+    VDW_CUDA(cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long), s));
+    k_learned_theta<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, false), s>>>(
+        n, grad, g, P, la, c->d_tw, c->d_spec, ep, c->d_invalid);
+    const bool want_pot = (v != nullptr) || (w != nullptr);
+    if (kind == RUN_GRAD) {
+        VDW_CUDA(cudaMemsetAsync(c->d_gK, 0, sizeof(double) * LRN_P * c->lrn_J, s));
+        k_learned_contract<CN2, true><<<nb_c, 256, smem_contract(g, C, true, c->lrn_J), s>>>(
+            c->d_spec, g, la, c->d_tw, ep + nb0, C, 1, c->d_gK, (float)(0.5 * Omega / ((double)g.N * (double)g.N)));
+    } else {
+        k_learned_contract<CN2, false><<<nb_c, 256, smem_contract(g, C, false, c->lrn_J), s>>>(
+            c->d_spec, g, la, c->d_tw, ep + nb0, C, want_pot ? 1 : 0, nullptr, 0.f);
+    }
+    if (E) {
+        int rc = pipeline_energy_final(c, ep, nb0, nb_c, E, s);
+        if (rc) return rc;
+    }
+    if (kind == RUN_GRAD) {
+        k_learned_assemble<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, true), s>>>(
+            c->d_spec, n, grad, g, P, la, c->d_tw, nullptr, nullptr, nullptr, c->d_U, 2);
+        const double dOmega = Omega / (double)g.N;
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        k_learned_param_grad<<<nsm, PG_THREADS, smem_pgrad(), s>>>(n, grad, g.N, P.n_min, la, c->d_U, nullptr, 0,
+                                                                   (float)(coef * dOmega), gout);
+        k_axpy<<<36, 256, 0, s>>>(gout + LRN_OFF_K, c->d_gK, coef, LRN_P * c->lrn_J);
+    } else if (want_pot) {
+        const int mode = (w != nullptr) ? 0 : 1;
+        k_learned_assemble<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, true), s>>>(
+            c->d_spec, n, grad, g, P, la, c->d_tw, v, w, c->d_wspec, nullptr, mode);
+        if (mode == 1) {
+            int rc = pipeline_divergence(c, v, s);
+            if (rc) return rc;
+        }
+    }
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
+int run_any(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, int kind, double coef,
+            double* gout, cudaStream_t s) {
+    const GridArgs& g = c->g;
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) return run<180, 180, 72>(c, n, grad, E, v, w, kind, coef, gout, s);
+    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) return run<256, 256, 96>(c, n, grad, E, v, w, kind, coef, gout, s);
+    return run<0, 0, 0>(c, n, grad, E, v, w, kind, coef, gout, s);
+}
+
+template <int CN1, int CN2, int CN3>
+void spectral_gradient(vdw_ctx* c, const float* f, float* out, cudaStream_t s) {
+    const GridArgs& g = c->g;
+    k_field_plane<CN1, CN3><<<g.N2, PLANE_THREADS, smem_plane1(g), s>>>(f, g, c->d_tw, c->d_spec);
+    k_pencil_grad<CN2><<<(g.ncols + GRAD_COLS - 1) / GRAD_COLS, 256, smem_pgrad_pencil(g), s>>>(
+        c->d_spec, c->d_wspec, g, c->d_tw, GRAD_COLS);
+    k_plane_inv3<CN1, CN3><<<dim3(g.N2, 3), PLANE_THREADS, smem_plane1(g), s>>>(c->d_wspec, g, c->d_tw, out);
+}
+
+bool lrn_ready(vdw_ctx* c) {
+    if (!c->planned) {
+        set_error("no plan");
+        return false;
+    }
+    if (!c->lrn_loaded) {
+        set_error("no learned model loaded");
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+// Size of the learned context's allocation and its layout (256-byte aligned pieces).
+struct LrnLayout {
+    size_t epart, w1, b1, b2, b3, w2r, w3r, w2f, w3f, w3t, w2t, knots, err, gK, total;
+};
+static LrnLayout lrn_layout(const GridArgs& g, int J) {
+    LrnLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    L.epart = take(sizeof(double) * ((size_t)g.N2 * L_CTAS + g.ncols + 1));
+    L.w1 = take(sizeof(float) * 2 * LRN_H);
+    L.b1 = take(sizeof(float) * LRN_H);
+    L.b2 = take(sizeof(float) * LRN_H);
+    L.b3 = take(sizeof(float) * LRN_M);
+    L.w2r = take(sizeof(float) * LRN_H * LRN_H);
+    L.w3r = take(sizeof(float) * LRN_M * LRN_H);
+    L.w2f = take(2 * LRN_H * LRN_H);
+    L.w3f = take(2 * LRN_N3 * LRN_H);
+    L.w3t = take(2 * LRN_H * LRN_N3);
+    L.w2t = take(2 * LRN_H * LRN_H);
+    L.knots = take(sizeof(float2) * (size_t)(J - 1) * LRN_P);
+    L.err = take(sizeof(int));
+    L.gK = take(sizeof(double) * (size_t)LRN_P * J);
+    L.total = o;
+    return L;
+}
+
+void learned_free(vdw_ctx* c) {
+    cudaFree(c->d_lrn);
+    cudaFree(c->d_U);
+    c->d_lrn = nullptr;
+    c->d_U = nullptr;
+    c->d_gK = nullptr;
+    c->lrn_loaded = 0;
+}
+
+int learned_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s) {
+    if (!lrn_ready(c)) return VDW_ERR_STATE;
+    return run_any(c, n, grad, E, v, w, RUN_ENERGY, 0.0, nullptr, s);
+}
+
+}  // namespace vdw
+
+using namespace vdw;
+
+extern "C" {
+
+long long vdw_learned_param_count(int J) { return (long long)LRN_OFF_K + (long long)LRN_P * J; }
+
+int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], const float* params, void* stream) {
+    if (!c || !feat || !params || J < 2 || J > L_MAXJ || !(k_max > 0.0)) return VDW_ERR_ARG;
+    if (!c->planned) {
+        set_error("vdw_learned_load: plan the grid first");
+        return VDW_ERR_STATE;
+    }
+    if (!(feat[1] > 0.0) || !(feat[3] > 0.0) || !(feat[4] > 0.0)) return VDW_ERR_ARG;
+    const GridArgs& g = c->g;
+    const double PI_D = 3.14159265358979323846;
+    const double gmax = 2.0 * PI_D * std::sqrt(std::pow((g.N1 / 2) / c->L[0], 2) + std::pow((g.N2 / 2) / c->L[1], 2) +
+                                               std::pow((g.N3 / 2) / c->L[2], 2));
+    if (gmax > k_max) {
+        set_error("vdw_learned_load: largest |G| of the grid exceeds the knots' k_max");
+        return VDW_ERR_SIZE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->d_lrn || c->lrn_J != J) {
+        cudaFree(c->d_lrn);
+        c->d_lrn = nullptr;
+        const LrnLayout L = lrn_layout(g, J);
+        VDW_CUDA(cudaMalloc(&c->d_lrn, L.total));
+        VDW_CUDA(cudaMemset(c->d_lrn, 0, L.total));
+        unsigned char* b = static_cast<unsigned char*>(c->d_lrn);
+        LearnedArgs& la = c->la;
+        la.w1 = reinterpret_cast<float*>(b + L.w1);
+        la.b1 = reinterpret_cast<float*>(b + L.b1);
+        la.b2 = reinterpret_cast<float*>(b + L.b2);
+        la.b3 = reinterpret_cast<float*>(b + L.b3);
+        la.w2r = reinterpret_cast<float*>(b + L.w2r);
+        la.w3r = reinterpret_cast<float*>(b + L.w3r);
+        la.w2f = reinterpret_cast<uint16_t*>(b + L.w2f);
+        la.w3f = reinterpret_cast<uint16_t*>(b + L.w3f);
+        la.w3t = reinterpret_cast<uint16_t*>(b + L.w3t);
+        la.w2t = reinterpret_cast<uint16_t*>(b + L.w2t);
+        la.knots = reinterpret_cast<float2*>(b + L.knots);
+        la.err = reinterpret_cast<int*>(b + L.err);
+        c->d_gK = reinterpret_cast<double*>(b + L.gK);
+        c->lrn_J = J;
+    }
+    LearnedArgs& la = c->la;
+    la.J = J;
+    la.dk = (float)(k_max / (J - 1));
+    la.inv_dk = (float)((J - 1) / k_max);
+    la.mu1 = (float)feat[0];
+    la.inv_sig1 = (float)(1.0 / feat[1]);
+    la.mu2 = (float)feat[2];
+    la.inv_sig2 = (float)(1.0 / feat[3]);
+    la.eps2 = (float)(feat[4] * feat[4]);
+    c->lrn_kmax = k_max;
+    k_learned_prepare<<<16, 256, 0, s>>>(params, la);
+    VDW_CUDA(cudaGetLastError());
+    const int rc = configure_all(c);
+    if (rc) return rc;
+    c->lrn_loaded = 1;
+    return VDW_OK;
+}
+
+int vdw_learned_energy_potential(vdw_handle c, const float* n, const float* grad, double* E, float* v, float* w,
+                                 void* stream) {
+    if (!c || !n || !grad) return VDW_ERR_ARG;
+    if (!lrn_ready(c)) return VDW_ERR_STATE;
+    return run_any(c, n, grad, E, v, w, RUN_ENERGY, 0.0, nullptr, (cudaStream_t)stream);
+}
+
+int vdw_learned_param_grad(vdw_handle c, const float* n, const float* grad, double coef, double* g_params, double* E,
+                           void* stream) {
+    if (!c || !n || !grad || !g_params) return VDW_ERR_ARG;
+    if (!lrn_ready(c)) return VDW_ERR_STATE;
+    if (!c->d_U) VDW_CUDA(cudaMalloc(&c->d_U, sizeof(float) * LRN_M * (size_t)c->g.N));
+    return run_any(c, n, grad, E, nullptr, nullptr, RUN_GRAD, coef, g_params, (cudaStream_t)stream);
+}
+
+int vdw_learned_fit_grad(vdw_handle c, const float* n, const float* grad, const float* target, const float* weight,
+                         double coef, double* g_params, void* stream) {
+    if (!c || !n || !grad || !target || !weight || !g_params) return VDW_ERR_ARG;
+    if (!lrn_ready(c)) return VDW_ERR_STATE;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    VDW_CUDA(cudaFuncSetAttribute(k_learned_param_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pgrad()));
+    k_learned_param_grad<<<nsm, PG_THREADS, smem_pgrad(), (cudaStream_t)stream>>>(
+        n, grad, c->g.N, c->pp.n_min, c->la, target, weight, 1, (float)coef, g_params);
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
+int vdw_learned_channels(vdw_handle c, const float* n, const float* grad, float* w_out, void* stream) {
+    if (!c || !n || !grad || !w_out) return VDW_ERR_ARG;
+    if (!lrn_ready(c)) return VDW_ERR_STATE;
+    const size_t sm = sizeof(MlpShared) + 2 * sizeof(MlpWG);
+    VDW_CUDA(cudaFuncSetAttribute(k_learned_channels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = (c->g.N + 2 * L_TILE - 1) / (2 * L_TILE);
+    const int nb = (int)std::min<long long>(tiles, 2LL * nsm);
+    k_learned_channels<<<nb, L_THREADS, sm, (cudaStream_t)stream>>>(n, grad, c->g.N, c->pp.n_min, c->la, w_out);
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
+int vdw_learned_status(vdw_handle c, int* tc_error) {
+    if (!c || !tc_error) return VDW_ERR_ARG;
+    if (!c->lrn_loaded) return VDW_ERR_STATE;
+    VDW_CUDA(cudaMemcpy(tc_error, c->la.err, sizeof(int), cudaMemcpyDeviceToHost));
+    return VDW_OK;
+}
+
+int vdw_basis_weights(vdw_handle c, const float* n, const float* grad, float* p_out, void* stream) {
+    if (!c || !n || !grad || !p_out) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    const int nb = (int)std::min<long long>((c->g.N + 255) / 256, 4096);
+    k_basis_weights<<<nb, 256, 0, (cudaStream_t)stream>>>(n, grad, c->g.N, c->pp, p_out);
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
+int vdw_spectral_gradient(vdw_handle c, const float* f, float* grad, void* stream) {
+    if (!c || !f || !grad) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    const GridArgs& g = c->g;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = VDW_OK;
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) {
+        rc = set_smem(k_field_plane<180, 72>, smem_plane1(g), "k_field_plane");
+        if (!rc) rc = set_smem(k_plane_inv3<180, 72>, smem_plane1(g), "k_plane_inv3");
+        if (!rc) rc = set_smem(k_pencil_grad<180>, smem_pgrad_pencil(g), "k_pencil_grad");
+        if (!rc) spectral_gradient<180, 180, 72>(c, f, grad, s);
+    } else if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) {
+        rc = set_smem(k_field_plane<256, 96>, smem_plane1(g), "k_field_plane");
+        if (!rc) rc = set_smem(k_plane_inv3<256, 96>, smem_plane1(g), "k_plane_inv3");
+        if (!rc) rc = set_smem(k_pencil_grad<256>, smem_pgrad_pencil(g), "k_pencil_grad");
+        if (!rc) spectral_gradient<256, 256, 96>(c, f, grad, s);
+    } else {
+        rc = set_smem(k_field_plane<0, 0>, smem_plane1(g), "k_field_plane");
+        if (!rc) rc = set_smem(k_plane_inv3<0, 0>, smem_plane1(g), "k_plane_inv3");
+        if (!rc) rc = set_smem(k_pencil_grad<0>, smem_pgrad_pencil(g), "k_pencil_grad");
+        if (!rc) spectral_gradient<0, 0, 0>(c, f, grad, s);
+    }
+    if (rc) return rc;
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
+int vdw_adam_step(float* p, const double* g, float* m, float* v, long long count, double lr, double beta1,
+                  double beta2, double eps, int step, void* stream) {
+    if (!p || !g || !m || !v || count <= 0 || step < 1) return VDW_ERR_ARG;
+    const float bc1 = (float)(1.0 - std::pow(beta1, step)), bc2 = (float)(1.0 - std::pow(beta2, step));
+    const int nb = (int)std::min<long long>((count + 255) / 256, 1024);
+    k_adam<<<nb, 256, 0, (cudaStream_t)stream>>>(p, g, m, v, count, (float)lr, (float)beta1, (float)beta2,
+                                                 (float)eps, bc1, bc2);
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
+}  // extern "C"

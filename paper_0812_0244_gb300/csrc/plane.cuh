@@ -1,0 +1,107 @@
+// Shared pieces of the transform kernels: block reductions, twiddle loads,
+// dispatch between the compile-time and runtime line transforms, and the
+// forward / inverse transform of one y plane (N3 rows of N1 reals <-> N3 x Nh
+// half spectrum) held in shared memory.
+#pragma once
+#include "fft.cuh"
+
+namespace vdw {
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed order); result valid in thread 0.
+__device__ inline double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    return s;
+}
+
+__device__ __forceinline__ void load_twiddles(float2* dst, const float2* src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// line-transform dispatch: compile-time length when CN > 0
+// ---------------------------------------------------------------------------
+// rows of one plane (packed real pairs), one row per warp iteration
+template <int CN, bool INV>
+__device__ __forceinline__ void row_fft(float2* p, const LinePlan& pl, const float2* tw, int lane) {
+    if constexpr (CN > 0) ct_fft<CN, 1, INV>(p, 1, 0, tw, lane);
+    else line_fft<INV>(p, 1, pl, tw, lane);
+}
+
+// the Nh columns of a plane (element stride Nh), several columns per warp for short lines
+template <int CN, bool INV>
+__device__ __forceinline__ void columns_fft(float2* plane, int Nh, const LinePlan& pl, const float2* tw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if constexpr (CN > 0) {
+        constexpr int L = CN <= 72 ? 3 : (CN <= 128 ? 2 : 1);
+        const int full = (Nh / L) * L;
+        for (int col = warp * L; col < full; col += nw * L) ct_fft<CN, L, INV>(plane + col, Nh, 1, tw, lane);
+        for (int col = full + warp; col < Nh; col += nw) ct_fft<CN, 1, INV>(plane + col, Nh, 1, tw, lane);
+    } else {
+        for (int col = warp; col < Nh; col += nw) line_fft<INV>(plane + col, Nh, pl, tw, lane);
+    }
+}
+
+// contiguous lines of length N2 (pencils)
+template <int CN, bool INV>
+__device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, const LinePlan& pl, const float2* tw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int l = warp; l < nlines; l += nw) {
+        if constexpr (CN > 0) ct_fft<CN, 1, INV>(lines + l * N2, 1, 0, tw, lane);
+        else line_fft<INV>(lines + l * N2, 1, pl, tw, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plane helpers (one y plane, N3 rows of N1 reals <-> N3 x Nh half spectrum)
+// ---------------------------------------------------------------------------
+// Real rows 2j and 2j+1 share the complex row at offset j (2 Nh), as real and
+// imaginary parts; this is the float offset of the start of real row z.
+__device__ __forceinline__ int packed_row(int z, int Nh) { return 2 * ((z >> 1) * 2 * Nh) + (z & 1); }
+
+// Forward: packed real rows -> half spectrum (x R2C, then z C2C).
+template <int CN1, int CN3>
+__device__ void plane_forward(float2* plane, const GridArgs& g, const float2* tw1, const float2* tw3) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int row = warp; row < g.N3 / 2; row += nw) {
+        float2* p = plane + row * 2 * g.Nh;
+        row_fft<CN1, false>(p, g.p1, tw1, lane);
+        r2c_untangle(p, g.N1, lane);
+    }
+    __syncthreads();
+    columns_fft<CN3, false>(plane, g.Nh, g.p3, tw3);
+    __syncthreads();
+}
+
+// Inverse: half spectrum -> packed real rows (z C2C inverse, then x C2R), unscaled.
+template <int CN1, int CN3>
+__device__ void plane_inverse(float2* plane, const GridArgs& g, const float2* tw1, const float2* tw3) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    columns_fft<CN3, true>(plane, g.Nh, g.p3, tw3);
+    __syncthreads();
+    for (int row = warp; row < g.N3 / 2; row += nw) {
+        float2* p = plane + row * 2 * g.Nh;
+        c2r_tangle(p, g.N1, lane);
+        row_fft<CN1, true>(p, g.p1, tw1, lane);
+    }
+    __syncthreads();
+}
+
+constexpr int PLANE_THREADS = 256;  // threads of the plane kernels (P1, P5)
+
+}  // namespace vdw

@@ -1,0 +1,292 @@
+"""Training and evaluation of the learned reduced basis on the GPU.
+
+The learned model (C ABI: vdw_learned_*) replaces the Nq = 20 cardinal
+splines by 8 channels theta_m = n w_m(x) from a 2-64-64-8 SiLU network and a
+learned pair kernel K_mn(|G|) on 256 uniform knots.  Every computation of a
+training step runs in the library's kernels: the spectral gradient of the
+densities, the plain Nq = 20 targets, the learned energy and potential, the
+parameter gradients, the regression gradient used to initialise the network
+and the Adam update.  PyTorch only holds device memory.
+
+Initialisation: the network is fitted to the plain method's cardinal weights
+p_a(q) of an Nq = 8 logarithmic mesh, and K to that mesh's radial table at the
+knots, so the untrained model is close to the plain method with 8 channels.
+
+Loss per density (natoms atoms):
+    L = ((E - E*) / natoms / e0)^2 + beta sum_i n_i (v_i - v*_i)^2 / (sum_i n_i v0^2)
+with (E*, v*) from the plain Nq = 20 path, e0 = 0.1 meV per atom and v0 the
+density-weighted RMS of v* over the training set.  The potential term's
+gradient uses sum_i lam_i dv_i/dp = (1/dOmega) d/de [dE/dp (n + e lam)] at
+e = 0 with lam = n (v - v*) (v = dE/dn / dOmega, grad n = D n), evaluated by
+a central difference of two parameter gradients; the step makes the largest
+relative change of n equal to rel_step.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import synthetic as S
+from . import vdwnl
+
+HA_PER_MEV = 1.0 / 27211.386245988
+J_KNOTS = 256
+K_MAX = 30.0
+M = vdwnl.LEARNED_M
+H = vdwnl.LEARNED_H
+P = M * (M + 1) // 2
+OFF_K = 2 * H + H + H * H + H + M * H + M
+
+TRAINED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "trained", "learned_m8_tube.npz")
+
+
+def tube_config(seed, rng_seed=None):
+    """Seeded nanotube variant: outer wall shift U(0, 2.46 A), rotation U(0, 36 deg)."""
+    rng = np.random.default_rng(seed if rng_seed is None else rng_seed)
+    return dict(seed=int(seed), shift_ang=float(rng.uniform(0.0, 2.46)), rot_deg=float(rng.uniform(0.0, 36.0)))
+
+
+@dataclass
+class Sample:
+    n: object          # (N3, N2, N1) FP32 device tensor
+    g: object          # (3, N3, N2, N1) spectral gradient
+    E_ref: float       # plain Nq = 20 energy
+    v_ref: object      # plain Nq = 20 potential
+    natoms: int
+    cfg: dict = field(default_factory=dict)
+
+
+def make_samples(configs, shape, ctx20, device="cuda"):
+    """Densities on the device, their spectral gradients and the plain targets."""
+    import torch
+    out = []
+    for cfg in configs:
+        n64, L, na = S.tube_density_torch(cfg["seed"], shape=shape, shift_ang=cfg["shift_ang"],
+                                          rot_deg=cfg["rot_deg"], device=device)
+        n = n64.to(torch.float32).contiguous()
+        g = ctx20.spectral_gradient(n)
+        E, v, _ = ctx20.compute(n, g)
+        out.append(Sample(n, g, float(E[0]), v, na, cfg))
+    torch.cuda.synchronize()
+    return out, L
+
+
+def feature_stats(samples, eps=0.1, n_min=1e-12):
+    """Mean and spread of the two features over the training densities."""
+    import torch
+    f1s, f2s = [], []
+    for s in samples:
+        n = s.n.double().reshape(-1)
+        ok = n > n_min
+        g2 = (s.g.double().reshape(3, -1) ** 2).sum(0)
+        s2 = g2[ok] * n[ok] ** (-8.0 / 3.0)
+        f1s.append(torch.log(n[ok])[::7])
+        f2s.append((0.5 * torch.log(s2 + eps * eps))[::7])
+    f1 = torch.cat(f1s)
+    f2 = torch.cat(f2s)
+    return (float(f1.mean()), float(f1.std()), float(f2.mean()), float(f2.std()), eps)
+
+
+def init_params(seed, table8, device="cuda"):
+    """Random network (He init) and K from the Nq = 8 radial table at the knots."""
+    import torch
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0.0, 1.0, (H, 2))
+    W2 = rng.normal(0.0, np.sqrt(2.0 / H), (H, H))
+    W3 = rng.normal(0.0, np.sqrt(1.0 / H), (M, H))
+    b1 = rng.normal(0.0, 0.1, H)
+    b2 = np.zeros(H)
+    b3 = np.full(M, 1.0 / M)
+    kk = np.arange(J_KNOTS) * K_MAX / (J_KNOTS - 1)
+    kmesh = np.linspace(0.0, table8["k_max"], table8["phi_k"].shape[2])
+    K = np.zeros((P, J_KNOTS))
+    p = 0
+    for a in range(M):
+        for b in range(a, M):
+            K[p] = np.interp(kk, kmesh, table8["phi_k"][a, b])
+            p += 1
+    flat = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3, K.ravel()])
+    return torch.tensor(flat, dtype=torch.float32, device=device)
+
+
+class Adam:
+    """Adam state with one learning rate for the network and one for the knots."""
+
+    def __init__(self, params, lr_net, lr_knots):
+        import torch
+        self.p = params
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.t = 0
+        self.lr_net, self.lr_knots = lr_net, lr_knots
+
+    def step(self, grad):
+        self.t += 1
+        vdwnl.adam_step(self.p[:OFF_K], grad[:OFF_K], self.m[:OFF_K], self.v[:OFF_K], self.t, self.lr_net)
+        if self.lr_knots > 0:
+            vdwnl.adam_step(self.p[OFF_K:], grad[OFF_K:], self.m[OFF_K:], self.v[OFF_K:], self.t, self.lr_knots)
+
+
+def fit_network(ctx, ctx8, params, feat, samples, steps, lr=3e-3, log=None):
+    """Fit the channel weights to the Nq = 8 cardinal weights p_a(q) with
+    density weights n / sum n (initialisation)."""
+    import torch
+    opt = Adam(params, lr, 0.0)
+    targets = [ctx8.basis_weights(s.n, s.g) for s in samples]
+    weights = [(s.n / s.n.sum()).contiguous() for s in samples]
+    gp = torch.zeros(params.numel(), dtype=torch.float64, device=params.device)
+    for it in range(steps):
+        k = it % len(samples)
+        gp.zero_()
+        ctx.learned_fit_grad(samples[k].n, samples[k].g, targets[k], weights[k], gp)
+        opt.step(gp)
+        ctx.learned_load(params, J_KNOTS, K_MAX, feat)
+        if log is not None and (it % 200 == 0 or it == steps - 1):
+            w = ctx.learned_channels(samples[k].n, samples[k].g)
+            err = float((weights[k] * ((w - targets[k]) ** 2).sum(0)).sum())
+            log("fit %5d  weighted |w - p|^2 = %.3e" % (it, err))
+
+
+def energy_error_per_atom(ctx, samples, learned=True):
+    """(E - E*) / natoms in Hartree for each sample."""
+    import torch
+    out = []
+    for s in samples:
+        E = torch.empty(3, dtype=torch.float64, device=s.n.device)
+        if learned:
+            ctx.learned_energy_potential(s.n, s.g, E)
+        else:
+            ctx.energy_potential(s.n, s.g, E)
+        out.append((float(E[0]) - s.E_ref) / s.natoms)
+    return np.array(out)
+
+
+def potential_error(ctx, samples):
+    """Density-weighted RMS of v - v* for each sample (Hartree)."""
+    import torch
+    out = []
+    for s in samples:
+        E = torch.empty(3, dtype=torch.float64, device=s.n.device)
+        v = torch.empty_like(s.n)
+        ctx.learned_energy_potential(s.n, s.g, E, v)
+        out.append(float(torch.sqrt((s.n * (v - s.v_ref) ** 2).sum() / s.n.sum())))
+    return np.array(out)
+
+
+def train(ctx, params, feat, samples, epochs, lr_net=1e-3, lr_knots=1e-3, beta=1.0, rel_step=1e-2,
+          e0=0.1 * HA_PER_MEV, v0=None, seed=0, log=None):
+    """Adam on the loss of the module docstring; one density per step."""
+    import torch
+    if v0 is None:
+        num = sum(float((s.n * s.v_ref ** 2).sum()) for s in samples)
+        den = sum(float(s.n.sum()) for s in samples)
+        v0 = np.sqrt(num / den)
+    opt = Adam(params, lr_net, lr_knots)
+    rng = np.random.default_rng(seed)
+    gp = torch.zeros(params.numel(), dtype=torch.float64, device=params.device)
+    dOmega = ctx.dOmega
+    hist = []
+    for ep in range(epochs):
+        order = rng.permutation(len(samples))
+        eloss, vloss = 0.0, 0.0
+        for k in order:
+            s = samples[k]
+            E = torch.empty(3, dtype=torch.float64, device=s.n.device)
+            v = torch.empty_like(s.n)
+            ctx.learned_energy_potential(s.n, s.g, E, v)
+            dE = float(E[0]) - s.E_ref
+            sn = float(s.n.sum())
+            dv = v - s.v_ref
+            eloss += (dE / s.natoms / e0) ** 2
+            vloss += beta * float((s.n * dv * dv).sum()) / (sn * v0 * v0)
+            gp.zero_()
+            ctx.learned_param_grad(s.n, s.g, gp, coef=2.0 * dE / (s.natoms * e0) ** 2)
+            if beta > 0:
+                lam = (s.n * dv).contiguous()
+                rel = float((dv.abs()).max())
+                eps = rel_step / rel if rel > 0 else 0.0
+                if eps > 0:
+                    c = 2.0 * beta / (sn * v0 * v0) / dOmega / (2.0 * eps)
+                    for sign in (1.0, -1.0):
+                        m = (s.n + sign * eps * lam).contiguous()
+                        ctx.learned_param_grad(m, ctx.spectral_gradient(m), gp, coef=sign * c)
+            opt.step(gp)
+            ctx.learned_load(params, J_KNOTS, K_MAX, feat)
+        hist.append((eloss / len(samples), vloss / len(samples)))
+        if log is not None:
+            log("epoch %3d  energy term %.4e  potential term %.4e" % (ep, hist[-1][0], hist[-1][1]))
+    return hist
+
+
+def save(path, params, feat, meta):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez(path, params=params.detach().cpu().numpy(), feat=np.asarray(feat), J=J_KNOTS, k_max=K_MAX,
+             meta=json.dumps(meta))
+
+
+def load(path=TRAINED_PATH):
+    z = np.load(path, allow_pickle=False)
+    return dict(params=z["params"], feat=tuple(float(x) for x in z["feat"]), J=int(z["J"]), k_max=float(z["k_max"]),
+                meta=json.loads(str(z["meta"])))
+
+
+def run(n_train=200, n_test=50, shape=(72, 180, 180), fit_steps=2000, epochs=20, seed=0, out=TRAINED_PATH,
+        log=print):
+    """The full experiment: 200 training and 50 held-out tube densities
+    (seeds 1000-1249), initialisation, training, evaluation."""
+    import torch
+    t0 = time.time()
+    ctx20 = vdwnl.VdwNL(vdwnl.Params(Nq=20))
+    p8 = vdwnl.Params(Nq=8)
+    ctx8 = vdwnl.VdwNL(p8)
+    table8 = vdwnl.kernel_table(p8)
+    table8["k_max"] = p8.k_max
+    cfgs = [tube_config(1000 + i) for i in range(n_train + n_test)]
+    _, L, _ = S.tube_density_torch(cfgs[0]["seed"], shape=(8, 8, 8), device="cpu")
+    ctx20.plan(shape, L)
+    ctx8.plan(shape, L)
+    ctx = vdwnl.VdwNL(vdwnl.Params(Nq=20)).plan(shape, L)
+    train_s, _ = make_samples(cfgs[:n_train], shape, ctx20)
+    test_s, _ = make_samples(cfgs[n_train:], shape, ctx20)
+    log("densities and targets: %.1f s" % (time.time() - t0))
+    feat = feature_stats(train_s)
+    params = init_params(seed, table8)
+    ctx.learned_load(params, J_KNOTS, K_MAX, feat)
+    fit_network(ctx, ctx8, params, feat, train_s, fit_steps, log=log)
+    err8 = energy_error_per_atom(ctx8, test_s, learned=False)
+    err_init = energy_error_per_atom(ctx, test_s)
+    log("held-out |dE|/atom: plain Nq=8 %.4f meV, learned init %.4f meV" %
+        (np.abs(err8).mean() / HA_PER_MEV, np.abs(err_init).mean() / HA_PER_MEV))
+    hist = train(ctx, params, feat, train_s, epochs, log=log)
+    err_tr = energy_error_per_atom(ctx, test_s)
+    verr = potential_error(ctx, test_s)
+    status = ctx.learned_status()
+    res = dict(n_train=n_train, n_test=n_test, shape=list(shape), epochs=epochs, fit_steps=fit_steps,
+               mae_mev_plain8=float(np.abs(err8).mean() / HA_PER_MEV),
+               mae_mev_init=float(np.abs(err_init).mean() / HA_PER_MEV),
+               mae_mev_trained=float(np.abs(err_tr).mean() / HA_PER_MEV),
+               max_mev_trained=float(np.abs(err_tr).max() / HA_PER_MEV),
+               spread_mev_plain8=float((err8 - err8.mean()).std() / HA_PER_MEV),
+               spread_mev_trained=float((err_tr - err_tr.mean()).std() / HA_PER_MEV),
+               v_wrms_trained=float(verr.mean()), history=hist, tc_error=status,
+               seconds=time.time() - t0)
+    log(json.dumps({k: v for k, v in res.items() if k != "history"}))
+    if out:
+        save(out, params, feat, res)
+    return res, ctx, params, feat, test_s
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="train the learned reduced basis on tube densities")
+    ap.add_argument("--train", type=int, default=200)
+    ap.add_argument("--test", type=int, default=50)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--fit-steps", type=int, default=2000)
+    ap.add_argument("--out", default=TRAINED_PATH)
+    a = ap.parse_args()
+    run(a.train, a.test, fit_steps=a.fit_steps, epochs=a.epochs, out=a.out)

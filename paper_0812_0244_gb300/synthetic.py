@@ -66,6 +66,64 @@ def _gaussian_sum(shape, L, centers, amps, sigmas, floor, cut=8.0):
     return n, g
 
 
+def _gaussian_sum_torch(shape, L, centers, amps, sigmas, floor, device, cut=8.0):
+    """Density part of _gaussian_sum evaluated with torch on a device (FP64):
+    the same Gaussians, boxes and images, accumulated by index_put_."""
+    import torch
+    N3, N2, N1 = shape
+    L = np.asarray(L, np.float64)
+    h = L / np.array([N1, N2, N3], np.float64)
+    n = torch.full(tuple(shape), float(floor), dtype=torch.float64, device=device)
+    for c, A, s in zip(centers, amps, sigmas):
+        R = cut * s
+        idx, dis = [], []
+        for d, Nd in enumerate((N1, N2, N3)):
+            lo = int(np.floor((c[d] - R) / h[d]))
+            hi = int(np.ceil((c[d] + R) / h[d]))
+            ii = np.arange(lo, hi + 1)
+            if ii.size > Nd:
+                ii = np.arange(Nd)
+                x = ii * h[d] - c[d]
+                x = x - L[d] * np.round(x / L[d])
+            else:
+                x = ii * h[d] - c[d]
+            idx.append(torch.as_tensor(np.mod(ii, Nd), device=device))
+            dis.append(torch.as_tensor(x, dtype=torch.float64, device=device))
+        x, y, z = dis
+        r2 = x[None, None, :] ** 2 + y[None, :, None] ** 2 + z[:, None, None] ** 2
+        val = A * torch.exp(-r2 / (2.0 * s * s))
+        iz, iy, ix = torch.meshgrid(idx[2], idx[1], idx[0], indexing="ij")
+        n.index_put_((iz.reshape(-1), iy.reshape(-1), ix.reshape(-1)), val.reshape(-1), accumulate=True)
+    return n
+
+
+def tube_density_torch(seed=0, shape=(72, 180, 180), inner=5, outer=10, shift_ang=0.0, rot_deg=0.0,
+                       dr_in_ang=0.0, dr_out_ang=0.0, cell_ang=(25.0, 25.0, 9.84), floor=1e-6, device="cuda"):
+    """tube_density's density (same seeded draws) evaluated on a torch device;
+    returns (n as an FP64 tensor, L, natoms).  For generating many training
+    densities quickly; the gradient is left to the caller."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(cell_ang, np.float64) * BOHR_PER_ANG
+    R_in = 3.0 * A_CC * inner / (2.0 * np.pi) + dr_in_ang
+    R_out = 3.0 * A_CC * outer / (2.0 * np.pi) + dr_out_ang
+    n_periods = int(round(cell_ang[2] / T_ARM))
+    s_in = armchair_sites(inner, R_in, n_periods)
+    s_out = armchair_sites(outer, R_out, n_periods, np.deg2rad(rot_deg), shift_ang)
+    sites = np.concatenate([s_in, s_out]) * BOHR_PER_ANG
+    sites[:, 0] += 0.5 * L[0]
+    sites[:, 1] += 0.5 * L[1]
+    sites[:, 2] = np.mod(sites[:, 2], L[2])
+    centers, amps, sigmas = [], [], []
+    for c in sites:
+        w = rng.uniform(0.3, 0.7)
+        for q, s in ((4.0 * w, rng.uniform(0.4, 1.2)), (4.0 * (1.0 - w), rng.uniform(0.4, 1.2))):
+            centers.append(c)
+            amps.append(q / ((2.0 * np.pi) ** 1.5 * s ** 3))
+            sigmas.append(s)
+    n = _gaussian_sum_torch(shape, L, centers, amps, sigmas, floor, device)
+    return n, L, len(sites)
+
+
 def two_atom_density(seed=0, shape=(24, 24, 24), cell_ang=10.0, sep_ang=3.0, floor=1e-6):
     """Two three-Gaussian 'atoms' in a cubic cell (the small plain-method case)."""
     rng = np.random.default_rng(seed)

@@ -72,8 +72,13 @@ class Params:
 
 EXPORTS = ["vdw_params_default", "vdw_kernel_table", "vdw_create", "vdw_plan", "vdw_energy_potential",
            "vdw_energy_potential_host", "vdw_last_invalid_points", "vdw_profile_enable", "vdw_profile_read",
-           "vdw_delta_energy_noalloc", "vdw_workspace_bytes", "vdw_destroy",
-           "vdw_error_string", "vdw_last_error"]
+           "vdw_delta_energy_noalloc", "vdw_spectral_gradient", "vdw_learned_param_count", "vdw_learned_load",
+           "vdw_learned_energy_potential", "vdw_learned_param_grad", "vdw_learned_fit_grad",
+           "vdw_learned_channels", "vdw_learned_status", "vdw_basis_weights", "vdw_adam_step",
+           "vdw_workspace_bytes", "vdw_destroy", "vdw_error_string", "vdw_last_error"]
+
+LEARNED_M = 8
+LEARNED_H = 64
 
 _LIB = None
 
@@ -98,6 +103,17 @@ def lib():
     L.vdw_profile_enable.argtypes = [vp, ctypes.c_int]
     L.vdw_profile_read.argtypes = [vp, fp]
     L.vdw_delta_energy_noalloc.argtypes = [vp, vp, vp, ctypes.c_longlong, ctypes.c_double, vp, vp]
+    L.vdw_spectral_gradient.argtypes = [vp, vp, vp, vp]
+    L.vdw_learned_param_count.argtypes = [ctypes.c_int]
+    L.vdw_learned_load.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, vp, vp]
+    L.vdw_learned_energy_potential.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.vdw_learned_param_grad.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp]
+    L.vdw_learned_fit_grad.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp]
+    L.vdw_learned_channels.argtypes = [vp, vp, vp, vp, vp]
+    L.vdw_learned_status.argtypes = [vp, P(ctypes.c_int)]
+    L.vdw_basis_weights.argtypes = [vp, vp, vp, vp, vp]
+    L.vdw_adam_step.argtypes = [vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
     L.vdw_workspace_bytes.argtypes = [vp, P(ctypes.c_size_t)]
     L.vdw_destroy.argtypes = [vp]
     L.vdw_error_string.argtypes = [ctypes.c_int]
@@ -107,6 +123,7 @@ def lib():
     for name in EXPORTS:
         if name not in ("vdw_error_string", "vdw_last_error"):
             getattr(L, name).restype = ctypes.c_int
+    L.vdw_learned_param_count.restype = ctypes.c_longlong
     _LIB = L
     return L
 
@@ -131,6 +148,31 @@ def kernel_table(params: Params | None = None):
     _check(lib().vdw_kernel_table(ctypes.byref(p), _dptr(qm), _dptr(phik), _dptr(phi0), _dptr(cs)),
            "vdw_kernel_table")
     return dict(q_mesh=qm, phi_k=phik, phi0=float(phi0[0]), C_s=float(cs[0]))
+
+
+def learned_param_count(J):
+    """Length of the learned model's flat parameter vector for J knots."""
+    return int(lib().vdw_learned_param_count(int(J)))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _cuda_f32(t, shape=None):
+    import torch
+    assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    if shape is not None:
+        assert tuple(t.shape) == tuple(shape), (tuple(t.shape), shape)
+
+
+def adam_step(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """vdw_adam_step on device tensors: p, m, v FP32, g FP64 (same length)."""
+    import torch
+    assert p.numel() == g.numel() == m.numel() == v.numel()
+    assert g.dtype == torch.float64 and p.dtype == m.dtype == v.dtype == torch.float32
+    _check(lib().vdw_adam_step(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), float(lr), float(beta1),
+                               float(beta2), float(eps), int(step), _stream_handle(stream)), "vdw_adam_step")
 
 
 def _stream_handle(stream):
@@ -171,8 +213,9 @@ class VdwNL:
         """Enqueue vdw_energy_potential on device tensors; returns (E, v, w)."""
         import torch
         assert n.is_cuda and n.dtype == torch.float32 and n.is_contiguous() and tuple(n.shape) == self.shape
-        assert grad.is_cuda and grad.dtype == torch.float32 and grad.is_contiguous()
-        assert tuple(grad.shape) == (3,) + self.shape
+        if grad is not None:  # None: the library computes the spectral gradient
+            assert grad.is_cuda and grad.dtype == torch.float32 and grad.is_contiguous()
+            assert tuple(grad.shape) == (3,) + self.shape
         for t, shp in ((v, self.shape), (w, (3,) + self.shape)):
             if t is not None:
                 assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == shp
@@ -188,8 +231,91 @@ class VdwNL:
         import torch
         E = torch.empty(3, dtype=torch.float64, device=n.device)
         v = torch.empty_like(n) if want_v else None
-        w = torch.empty_like(grad) if want_w else None
+        w = torch.empty((3,) + tuple(n.shape), dtype=torch.float32, device=n.device) if want_w else None
         return self.energy_potential(n, grad, E, v, w, stream)
+
+    # ---- spectral gradient and the learned reduced basis -----------------
+    def spectral_gradient(self, f, out=None, stream=None):
+        """grad f = D f (spectral, Nyquist removed) into out (3, N3, N2, N1)."""
+        import torch
+        _cuda_f32(f, self.shape)
+        if out is None:
+            out = torch.empty((3,) + self.shape, dtype=torch.float32, device=f.device)
+        _cuda_f32(out, (3,) + self.shape)
+        _check(lib().vdw_spectral_gradient(self._h, _ptr(f), _ptr(out), _stream_handle(stream)),
+               "vdw_spectral_gradient")
+        return out
+
+    def learned_load(self, params, J, k_max, feat, stream=None):
+        """vdw_learned_load: params a device FP32 tensor of learned_param_count(J)
+        values, feat = (mu1, sig1, mu2, sig2, eps)."""
+        _cuda_f32(params)
+        assert params.numel() == learned_param_count(J)
+        f = np.ascontiguousarray(np.asarray(feat, dtype=np.float64).reshape(5))
+        self._lrn_params = params  # keep alive until the prepare kernel ran
+        _check(lib().vdw_learned_load(self._h, int(J), float(k_max), _dptr(f), _ptr(params), _stream_handle(stream)),
+               "vdw_learned_load")
+
+    def learned_energy_potential(self, n, grad, E=None, v=None, w=None, stream=None):
+        _cuda_f32(n, self.shape)
+        _cuda_f32(grad, (3,) + self.shape)
+        _check(lib().vdw_learned_energy_potential(self._h, _ptr(n), _ptr(grad), _ptr(E), _ptr(v), _ptr(w),
+                                                  _stream_handle(stream)), "vdw_learned_energy_potential")
+        return E, v, w
+
+    def learned_compute(self, n, grad, want_v=True, want_w=False, stream=None):
+        import torch
+        E = torch.empty(3, dtype=torch.float64, device=n.device)
+        v = torch.empty_like(n) if want_v else None
+        w = torch.empty_like(grad) if want_w else None
+        return self.learned_energy_potential(n, grad, E, v, w, stream)
+
+    def learned_param_grad(self, n, grad, g_params, coef=1.0, E=None, stream=None):
+        """g_params (FP64 device) += coef dE/dparams; E (FP64 [3]) optional."""
+        import torch
+        _cuda_f32(n, self.shape)
+        _cuda_f32(grad, (3,) + self.shape)
+        assert g_params.is_cuda and g_params.dtype == torch.float64
+        _check(lib().vdw_learned_param_grad(self._h, _ptr(n), _ptr(grad), float(coef), _ptr(g_params), _ptr(E),
+                                            _stream_handle(stream)), "vdw_learned_param_grad")
+        return g_params
+
+    def learned_fit_grad(self, n, grad, target, weight, g_params, coef=1.0, stream=None):
+        import torch
+        _cuda_f32(n, self.shape)
+        _cuda_f32(grad, (3,) + self.shape)
+        _cuda_f32(target, (LEARNED_M,) + self.shape)
+        _cuda_f32(weight, self.shape)
+        assert g_params.is_cuda and g_params.dtype == torch.float64
+        _check(lib().vdw_learned_fit_grad(self._h, _ptr(n), _ptr(grad), _ptr(target), _ptr(weight), float(coef),
+                                          _ptr(g_params), _stream_handle(stream)), "vdw_learned_fit_grad")
+        return g_params
+
+    def learned_channels(self, n, grad, out=None, stream=None):
+        import torch
+        _cuda_f32(n, self.shape)
+        _cuda_f32(grad, (3,) + self.shape)
+        if out is None:
+            out = torch.empty((LEARNED_M,) + self.shape, dtype=torch.float32, device=n.device)
+        _check(lib().vdw_learned_channels(self._h, _ptr(n), _ptr(grad), _ptr(out), _stream_handle(stream)),
+               "vdw_learned_channels")
+        return out
+
+    def learned_status(self):
+        e = ctypes.c_int()
+        _check(lib().vdw_learned_status(self._h, ctypes.byref(e)), "vdw_learned_status")
+        return e.value
+
+    def basis_weights(self, n, grad, out=None, stream=None):
+        """Plain cardinal weights p_a(q) (Nq, N3, N2, N1) for this context's mesh."""
+        import torch
+        _cuda_f32(n, self.shape)
+        _cuda_f32(grad, (3,) + self.shape)
+        if out is None:
+            out = torch.empty((self.params.Nq,) + self.shape, dtype=torch.float32, device=n.device)
+        _check(lib().vdw_basis_weights(self._h, _ptr(n), _ptr(grad), _ptr(out), _stream_handle(stream)),
+               "vdw_basis_weights")
+        return out
 
     def energy_potential_host(self, n, grad, E=None, v=None, stream=None):
         """vdw_energy_potential_host on numpy float32 arrays (pinned or pageable)."""

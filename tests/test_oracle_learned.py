@@ -193,3 +193,26 @@ def test_learned_loss_grad_matches_finite_differences(table, monkeypatch):
     # the potential term alone is not negligible in this check
     Gv = LO.loss_grad(n, L, mdl, table, ref["E"], ref["v"], 2, a=0.0, b=b)
     assert np.abs(Gv).max() > 1e-2 * np.abs(G).max()
+
+
+def test_fit_grad_matches_finite_differences(monkeypatch):
+    """Regression gradient of the channel weights against central differences."""
+    monkeypatch.setattr(LO, "bf16_round", lambda a: np.asarray(a, np.float64))
+    n, g, L = _tiny(21)
+    mdl = LO.random_model(22)
+    rng = np.random.default_rng(23)
+    target = rng.normal(0, 0.3, (mdl.M,) + n.shape)
+    weight = n / n.sum()
+    G = LO.fit_grad(n, g, mdl, target, weight, 1e-12)
+
+    def F(p):
+        m = mdl.with_flat(p)
+        ft = LO.features(n, g, m, 1e-12)
+        w = LO.mlp_forward(ft["x1"].ravel(), ft["x2"].ravel(), m)["w"]
+        return float(np.sum(weight.ravel() * np.sum((w - target.reshape(mdl.M, -1)) ** 2, axis=0)))
+
+    p0 = mdl.flat()
+    dirn = rng.normal(size=p0.size)
+    h = 1e-6
+    fd = (F(p0 + h * dirn) - F(p0 - h * dirn)) / (2 * h)
+    assert abs(fd - float(G @ dirn)) < 1e-6 * abs(fd)
