@@ -211,6 +211,48 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def learned_leg(ctx, n, g, E, v, flush, stream, K, E_plain, natoms, ms_plain, N):
+    """Time the learned 8-channel path (E and v) like the plain one and compare
+    its energy with the plain Nq = 20 energy of the same density."""
+    import torch
+    from paper_0812_0244_gb300 import learned as LR
+    from paper_0812_0244_gb300 import vdwnl
+    if os.path.exists(LR.TRAINED_PATH):
+        mdl = LR.load(LR.TRAINED_PATH)
+        params = torch.tensor(mdl["params"], dtype=torch.float32, device=n.device)
+        feat, base, kind = mdl["feat"], mdl["base"], "trained (%s)" % os.path.relpath(LR.TRAINED_PATH, ROOT)
+        J, kmax = mdl["J"], mdl["k_max"]
+    else:
+        p8 = vdwnl.Params(Nq=8, q_1=LR.Q1_8, lam=LR.LAM_8)
+        t8 = vdwnl.kernel_table(p8)
+        t8["k_max"] = p8.k_max
+        params = LR.init_params(0, t8, device=n.device)
+        feat, base, kind = (-8.0, 4.0, 2.0, 3.0, 0.1), (LR.Q1_8, LR.LAM_8), "untrained initialisation"
+        J, kmax = LR.J_KNOTS, LR.K_MAX
+    ctx.learned_load(params, J, kmax, feat, base)
+    for _ in range(3):
+        ctx.learned_energy_potential(n, g, E, v)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    for i in range(K):
+        flush.zero_()
+        starts[i].record(stream)
+        ctx.learned_energy_potential(n, g, E, v)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    ms_l = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K
+    El = float(E[0])
+    ctx.profile(True)
+    ctx.learned_energy_potential(n, g, E, v)
+    stages = {k: round(t, 4) for k, t in ctx.profile_read().items()}
+    ctx.profile(False)
+    return {"model": kind, "ms_per_step": ms_l, "value": N / (ms_l * 1e-3), "unit": UNIT,
+            "speedup_vs_plain_nq20": ms_plain / ms_l, "stages_ms": stages,
+            "energy_error_mev_per_atom_vs_plain_nq20": (El - E_plain) / natoms * 27211.386245988,
+            "tc_error": ctx.learned_status()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,6 +376,14 @@ def main():
     except Exception:
         cufft_ms = None
 
+    # learned reduced basis (M = 8 channels) on the same density: the trained
+    # model if one is stored in the package, else its initialisation
+    learned = None
+    try:
+        learned = learned_leg(ctx, n, g, E, v, flush, stream, min(K, 100), float(Eh[0]), int(d["natoms"]), ms, N)
+    except Exception as ex:  # reported, never silently replaced
+        learned = {"error": str(ex)[:200]}
+
     # end to end through the host-pointer entry point (pinned buffers)
     n_p = torch.from_numpy(n_h).pin_memory()
     g_p = torch.from_numpy(g_h).pin_memory()
@@ -382,6 +432,7 @@ def main():
                                         "alone, no pointwise work or contraction; reference only"
                                         % (params.Nq + 3, params.Nq + 1)},
             "clocks": clocks,
+            "learned_m8": learned,
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

@@ -197,8 +197,9 @@ int vdw_spectral_gradient(vdw_handle h, const float* f, float* grad, void* strea
  * cardinal-spline channels theta_a = n p_a(q) (Eq. fofx) and the radial table
  * phi_ab(k) (Eq. Eoffk) by VDW_LEARNED_M = 8 channels theta_m = n w_m whose
  * weights w come from a 2-64-64-8 SiLU network of two features, and by a
- * learned symmetric pair kernel K_mn(k), piecewise linear on J uniform knots
- * k_j = j k_max/(J-1).  The local correction Delta E of Eqs. (DEnl, Depsnl)
+ * learned symmetric pair kernel K_mn(k), Catmull-Rom cubic on J uniform knots
+ * k_j = j k_max/(J-1) (K even in k: the knot before k = 0 mirrors knot 1; the
+ * knot past the last is the linear extrapolation).  The local correction Delta E of Eqs. (DEnl, Depsnl)
  * is kept unchanged.  The contraction, transforms and assembly are those of
  * the plain method (Eqs. Eoffk, epsilon, epsofk, Vi) with M channels.
  *
@@ -218,14 +219,20 @@ int vdw_spectral_gradient(vdw_handle h, const float* f, float* grad, void* strea
 long long vdw_learned_param_count(int J);
 
 /* Load (or reload, e.g. after a training step) a model for the planned grid.
- *   J       knots, 2 <= J <= 256;  k_max  last knot (bohr^-1)
+ *   J       knots, 4 <= J <= 256;  k_max  last knot (bohr^-1)
  *   feat    host [5]: mu1, sig1, mu2, sig2, eps of the features
+ *   base_q1, base_lambda
+ *           0, 0: channel weights w = network output.  base_q1 > 0: w_m =
+ *           p_m(q) + network output m, with p_m the cardinal cubic splines
+ *           (Eq. fofx) on the 8-point mesh q_a = q_1 + (q_c - q_1)
+ *           (lambda^a - 1)/(lambda^7 - 1) and q of Eq. (Sat) clamped to it:
+ *           the network then learns a correction to the plain method's basis
  *   params  device [vdw_learned_param_count(J)] FP32; read by a kernel on
  *           stream, so it may be updated right after on the same stream.
  * The context derives its own copies (bf16 operands, knot intervals); the
  * first call allocates them (synchronous), later calls only enqueue. */
-int vdw_learned_load(vdw_handle h, int J, double k_max, const double feat[5], const float* params,
-                     void* stream);
+int vdw_learned_load(vdw_handle h, int J, double k_max, const double feat[5], double base_q1,
+                     double base_lambda, const float* params, void* stream);
 
 /* E and v of the learned model; arguments and outputs exactly as
  * vdw_energy_potential (E[1] holds the learned soft part, E[2] Delta E).

@@ -15,8 +15,16 @@ small network instead of the splines:
              z2 = W2 h1 + b2, h2 = bf16(silu(z2))
              w  = W3 h2 + b3                         (M outputs)
              weights W1, W2, W3 take bf16 values; biases and sums are wider
+  base       optional: w_m = p_m(q) + (network output m), with p_m the
+             cardinal cubic splines (Eq. fofx) on an M-point logarithmic
+             mesh (q_1, lambda, q_c) and q = h(q0) of Eq. (Sat) clamped to
+             that mesh (its derivative is zero where the clamp acts); the
+             network then learns a correction to the plain method's basis
   channels   theta_m = n w_m (zero where n <= n_min or n is not finite)
-  kernel     K_mn(k) piecewise linear on J uniform knots k_j = j dk,
+  kernel     K_mn(k) on J uniform knots k_j = j dk, interpolated by
+             Catmull-Rom cubics (value at k in [k_j, k_j+1] from the knots
+             j-1 .. j+2; K is even in k, so K_-1 = K_1, and the knot past
+             the last is the linear extrapolation 2 K_J-1 - K_J-2);
              symmetric, stored as the M(M+1)/2 pairs m <= n (row-major)
   energy     E = 1/2 Omega sum_G sum_mn theta_m(G)* K_mn(|G|) theta_n(G)
                  + Delta E   (the paper's local softening correction, Eqs.
@@ -87,6 +95,8 @@ class LearnedModel:
     mu2: float
     sig2: float
     eps: float      # s2 regulariser (same units as |grad n| / n^(4/3))
+    base_q1: float = 0.0    # base mesh (0: no base)
+    base_lam: float = 0.0
 
     @property
     def P(self):
@@ -113,7 +123,7 @@ class LearnedModel:
             o += k
         assert o == v.size
         return LearnedModel(self.M, *out, dk=self.dk, mu1=self.mu1, sig1=self.sig1, mu2=self.mu2,
-                            sig2=self.sig2, eps=self.eps)
+                            sig2=self.sig2, eps=self.eps, base_q1=self.base_q1, base_lam=self.base_lam)
 
 
 def pair_index(M):
@@ -121,8 +131,9 @@ def pair_index(M):
     return [(m, n) for m in range(M) for n in range(m, M)]
 
 
-def random_model(seed, M=8, J=256, k_max=30.0, mu=(-4.0, 1.0), sig=(3.0, 2.0), eps=0.1, kscale=1.0):
-    """Seeded model with He-style weights and smooth random pair kernels."""
+def random_model(seed, M=8, J=256, k_max=30.0, mu=(-4.0, 1.0), sig=(3.0, 2.0), eps=0.1, kscale=1.0, base=(0.0, 0.0)):
+    """Seeded model with He-style weights and smooth random pair kernels;
+    base = (q_1, lambda) of an optional spline base mesh."""
     rng = np.random.default_rng(seed)
     W1 = rng.normal(0.0, np.sqrt(2.0 / 2), (H, 2))
     W2 = rng.normal(0.0, np.sqrt(2.0 / H), (H, H))
@@ -137,7 +148,7 @@ def random_model(seed, M=8, J=256, k_max=30.0, mu=(-4.0, 1.0), sig=(3.0, 2.0), e
     for p in range(P):
         a, w = rng.uniform(-1.0, 1.0), rng.uniform(0.5, 3.0)
         K[p] = kscale * a * np.exp(-(k / w) ** 2)
-    return LearnedModel(M, W1, b1, W2, b2, W3, b3, K, dk, mu[0], sig[0], mu[1], sig[1], eps)
+    return LearnedModel(M, W1, b1, W2, b2, W3, b3, K, dk, mu[0], sig[0], mu[1], sig[1], eps, base[0], base[1])
 
 
 # --------------------------------------------------------------------------
@@ -159,6 +170,28 @@ def features(n, grad, mdl: LearnedModel, n_min):
     dx2_dn = -(4.0 / 3.0) * s2 / (ns * den * mdl.sig2)
     gx2 = ns ** (-8.0 / 3.0) / (den * mdl.sig2)
     return dict(ok=ok, n=np.where(ok, ns, 0.0), x1=x1, x2=x2, dx1_dn=dx1_dn, dx2_dn=dx2_dn, gx2=gx2)
+
+
+def base_basis(n, grad, mdl: LearnedModel, T: V.KernelTable):
+    """p_m(q), dp_m/dq on the base mesh and dq/dn, (dq/d|grad n|)/|grad n| with
+    the clamp's zero derivative; zeros everywhere when the model has no base."""
+    shape = np.shape(n)
+    if not mdl.base_q1 > 0:
+        z = np.zeros((mdl.M,) + shape)
+        return z, z.copy(), np.zeros(shape), np.zeros(shape)
+    p = T.p
+    qb = V.q_mesh(V.Params(Nq=mdl.M, q_1=mdl.base_q1, lam=mdl.base_lam, q_c=p.q_c))
+    Mb = V.cardinal_M(qb)
+    n = np.asarray(n, np.float64)
+    ok = np.isfinite(n) & (n > p.n_min)
+    ns = np.where(ok, n, 1.0)
+    gmod = np.where(ok, np.sqrt(np.sum(np.asarray(grad, np.float64) ** 2, axis=0)), 0.0)
+    q0, dq0_dn, dq0_dg = V.q0_unsaturated(ns, gmod)
+    q, hp = V.saturate(q0, p.q_c, p.m_c)
+    inside = (q >= qb[0]) & (q <= qb[-1])
+    P, dP = V.cardinal_eval(qb, Mb, np.clip(q, qb[0], qb[-1]))
+    okf = ok.astype(np.float64)
+    return P * okf, dP * okf, hp * dq0_dn * inside * okf, hp * dq0_dg * inside * okf
 
 
 def mlp_forward(x1, x2, mdl: LearnedModel):
@@ -192,17 +225,37 @@ def mlp_vjp_inputs(f, u, vjp_bf16=True):
 
 
 def knot_weights(kmod, dk, J):
-    """Piecewise-linear interpolation on knots j dk: interval j (clamped to the
-    last one) and position t, so K(k) = (1 - t) K[j] + t K[j + 1]."""
+    """Catmull-Rom interpolation on knots j dk: for each k the four knot
+    indices (j-1 .. j+2, j the interval clamped to the last one) and weights,
+    with the index -1 folded onto knot 1 (K even in k) and the index J
+    expressed through knots J-1 and J-2 (linear extrapolation).  Returns
+    (idx, wts), each of shape (6, m): some entries carry zero weight."""
     s = np.asarray(kmod, np.float64) / dk
     j = np.minimum(np.floor(s).astype(np.int64), J - 2)
-    return j, s - j
+    t = s - j
+    w = [(-t ** 3 + 2 * t ** 2 - t) / 2, (3 * t ** 3 - 5 * t ** 2 + 2) / 2,
+         (-3 * t ** 3 + 4 * t ** 2 + t) / 2, (t ** 3 - t ** 2) / 2]
+    idx, wts = [], []
+    for i, wi in zip(range(-1, 3), w):
+        k = j + i
+        lo = k < 0
+        hi = k > J - 1
+        idx.append(np.where(lo, 1, np.where(hi, J - 1, k)))
+        wts.append(np.where(hi, 2.0 * wi, wi))
+        idx.append(np.where(hi, J - 2, 0))
+        wts.append(np.where(hi, -wi, 0.0))
+    idx = np.array(idx)
+    wts = np.array(wts)
+    keep = np.array([0, 2, 4, 6, 7, 1])  # the six slots: 4 knots + the extrapolation's second term
+    return idx[keep], wts[keep]
 
 
 def kernel_eval(mdl: LearnedModel, kmod):
     """K_mn(|G|) for flat |G| values: array (M, M, m)."""
-    j, t = knot_weights(kmod, mdl.dk, mdl.J)
-    vals = (1.0 - t)[None, :] * mdl.K[:, j] + t[None, :] * mdl.K[:, j + 1]   # (P, m)
+    idx, wts = knot_weights(kmod, mdl.dk, mdl.J)
+    vals = np.zeros((mdl.P, idx.shape[1]))
+    for r in range(idx.shape[0]):
+        vals += wts[r][None, :] * mdl.K[:, idx[r]]
     out = np.empty((mdl.M, mdl.M, vals.shape[1]))
     for p, (m, n) in enumerate(pair_index(mdl.M)):
         out[m, n] = vals[p]
@@ -230,7 +283,8 @@ def energy_potential(n, grad, cell, mdl: LearnedModel, T: V.KernelTable, want_v=
     ok = ft["ok"]
     nn = ft["n"]
     f = mlp_forward(ft["x1"].ravel(), ft["x2"].ravel(), mdl)
-    w = f["w"].reshape((mdl.M,) + shape) * ok[None]
+    Pb, dPb, dq_dn_b, dq_dg_b = base_basis(n, grad, mdl, T)
+    w = (f["w"].reshape((mdl.M,) + shape) + Pb) * ok[None]
     theta = nn[None] * w
     th_hat = np.fft.fftn(theta, axes=(1, 2, 3)) / N
     g1, g2, g3 = V.g_vectors(shape, L)
@@ -252,9 +306,10 @@ def energy_potential(n, grad, cell, mdl: LearnedModel, T: V.KernelTable, want_v=
         q4 = np.where(pw["ok"], q ** 4, 1.0)
         dE_n = T.C_s * (pw["n"] / q ** 3 - 1.5 * pw["n"] ** 2 / q4 * pw["dq_dn"])
         dE_g = -1.5 * T.C_s * pw["n"] ** 2 / q4 * pw["dq_dg"]
-        v_loc = S0 + nn * (c[0] * ft["dx1_dn"] + c[1] * ft["dx2_dn"]) + dE_n
+        S1b = np.sum(u * dPb, axis=0)
+        v_loc = S0 + nn * (c[0] * ft["dx1_dn"] + c[1] * ft["dx2_dn"] + S1b * dq_dn_b) + dE_n
         v_loc = np.where(ok, v_loc, 0.0)
-        gg = np.where(ok, nn * c[1] * ft["gx2"] + dE_g, 0.0)
+        gg = np.where(ok, nn * (c[1] * ft["gx2"] + S1b * dq_dg_b) + dE_g, 0.0)
         wv = gg[None] * np.asarray(grad, np.float64)
         out.update(v=v_loc - V.spectral_divergence(wv, L), v_loc=v_loc, w=wv)
     if want_grad:
@@ -265,14 +320,14 @@ def energy_potential(n, grad, cell, mdl: LearnedModel, T: V.KernelTable, want_v=
 def param_grad(f, th_hat, kmod, u, nn, ok, mdl: LearnedModel, Omega, dOmega):
     """dE/dparams (flat, in the library's order) by backpropagation."""
     M = mdl.M
-    # kernel knots: dE/dK_p[j] = 1/2 Omega sum_G l_j(|G|) (2 - delta_mn) Re(conj th_m th_n)
-    j, t = knot_weights(kmod, mdl.dk, mdl.J)
+    # kernel knots: dE/dK_p[j] = 1/2 Omega sum_G w_j(|G|) (2 - delta_mn) Re(conj th_m th_n)
+    idx, wts = knot_weights(kmod, mdl.dk, mdl.J)
     th = th_hat.reshape(M, -1)
     gK = np.zeros_like(mdl.K)
     for p, (m, n) in enumerate(pair_index(M)):
         r = np.real(np.conj(th[m]) * th[n]) * (1.0 if m == n else 2.0) * 0.5 * Omega
-        gK[p] = np.bincount(j, weights=(1.0 - t) * r, minlength=mdl.J) + \
-            np.bincount(j + 1, weights=t * r, minlength=mdl.J)
+        for q in range(idx.shape[0]):
+            gK[p] += np.bincount(idx[q], weights=wts[q] * r, minlength=mdl.J)
     # network: cotangent of the outputs w_m at each point is dOmega n u_m
     do = (dOmega * nn * ok)[None] * u
     do = do.reshape(M, -1)

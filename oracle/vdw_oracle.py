@@ -574,8 +574,10 @@ def pointwise(n, grad, T: KernelTable):
     P, dP = cardinal_eval(T.qm, T.Mq, qcl)
     okf = ok.astype(np.float64)
     theta = ns * P * okf
-    dq_dn = hp * dq0_dn
-    dq_dg = hp * dq0_dg  # (dq/d|g|)/|g|
+    # q below the mesh is clamped to q_1: the clamped q does not vary there
+    inside = (q >= T.qm[0]).astype(np.float64)
+    dq_dn = hp * dq0_dn * inside
+    dq_dg = hp * dq0_dg * inside  # (dq/d|g|)/|g|
     return dict(ok=ok, n=ns * okf, q=qcl, P=P * okf, dP=dP * okf, theta=theta,
                 dq_dn=dq_dn * okf, dq_dg=dq_dg * okf)
 

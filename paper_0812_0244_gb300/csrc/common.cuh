@@ -75,8 +75,11 @@ struct LearnedArgs {
     const uint16_t* w2t;    // transposed-product operand W2^T [H][H]
     const float* w2r;       // W2 bf16-rounded values, row-major [H][H] (CUDA-core kernels)
     const float* w3r;       // W3 bf16-rounded values, row-major [M][H]
-    const float2* knots;    // [J-1][P]: (K[j], K[j+1] - K[j]) per interval
+    const float4* knots;    // [J-1][P]: cubic coefficients in t of the Catmull-Rom piece on interval j
     int* err;               // set when a tensor-core wait gives up
+    int base;               // channel weights = spline base + network (1) or network alone (0)
+    float bqm[LRN_M];       // base mesh
+    float bMq[LRN_M * LRN_M];  // bMq[m * M + k]: second derivative of base spline m at knot k
 };
 
 }  // namespace vdw

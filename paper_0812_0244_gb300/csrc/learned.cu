@@ -48,9 +48,12 @@ constexpr int L_MAXJ = 256;       // knots held in shared memory by the knot-gra
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+// SiLU and its derivative with the fast exponential and division: their
+// error (a few FP32 ulp) is far below the bf16 rounding the activations get.
+// The exponent is capped so that 1 + e stays inside __fdividef's range.
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.f + __expf(fminf(-z, 80.f))); }
 __device__ __forceinline__ float silu_prime(float z) {
-    const float s = 1.f / (1.f + __expf(-z));
+    const float s = __fdividef(1.f, 1.f + __expf(fminf(-z, 80.f)));
     return s * (1.f + z * (1.f - s));
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -96,19 +99,51 @@ __device__ __forceinline__ Feat features(float n, float gx, float gy, float gz, 
     return f;
 }
 
+// Cardinal cubic splines of the base mesh (Eq. fofx on an M-point mesh): p_m
+// and dp_m/dq at q clamped to the mesh; returns false where the clamp acts
+// (the derivative of the clamped basis is then zero).
+__device__ __forceinline__ bool base_weights(float q, const LearnedArgs& la, float* p, float* dp) {
+    const float lo = la.bqm[0], hi = la.bqm[LRN_M - 1];
+    const bool inside = (q >= lo) && (q <= hi);
+    const float qc = fminf(fmaxf(q, lo), hi);
+    int k = 0;  // knots <= q among the interior ones: interval in [0, M - 2]
+#pragma unroll
+    for (int i = 1; i < LRN_M - 1; ++i) k += (qc >= la.bqm[i]) ? 1 : 0;
+    const float x0 = la.bqm[k], x1 = la.bqm[k + 1], h = x1 - x0;
+    const float A = (x1 - qc) / h, B = 1.f - A;
+    const float h6 = h * h / 6.f;
+    const float cA = (A * A * A - A) * h6, cB = (B * B * B - B) * h6;
+    const float dA = -(3.f * A * A - 1.f) / 6.f * h, dB = (3.f * B * B - 1.f) / 6.f * h;
+#pragma unroll
+    for (int m = 0; m < LRN_M; ++m) {
+        const float Ma = la.bMq[m * LRN_M + k], Mb = la.bMq[m * LRN_M + k + 1];
+        const float ya = (m == k) ? 1.f : 0.f, yb = (m == k + 1) ? 1.f : 0.f;
+        p[m] = A * ya + B * yb + cA * Ma + cB * Mb;
+        dp[m] = (yb - ya) / h + dA * Ma + dB * Mb;
+    }
+    return inside;
+}
+
 // ---------------------------------------------------------------------------
 // shared memory of the tensor-core network
 // ---------------------------------------------------------------------------
+// forward operands and the small layers; the transposed operands of the
+// Jacobian-vector product follow only in the kernels that need them
 struct __align__(128) MlpShared {
     uint16_t w2f[LRN_H * LRN_H];
     uint16_t w3f[LRN_N3 * LRN_H];
-    uint16_t w3t[LRN_H * LRN_N3];
-    uint16_t w2t[LRN_H * LRN_H];
     float w1[2 * LRN_H], b1[LRN_H], b2[LRN_H], b3[LRN_M];
 };
+struct __align__(128) MlpShared2 {
+    uint16_t w3t[LRN_H * LRN_N3];
+    uint16_t w2t[LRN_H * LRN_H];
+};
+// One warpgroup's activation operand; the cotangent operand of the
+// Jacobian-vector product ([128][16]) reuses its first 4 KB once the forward
+// layers are done with it.
 struct __align__(128) MlpWG {
-    uint16_t A[L_TILE * LRN_H];   // activation operand of the tile
-    uint16_t U[L_TILE * LRN_N3];  // cotangent operand (Jacobian-vector product)
+    uint16_t A[L_TILE * LRN_H];
+    __device__ uint16_t* U() { return A; }
 };
 struct MlpCtl {
     uint64_t bar[2];
@@ -116,19 +151,19 @@ struct MlpCtl {
     int abort[2];  // per warpgroup: a wait gave up
 };
 
-__device__ void mlp_load_weights(MlpShared* S, const LearnedArgs& la, bool transposed) {
+__device__ void mlp_load_weights(MlpShared* S, MlpShared2* S2, const LearnedArgs& la) {
     const uint4* s1 = reinterpret_cast<const uint4*>(la.w2f);
     uint4* d1 = reinterpret_cast<uint4*>(S->w2f);
     for (int i = threadIdx.x; i < LRN_H * LRN_H / 8; i += blockDim.x) d1[i] = s1[i];
     const uint4* s2 = reinterpret_cast<const uint4*>(la.w3f);
     uint4* d2 = reinterpret_cast<uint4*>(S->w3f);
     for (int i = threadIdx.x; i < LRN_N3 * LRN_H / 8; i += blockDim.x) d2[i] = s2[i];
-    if (transposed) {
+    if (S2) {
         const uint4* s3 = reinterpret_cast<const uint4*>(la.w3t);
-        uint4* d3 = reinterpret_cast<uint4*>(S->w3t);
+        uint4* d3 = reinterpret_cast<uint4*>(S2->w3t);
         for (int i = threadIdx.x; i < LRN_H * LRN_N3 / 8; i += blockDim.x) d3[i] = s3[i];
         const uint4* s4 = reinterpret_cast<const uint4*>(la.w2t);
-        uint4* d4 = reinterpret_cast<uint4*>(S->w2t);
+        uint4* d4 = reinterpret_cast<uint4*>(S2->w2t);
         for (int i = threadIdx.x; i < LRN_H * LRN_H / 8; i += blockDim.x) d4[i] = s4[i];
     }
     for (int i = threadIdx.x; i < 2 * LRN_H; i += blockDim.x) S->w1[i] = la.w1[i];
@@ -227,15 +262,15 @@ __device__ bool mlp_forward(MlpShared* S, MlpWG* W, MlpCtl* ctl, int wg, int r, 
 // Jacobian-vector product of the network with the cotangent u (8 values):
 // c_j = sum_m u_m d w_m / d x_j.  Needs the forward's layer-2 accumulator in
 // columns [0, 64); uses [64, 128) and then [0, 64) again.
-__device__ bool mlp_vjp(MlpShared* S, MlpWG* W, MlpCtl* ctl, int wg, int r, uint32_t& phase, float x1, float x2,
-                        const float* u, float& c1, float& c2, int* err) {
+__device__ bool mlp_vjp(MlpShared* S, MlpShared2* S2, MlpWG* W, MlpCtl* ctl, int wg, int r, uint32_t& phase,
+                        float x1, float x2, const float* u, float& c1, float& c2, int* err) {
     float uu[16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) uu[m] = m < LRN_M ? u[m] : 0.f;
-    store8_bf16(W->U + tc::kmaj(r, 0, LRN_N3), uu);
-    store8_bf16(W->U + tc::kmaj(r, 8, LRN_N3), uu + 8);
+    store8_bf16(W->U() + tc::kmaj(r, 0, LRN_N3), uu);
+    store8_bf16(W->U() + tc::kmaj(r, 8, LRN_N3), uu + 8);
     // G2 = U W3 (tile x 64) into columns [64, 128)
-    if (!wg_mma(ctl, wg, r, phase, W->U, S->w3t, LRN_N3, LRN_H, 64, err)) return false;
+    if (!wg_mma(ctl, wg, r, phase, W->U(), S2->w3t, LRN_N3, LRN_H, 64, err)) return false;
 #pragma unroll
     for (int c = 0; c < LRN_H / 16; ++c) {
         float z[16], g[16];
@@ -247,7 +282,7 @@ __device__ bool mlp_vjp(MlpShared* S, MlpWG* W, MlpCtl* ctl, int wg, int r, uint
         store8_bf16(W->A + tc::kmaj(r, 16 * c + 8, LRN_H), g + 8);
     }
     // G1 = delta2 W2 (tile x 64) into columns [0, 64)
-    if (!wg_mma(ctl, wg, r, phase, W->A, S->w2t, LRN_H, LRN_H, 0, err)) return false;
+    if (!wg_mma(ctl, wg, r, phase, W->A, S2->w2t, LRN_H, LRN_H, 0, err)) return false;
     c1 = 0.f;
     c2 = 0.f;
 #pragma unroll
@@ -287,7 +322,7 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
     uint16_t* w3f = const_cast<uint16_t*>(la.w3f);
     uint16_t* w3t = const_cast<uint16_t*>(la.w3t);
     uint16_t* w2t = const_cast<uint16_t*>(la.w2t);
-    float2* kn = const_cast<float2*>(la.knots);
+    float4* kn = const_cast<float4*>(la.knots);
     const int t = threadIdx.x + blockIdx.x * blockDim.x, nt = blockDim.x * gridDim.x;
     auto bfu = [](float x) { return (uint16_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)); };
     for (int i = t; i < 2 * LRN_H; i += nt) w1[i] = bf16r(flat[LRN_OFF_W1 + i]);
@@ -310,11 +345,17 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
         w3f[tc::kmaj(m, j, LRN_H)] = bfu(x);
         w3t[tc::kmaj(j, m, LRN_N3)] = bfu(x);
     }
+    // Catmull-Rom piece on [k_j, k_j+1] from knots j-1 .. j+2: K is even in k
+    // (K_-1 = K_1) and continues linearly past the last knot
     const float* K = flat + LRN_OFF_K;
-    for (int i = t; i < (la.J - 1) * LRN_P; i += nt) {
+    const int J = la.J;
+    for (int i = t; i < (J - 1) * LRN_P; i += nt) {
         const int j = i / LRN_P, p = i % LRN_P;
-        const float k0 = K[p * la.J + j], k1 = K[p * la.J + j + 1];
-        kn[i] = make_float2(k0, k1 - k0);
+        const float* Kp = K + p * J;
+        const float P0 = Kp[j == 0 ? 1 : j - 1], P1 = Kp[j], P2 = Kp[j + 1];
+        const float P3 = j + 2 <= J - 1 ? Kp[j + 2] : 2.f * Kp[J - 1] - Kp[J - 2];
+        kn[i] = make_float4(P1, 0.5f * (P2 - P0), P0 - 2.5f * P1 + 2.f * P2 - 0.5f * P3,
+                            -0.5f * P0 + 1.5f * P1 - 1.5f * P2 + 0.5f * P3);
     }
 }
 
@@ -324,7 +365,7 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
 // Tile T (128 consecutive points of the plane, index i = z N1 + x) belongs to
 // block (T / 2) mod 8, warpgroup T mod 2.
 template <int CN1, int CN3>
-__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
+__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 2)
     k_learned_theta(const float* __restrict__ n, const float* __restrict__ grad, GridArgs g, PointParams P,
                     LearnedArgs la, const float2* __restrict__ tw, float2* __restrict__ spec,
                     double* __restrict__ epart, unsigned long long* __restrict__ invalid) {
@@ -344,7 +385,7 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
     MlpWG* W = Wb + wg;
     load_twiddles(tw1, tw, g.N1);
     load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
-    mlp_load_weights(S, la, false);
+    mlp_load_weights(S, nullptr, la);
     for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
     mlp_setup(&ctl);
     float* pf = reinterpret_cast<float*>(plane);
@@ -372,17 +413,23 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
         }
         const Feat f = features(ni, gx, gy, gz, la, P.n_min);
         const bool ok = in && f.ok;
+        float pb[LRN_M], dpb[LRN_M];
+#pragma unroll
+        for (int m = 0; m < LRN_M; ++m) pb[m] = 0.f;
         if (in) {
             bad += (!(ni >= 0.f) || !isfinite(ni)) ? 1u : 0u;
             const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
-            if (qp.k != K_INVALID) eacc += (double)(0.5f * P.C_s * ni * ni / (qp.q * qp.q * qp.q));
+            if (qp.k != K_INVALID) {
+                eacc += (double)(0.5f * P.C_s * ni * ni / (qp.q * qp.q * qp.q));
+                if (la.base) base_weights(qp.q, la, pb, dpb);
+            }
         }
         float o[LRN_M];
         if (!mlp_forward(S, W, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, la.err)) break;
         if (in) {
             const int off = packed_row(z, g.Nh) + 2 * x;
 #pragma unroll
-            for (int m = 0; m < LRN_M; ++m) rem[m][off] = ok ? ni * o[m] : 0.f;
+            for (int m = 0; m < LRN_M; ++m) rem[m][off] = ok ? ni * (o[m] + pb[m]) : 0.f;
         }
     }
     mlp_teardown(&ctl);
@@ -443,7 +490,10 @@ __global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ s
         const float s = sqrtf(G2) * la.inv_dk;
         const int j = min((int)s, la.J - 2);
         const float t = s - (float)j;
-        const float2* cf = la.knots + (long long)j * LRN_P;
+        const float4* cf = la.knots + (long long)j * LRN_P;
+        // Catmull-Rom weights of the knots j-1 .. j+2 (knot-gradient bins)
+        const float wm1 = 0.5f * t * (t * (2.f - t) - 1.f), w0 = 1.f + t * t * (1.5f * t - 2.5f);
+        const float w1 = 0.5f * t * (1.f + t * (4.f - 3.f * t)), w2 = 0.5f * t * t * (t - 1.f);
         const float2* pa = lines + cc * N2 + ya;
         const float2* pb = lines + cc * N2 + yb;
         float2 ua[NQ], ub[NQ];
@@ -460,8 +510,8 @@ __global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ s
             const float2 taa = pa[a * LS], tba = pb[a * LS];
 #pragma unroll
             for (int b = a; b < NQ; ++b, ++p) {
-                const float2 c = cf[p];
-                const float phi = fmaf(t, c.y, c.x);
+                const float4 c = cf[p];
+                const float phi = fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
                 const float2 tab = pa[b * LS], tbb = pb[b * LS];
                 ua[a].x = fmaf(phi, tab.x, ua[a].x);
                 ua[a].y = fmaf(phi, tab.y, ua[a].y);
@@ -478,8 +528,16 @@ __global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ s
                     float rr2 = taa.x * tab.x + taa.y * tab.y;
                     if (two) rr2 += tba.x * tbb.x + tba.y * tbb.y;
                     const float rv = halfOmega * wgt * (b != a ? 2.f : 1.f) * rr2;
-                    atomicAdd(&bins[p * la.J + j], (1.f - t) * rv);
-                    atomicAdd(&bins[p * la.J + j + 1], t * rv);
+                    float* bp = bins + p * la.J;
+                    atomicAdd(&bp[j == 0 ? 1 : j - 1], wm1 * rv);
+                    atomicAdd(&bp[j], w0 * rv);
+                    atomicAdd(&bp[j + 1], w1 * rv);
+                    if (j + 2 <= la.J - 1) {
+                        atomicAdd(&bp[j + 2], w2 * rv);
+                    } else {
+                        atomicAdd(&bp[la.J - 1], 2.f * w2 * rv);
+                        atomicAdd(&bp[la.J - 2], -w2 * rv);
+                    }
                 }
             }
         }
@@ -538,7 +596,8 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
     float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
     MlpShared* S = reinterpret_cast<MlpShared*>(smraw + plane_bytes(g.N3, g.Nh, g.N1));
-    MlpWG* Wb = reinterpret_cast<MlpWG*>(reinterpret_cast<unsigned char*>(S) + sizeof(MlpShared));
+    MlpShared2* S2 = reinterpret_cast<MlpShared2*>(reinterpret_cast<unsigned char*>(S) + sizeof(MlpShared));
+    MlpWG* Wb = reinterpret_cast<MlpWG*>(reinterpret_cast<unsigned char*>(S2) + sizeof(MlpShared2));
     float* gg_s = reinterpret_cast<float*>(Wb + 2);  // g of this block's tiles
     const int y = blockIdx.x;
     const int rank = (int)cluster.block_rank();
@@ -548,7 +607,7 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
     const long long N = g.N;
     load_twiddles(tw1, tw, g.N1);
     load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
-    if (mode != 2) mlp_load_weights(S, la, true);
+    if (mode != 2) mlp_load_weights(S, S2, la);
     for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
     // u_m of this block's channel
     const float2* src = spec + ((long long)rank * g.N2 + y) * g.ncols;
@@ -597,22 +656,32 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
         float o[LRN_M];
         if (!mlp_forward(S, W, &ctl, wg, r, phase, x1, x2, o, la.err)) break;
         float c1 = 0.f, c2 = 0.f;
-        if (!mlp_vjp(S, W, &ctl, wg, r, phase, x1, x2, u, c1, c2, la.err)) break;
+        if (!mlp_vjp(S, S2, W, &ctl, wg, r, phase, x1, x2, u, c1, c2, la.err)) break;
         float vl = 0.f, gg = 0.f;
         if (ok) {
-            float s0 = 0.f;
-#pragma unroll
-            for (int m = 0; m < LRN_M; ++m) s0 = fmaf(u[m], o[m], s0);
             const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
-            float dEn = 0.f, dEg = 0.f;
+            float dEn = 0.f, dEg = 0.f, bn = 0.f, bg = 0.f;
+            float pb[LRN_M], dpb[LRN_M];
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) pb[m] = dpb[m] = 0.f;
             if (qp.k != K_INVALID) {
                 const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
                 const float cn = 1.5f * P.C_s * ni * ni / q4;
                 dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
                 dEg = -cn * qp.dq_dg;
+                if (la.base && base_weights(q, la, pb, dpb)) {
+                    bn = qp.dq_dn;
+                    bg = qp.dq_dg;
+                }
             }
-            vl = s0 + ni * (c1 * f.dx1_dn + c2 * f.dx2_dn) + dEn;
-            gg = ni * c2 * f.gx2 + dEg;
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) {
+                s0 = fmaf(u[m], o[m] + pb[m], s0);
+                s1 = fmaf(u[m], dpb[m], s1);
+            }
+            vl = s0 + ni * (c1 * f.dx1_dn + c2 * f.dx2_dn + s1 * bn) + dEn;
+            gg = ni * (c2 * f.gx2 + s1 * bg) + dEg;
         }
         if (in) {
             if (v) v[gi] = vl;
@@ -654,14 +723,17 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(L_THREADS, 1) k_learned_channels(const float* __restrict__ n,
                                                                    const float* __restrict__ grad, long long N,
-                                                                   float n_min, LearnedArgs la,
+                                                                   PointParams P, LearnedArgs la,
                                                                    float* __restrict__ wout) {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ MlpCtl ctl;
+    __shared__ float qm[MAX_NQ];
+    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
+    const float n_min = P.n_min;
     MlpShared* S = reinterpret_cast<MlpShared*>(smraw);
     MlpWG* Wb = reinterpret_cast<MlpWG*>(smraw + sizeof(MlpShared));
     const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
-    mlp_load_weights(S, la, false);
+    mlp_load_weights(S, nullptr, la);
     mlp_setup(&ctl);
     uint32_t phase = 0;
     const long long ntiles = (N + L_TILE - 1) / L_TILE;
@@ -677,11 +749,18 @@ __global__ void __launch_bounds__(L_THREADS, 1) k_learned_channels(const float* 
         }
         const Feat f = features(ni, gx, gy, gz, la, n_min);
         const bool ok = in && f.ok;
+        float pb[LRN_M], dpb[LRN_M];
+#pragma unroll
+        for (int m = 0; m < LRN_M; ++m) pb[m] = 0.f;
+        if (ok && la.base) {
+            const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
+            if (qp.k != K_INVALID) base_weights(qp.q, la, pb, dpb);
+        }
         float o[LRN_M];
         if (!mlp_forward(S, Wb + wg, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, la.err)) break;
         if (in)
 #pragma unroll
-            for (int m = 0; m < LRN_M; ++m) wout[m * N + i] = ok ? o[m] : 0.f;
+            for (int m = 0; m < LRN_M; ++m) wout[m * N + i] = ok ? o[m] + pb[m] : 0.f;
     }
     mlp_teardown(&ctl);
 }
@@ -966,7 +1045,8 @@ size_t smem_cluster(const GridArgs& g, bool assemble) {
     const int np = g.N1 * g.N3;
     const int ntiles = (np + L_TILE - 1) / L_TILE;
     const size_t gg = assemble ? sizeof(float) * (size_t)((ntiles + 2 * L_CTAS - 1) / (2 * L_CTAS)) * 2 * L_TILE : 0;
-    return plane_bytes(g.N3, g.Nh, g.N1) + sizeof(MlpShared) + 2 * sizeof(MlpWG) + gg;
+    return plane_bytes(g.N3, g.Nh, g.N1) + sizeof(MlpShared) + (assemble ? sizeof(MlpShared2) : 0) +
+           2 * sizeof(MlpWG) + gg;
 }
 int contract_cols(const GridArgs& g) {
     int C = 8;
@@ -1059,9 +1139,22 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     const int nb0 = g.N2 * L_CTAS;
     double* ep = lrn_epart(c);
     const double Omega = c->L[0] * c->L[1] * c->L[2];
+    // stage marks for vdw_profile_read: 1 network + channel planes, 2 pencils,
+    // 3 energy, 4 assembly, 6 divergence (stages 0 and 5 are not separate)
+    auto mark = [&](int stage) {
+        if (c->prof) {
+            cudaEventRecord(c->ev[stage + 1], s);
+            c->ev_done[stage] = 1;
+        }
+    };
+    if (c->prof) {
+        for (int i = 0; i < VDW_NSTAGES; ++i) c->ev_done[i] = 0;
+        cudaEventRecord(c->ev[0], s);
+    }
     VDW_CUDA(cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long), s));
     k_learned_theta<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, false), s>>>(
         n, grad, g, P, la, c->d_tw, c->d_spec, ep, c->d_invalid);
+    mark(1);
     const bool want_pot = (v != nullptr) || (w != nullptr);
     if (kind == RUN_GRAD) {
         VDW_CUDA(cudaMemsetAsync(c->d_gK, 0, sizeof(double) * LRN_P * c->lrn_J, s));
@@ -1071,9 +1164,11 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
         k_learned_contract<CN2, false><<<nb_c, 256, smem_contract(g, C, false, c->lrn_J), s>>>(
             c->d_spec, g, la, c->d_tw, ep + nb0, C, want_pot ? 1 : 0, nullptr, 0.f);
     }
+    mark(2);
     if (E) {
         int rc = pipeline_energy_final(c, ep, nb0, nb_c, E, s);
         if (rc) return rc;
+        mark(3);
     }
     if (kind == RUN_GRAD) {
         k_learned_assemble<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, true), s>>>(
@@ -1089,9 +1184,11 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
         const int mode = (w != nullptr) ? 0 : 1;
         k_learned_assemble<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, true), s>>>(
             c->d_spec, n, grad, g, P, la, c->d_tw, v, w, c->d_wspec, nullptr, mode);
+        mark(4);
         if (mode == 1) {
             int rc = pipeline_divergence(c, v, s);
             if (rc) return rc;
+            mark(6);
         }
     }
     VDW_CUDA(cudaGetLastError());
@@ -1152,7 +1249,7 @@ static LrnLayout lrn_layout(const GridArgs& g, int J) {
     L.w3f = take(2 * LRN_N3 * LRN_H);
     L.w3t = take(2 * LRN_H * LRN_N3);
     L.w2t = take(2 * LRN_H * LRN_H);
-    L.knots = take(sizeof(float2) * (size_t)(J - 1) * LRN_P);
+    L.knots = take(sizeof(float4) * (size_t)(J - 1) * LRN_P);
     L.err = take(sizeof(int));
     L.gK = take(sizeof(double) * (size_t)LRN_P * J);
     L.total = o;
@@ -1181,8 +1278,10 @@ extern "C" {
 
 long long vdw_learned_param_count(int J) { return (long long)LRN_OFF_K + (long long)LRN_P * J; }
 
-int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], const float* params, void* stream) {
-    if (!c || !feat || !params || J < 2 || J > L_MAXJ || !(k_max > 0.0)) return VDW_ERR_ARG;
+int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], double base_q1, double base_lambda,
+                     const float* params, void* stream) {
+    if (!c || !feat || !params || J < 4 || J > L_MAXJ || !(k_max > 0.0)) return VDW_ERR_ARG;
+    if (base_q1 > 0.0 && !(base_q1 < c->p.q_c && base_lambda > 0.0 && base_lambda != 1.0)) return VDW_ERR_ARG;
     if (!c->planned) {
         set_error("vdw_learned_load: plan the grid first");
         return VDW_ERR_STATE;
@@ -1215,7 +1314,7 @@ int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], co
         la.w3f = reinterpret_cast<uint16_t*>(b + L.w3f);
         la.w3t = reinterpret_cast<uint16_t*>(b + L.w3t);
         la.w2t = reinterpret_cast<uint16_t*>(b + L.w2t);
-        la.knots = reinterpret_cast<float2*>(b + L.knots);
+        la.knots = reinterpret_cast<float4*>(b + L.knots);
         la.err = reinterpret_cast<int*>(b + L.err);
         c->d_gK = reinterpret_cast<double*>(b + L.gK);
         c->lrn_J = J;
@@ -1230,6 +1329,33 @@ int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], co
     la.inv_sig2 = (float)(1.0 / feat[3]);
     la.eps2 = (float)(feat[4] * feat[4]);
     c->lrn_kmax = k_max;
+    la.base = base_q1 > 0.0 ? 1 : 0;
+    if (la.base) {
+        // base mesh q_a = q_1 + (q_c - q_1)(lambda^a - 1)/(lambda^(M-1) - 1) and its
+        // cardinal natural splines (second derivatives by the tridiagonal solve)
+        double qb[LRN_M], Mb[LRN_M][LRN_M];
+        const double den = std::pow(base_lambda, LRN_M - 1) - 1.0;
+        for (int a = 0; a < LRN_M; ++a)
+            qb[a] = base_q1 + (c->p.q_c - base_q1) * (std::pow(base_lambda, a) - 1.0) / den;
+        for (int a = 0; a < LRN_M; ++a) {
+            double cp[LRN_M], dd[LRN_M];
+            for (int i = 0; i < LRN_M; ++i) Mb[a][i] = 0.0;
+            for (int i = 1; i <= LRN_M - 2; ++i) {
+                const double h0 = qb[i] - qb[i - 1], h1 = qb[i + 1] - qb[i];
+                const double y0 = (i - 1 == a), y1 = (i == a), y2 = (i + 1 == a);
+                const double rhs = 6.0 * ((y2 - y1) / h1 - (y1 - y0) / h0);
+                const double lo = (i > 1) ? h0 : 0.0;
+                const double dn = 2.0 * (h0 + h1) - (i > 1 ? lo * cp[i - 1] : 0.0);
+                cp[i] = h1 / dn;
+                dd[i] = (rhs - (i > 1 ? lo * dd[i - 1] : 0.0)) / dn;
+            }
+            for (int i = LRN_M - 2; i >= 1; --i) Mb[a][i] = dd[i] - (i < LRN_M - 2 ? cp[i] * Mb[a][i + 1] : 0.0);
+        }
+        for (int a = 0; a < LRN_M; ++a) {
+            la.bqm[a] = (float)qb[a];
+            for (int k = 0; k < LRN_M; ++k) la.bMq[a * LRN_M + k] = (float)Mb[a][k];
+        }
+    }
     k_learned_prepare<<<16, 256, 0, s>>>(params, la);
     VDW_CUDA(cudaGetLastError());
     const int rc = configure_all(c);
@@ -1277,7 +1403,7 @@ int vdw_learned_channels(vdw_handle c, const float* n, const float* grad, float*
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long tiles = (c->g.N + 2 * L_TILE - 1) / (2 * L_TILE);
     const int nb = (int)std::min<long long>(tiles, 2LL * nsm);
-    k_learned_channels<<<nb, L_THREADS, sm, (cudaStream_t)stream>>>(n, grad, c->g.N, c->pp.n_min, c->la, w_out);
+    k_learned_channels<<<nb, L_THREADS, sm, (cudaStream_t)stream>>>(n, grad, c->g.N, c->pp, c->la, w_out);
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
 }

@@ -61,6 +61,8 @@ __device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz,
         h = -P.q_c * expm1f(-S);
         hp = expf(-S) * dS;
     }
+    // below the mesh q is clamped to q_1 and no longer varies with n, grad n
+    if (h < qm[0]) hp = 0.f;
     float q = fminf(fmaxf(h, qm[0]), qm[P.Nq - 1]);
     // interval: number of knots <= q, minus one, in [0, Nq-2]
     int lo = 0, hi = P.Nq - 1;  // invariant: qm[lo] <= q (or lo = 0), answer in [lo, hi)

@@ -105,7 +105,7 @@ def lib():
     L.vdw_delta_energy_noalloc.argtypes = [vp, vp, vp, ctypes.c_longlong, ctypes.c_double, vp, vp]
     L.vdw_spectral_gradient.argtypes = [vp, vp, vp, vp]
     L.vdw_learned_param_count.argtypes = [ctypes.c_int]
-    L.vdw_learned_load.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, vp, vp]
+    L.vdw_learned_load.argtypes = [vp, ctypes.c_int, ctypes.c_double, dp, ctypes.c_double, ctypes.c_double, vp, vp]
     L.vdw_learned_energy_potential.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.vdw_learned_param_grad.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp, vp]
     L.vdw_learned_fit_grad.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp]
@@ -246,15 +246,16 @@ class VdwNL:
                "vdw_spectral_gradient")
         return out
 
-    def learned_load(self, params, J, k_max, feat, stream=None):
+    def learned_load(self, params, J, k_max, feat, base=(0.0, 0.0), stream=None):
         """vdw_learned_load: params a device FP32 tensor of learned_param_count(J)
-        values, feat = (mu1, sig1, mu2, sig2, eps)."""
+        values, feat = (mu1, sig1, mu2, sig2, eps), base = (q_1, lambda) of the
+        optional spline base mesh ((0, 0): none)."""
         _cuda_f32(params)
         assert params.numel() == learned_param_count(J)
         f = np.ascontiguousarray(np.asarray(feat, dtype=np.float64).reshape(5))
         self._lrn_params = params  # keep alive until the prepare kernel ran
-        _check(lib().vdw_learned_load(self._h, int(J), float(k_max), _dptr(f), _ptr(params), _stream_handle(stream)),
-               "vdw_learned_load")
+        _check(lib().vdw_learned_load(self._h, int(J), float(k_max), _dptr(f), float(base[0]), float(base[1]),
+                                      _ptr(params), _stream_handle(stream)), "vdw_learned_load")
 
     def learned_energy_potential(self, n, grad, E=None, v=None, w=None, stream=None):
         _cuda_f32(n, self.shape)

@@ -34,9 +34,9 @@ def f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
 
 
-def model_for(n, grad, seed, kscale=1e-3):
+def model_for(n, grad, seed, kscale=1e-3, base=(0.0, 0.0)):
     """A seeded random model whose features are standardised on this density."""
-    mdl = LO.random_model(seed, J=J, k_max=KMAX, kscale=kscale)
+    mdl = LO.random_model(seed, J=J, k_max=KMAX, kscale=kscale, base=base)
     ok = n > 1e-12
     s2 = np.sum(grad ** 2, axis=0)[ok] * n[ok] ** (-8.0 / 3.0)
     f1 = np.log(n[ok])
@@ -50,27 +50,33 @@ def gpu_ctx(torch, shape, L, mdl):
     from paper_0812_0244_gb300 import vdwnl
     ctx = vdwnl.VdwNL(vdwnl.Params()).plan(shape, L)
     params = torch.tensor(f32(mdl.flat()), device="cuda")
-    ctx.learned_load(params, J, KMAX, (mdl.mu1, mdl.sig1, mdl.mu2, mdl.sig2, mdl.eps))
+    ctx.learned_load(params, J, KMAX, (mdl.mu1, mdl.sig1, mdl.mu2, mdl.sig2, mdl.eps), (mdl.base_q1, mdl.base_lam))
     return ctx, params
+
+
+BASE = (0.6, 1.45)
 
 
 def cases():
     d = S.two_atom_density(3, shape=(24, 24, 24))
-    yield "two_atom_24", f32(d["n"]), f32(d["grad"]), d["L"]
+    yield "two_atom_24", f32(d["n"]), f32(d["grad"]), d["L"], (0.0, 0.0)
+    yield "two_atom_24_base", f32(d["n"]), f32(d["grad"]), d["L"], BASE
     d = S.two_atom_density(4, shape=(36, 30, 20))
-    yield "two_atom_36x30x20", f32(d["n"]), f32(d["grad"]), d["L"]
+    yield "two_atom_36x30x20_base", f32(d["n"]), f32(d["grad"]), d["L"], BASE
 
 
 @pytest.mark.parametrize("case", list(cases()), ids=lambda c: c[0])
 def test_channels_match_oracle(torch_cuda, table, case):
     torch = torch_cuda
-    _, n, g, L = case
-    mdl = model_for(n.astype(np.float64), g.astype(np.float64), 31)
+    _, n, g, L, base = case
+    mdl = model_for(n.astype(np.float64), g.astype(np.float64), 31, base=base)
     ctx, _ = gpu_ctx(torch, n.shape, L, mdl)
     w = ctx.learned_channels(torch.tensor(n, device="cuda"), torch.tensor(g, device="cuda")).cpu().numpy()
     assert ctx.learned_status() == 0
-    ft = LO.features(n.astype(np.float64), g.astype(np.float64), mdl, 1e-12)
-    ref = LO.mlp_forward(ft["x1"].ravel(), ft["x2"].ravel(), mdl)["w"].reshape(w.shape) * ft["ok"][None]
+    n64, g64 = n.astype(np.float64), g.astype(np.float64)
+    ft = LO.features(n64, g64, mdl, 1e-12)
+    ref = LO.mlp_forward(ft["x1"].ravel(), ft["x2"].ravel(), mdl)["w"].reshape(w.shape)
+    ref = (ref + LO.base_basis(n64, g64, mdl, table)[0]) * ft["ok"][None]
     err = np.abs(w - ref)
     scale = np.abs(ref).max()
     assert np.median(err) < 1e-5 * scale
@@ -81,9 +87,9 @@ def test_channels_match_oracle(torch_cuda, table, case):
 @pytest.mark.parametrize("case", list(cases()), ids=lambda c: c[0])
 def test_energy_and_potential_match_oracle(torch_cuda, table, case):
     torch = torch_cuda
-    _, n, g, L = case
+    _, n, g, L, base = case
     n64, g64 = n.astype(np.float64), g.astype(np.float64)
-    mdl = model_for(n64, g64, 32)
+    mdl = model_for(n64, g64, 32, base=base)
     ctx, _ = gpu_ctx(torch, n.shape, L, mdl)
     E, v, _ = ctx.learned_compute(torch.tensor(n, device="cuda"), torch.tensor(g, device="cuda"))
     E = E.cpu().numpy()
@@ -205,7 +211,7 @@ def test_learned_full_tube_matches_oracle(torch_cuda, table):
     d = S.tube_density(1, shift_ang=0.7, rot_deg=12.0)
     n, g, L = f32(d["n"]), f32(d["grad"]), d["L"]
     n64, g64 = n.astype(np.float64), g.astype(np.float64)
-    mdl = model_for(n64, g64, 36)
+    mdl = model_for(n64, g64, 36, base=BASE)
     ctx, _ = gpu_ctx(torch, n.shape, L, mdl)
     E, v, _ = ctx.learned_compute(torch.tensor(n, device="cuda"), torch.tensor(g, device="cuda"))
     E = E.cpu().numpy()

@@ -64,17 +64,41 @@ def test_mlp_forward_matches_torch_linear_silu():
     np.testing.assert_allclose(f["w"].T, w.numpy(), rtol=1e-12, atol=1e-12)
 
 
-def test_knot_interpolation_reproduces_linear_functions():
+def test_knot_interpolation_catmull_rom():
+    """The knot interpolation passes through the knots, reproduces quadratics
+    away from the ends (Catmull-Rom is exact for polynomials of degree <= 2
+    on uniform knots), continues an even function evenly through k = 0 and a
+    linear one linearly past the last knot."""
     mdl = LO.random_model(4, M=3, J=32, k_max=10.0)
     kj = np.arange(mdl.J) * mdl.dk
-    alpha = np.linspace(-1, 1, mdl.P)
-    beta = np.linspace(0.3, -0.2, mdl.P)
-    mdl.K = alpha[:, None] + beta[:, None] * kj[None]
-    k = np.random.default_rng(2).uniform(0, 10.0, 500)
+    a0 = np.linspace(-1, 1, mdl.P)
+    a1 = np.linspace(0.3, -0.2, mdl.P)
+    a2 = np.linspace(0.05, 0.1, mdl.P)
+    rng = np.random.default_rng(2)
+    # through the knots
+    mdl.K = rng.normal(size=(mdl.P, mdl.J))
+    Kk = LO.kernel_eval(mdl, kj)
+    for p, (m, n) in enumerate(LO.pair_index(mdl.M)):
+        np.testing.assert_allclose(Kk[m, n], mdl.K[p], atol=1e-14)
+        np.testing.assert_array_equal(Kk[m, n], Kk[n, m])
+    # quadratics on the interior intervals
+    mdl.K = a0[:, None] + a1[:, None] * kj[None] + a2[:, None] * kj[None] ** 2
+    k = rng.uniform(kj[1], kj[-2], 500)
     Kk = LO.kernel_eval(mdl, k)
     for p, (m, n) in enumerate(LO.pair_index(mdl.M)):
-        np.testing.assert_allclose(Kk[m, n], alpha[p] + beta[p] * k, rtol=0, atol=1e-13)
-        np.testing.assert_array_equal(Kk[m, n], Kk[n, m])
+        np.testing.assert_allclose(Kk[m, n], a0[p] + a1[p] * k + a2[p] * k ** 2, atol=1e-12)
+    # even quadratic through k = 0 (the mirrored knot K_-1 = K_1)
+    mdl.K = a0[:, None] + a2[:, None] * kj[None] ** 2
+    k = rng.uniform(0.0, kj[1], 200)
+    Kk = LO.kernel_eval(mdl, k)
+    for p, (m, n) in enumerate(LO.pair_index(mdl.M)):
+        np.testing.assert_allclose(Kk[m, n], a0[p] + a2[p] * k ** 2, atol=1e-12)
+    # linear past the last interval's far knot
+    mdl.K = a0[:, None] + a1[:, None] * kj[None]
+    k = rng.uniform(kj[-2], kj[-1], 200)
+    Kk = LO.kernel_eval(mdl, k)
+    for p, (m, n) in enumerate(LO.pair_index(mdl.M)):
+        np.testing.assert_allclose(Kk[m, n], a0[p] + a1[p] * k, atol=1e-12)
 
 
 def test_learned_energy_equals_real_space_double_sum(table):
@@ -115,12 +139,14 @@ def _tiny(seed=7, shape=(10, 8, 12), L=(9.0, 8.0, 10.0)):
     return n, O.spectral_gradient(n, L), L
 
 
-def test_learned_potential_matches_finite_differences(table, monkeypatch):
-    """v (exact Jacobian-vector product) = dE/dn_i / dOmega with grad n = D n.
-    The activations' bf16 rounding makes E piecewise constant in n, so this
-    pin runs with it off; the bf16 product is then compared with the exact one."""
+@pytest.mark.parametrize("base", [(0.0, 0.0), (0.6, 1.45)], ids=["network", "spline_base"])
+def test_learned_potential_matches_finite_differences(table, monkeypatch, base):
+    """v (exact Jacobian-vector product) = dE/dn_i / dOmega with grad n = D n,
+    with and without the spline base.  The activations' bf16 rounding makes E
+    piecewise constant in n, so this pin runs with it off; the bf16 product is
+    then compared with the exact one."""
     n, g, L = _tiny()
-    mdl = LO.random_model(6)
+    mdl = LO.random_model(6, base=base)
     rb = LO.energy_potential(n, g, L, mdl, table, vjp_bf16=True)
     monkeypatch.setattr(LO, "bf16_round", lambda a: np.asarray(a, np.float64))
     r = LO.energy_potential(n, g, L, mdl, table, vjp_bf16=False)
@@ -216,3 +242,20 @@ def test_fit_grad_matches_finite_differences(monkeypatch):
     h = 1e-6
     fd = (F(p0 + h * dirn) - F(p0 - h * dirn)) / (2 * h)
     assert abs(fd - float(G @ dirn)) < 1e-6 * abs(fd)
+
+
+def test_spline_base_reproduces_plain_method_basis(table):
+    """With the network's output switched off (W3 = 0, b3 = 0) and an M-point
+    base mesh, the channels are the plain method's cardinal weights on that
+    mesh: theta_m = n p_m(q) (Eq. fofx), against the plain oracle's pointwise
+    evaluation with an M-point table."""
+    n, g, L = _tiny(31)
+    mdl = LO.random_model(32, base=(0.6, 1.45))
+    mdl.W3[:] = 0.0
+    mdl.b3[:] = 0.0
+    r = LO.energy_potential(n, g, L, mdl, table, want_v=False)
+    p8 = O.Params(Nq=8, q_1=0.6, lam=1.45)
+    qm = O.q_mesh(p8)
+    T8 = O.KernelTable(p=p8, qm=qm, Mq=O.cardinal_M(qm), phi0=0.0, C_s=table.C_s, k=None, phik=None)
+    pw = O.pointwise(n, g, T8)
+    np.testing.assert_allclose(r["theta"], pw["theta"], rtol=1e-12, atol=1e-15)
