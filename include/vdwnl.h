@@ -272,6 +272,12 @@ int vdw_basis_weights(vdw_handle h, const float* n, const float* grad, float* p_
 int vdw_adam_step(float* p, const double* g, float* m, float* v, long long count, double lr, double beta1,
                   double beta2, double eps, int step, void* stream);
 
+/* *gave_up = 1 if, since vdw_plan, a bounded wait inside a kernel (an
+ * asynchronous copy or a tensor-core completion) ran out and the kernel
+ * carried on without it, so results may be wrong; else 0.  Every such wait
+ * polls a bounded number of times instead of spinning forever.  Synchronous. */
+int vdw_wait_status(vdw_handle h, int* gave_up);
+
 /* Bytes of device memory the context holds. */
 int vdw_workspace_bytes(vdw_handle h, size_t* bytes);
 

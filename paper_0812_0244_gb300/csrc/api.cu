@@ -47,6 +47,10 @@ static void free_plan(vdw_ctx* c) {
     c->d_E = nullptr;
     cudaFree(c->d_gtmp);
     c->d_gtmp = nullptr;
+    cudaFree(c->d_gg);
+    cudaFree(c->d_flags);
+    c->d_gg = nullptr;
+    c->d_flags = nullptr;
     learned_free(c);
     c->planned = 0;
 }
@@ -174,6 +178,9 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     VDW_CUDA(cudaMalloc(&c->d_k, g.N));
     VDW_CUDA(cudaMalloc(&c->d_epart, sizeof(double) * (c->nb_point + c->nb_pencil)));
     VDW_CUDA(cudaMalloc(&c->d_invalid, sizeof(unsigned long long)));
+    VDW_CUDA(cudaMalloc(&c->d_gg, sizeof(float) * (size_t)g.N));
+    VDW_CUDA(cudaMalloc(&c->d_flags, sizeof(int)));
+    VDW_CUDA(cudaMemset(c->d_flags, 0, sizeof(int)));
     VDW_CUDA(cudaMemset(c->d_invalid, 0, sizeof(unsigned long long)));
     if (c->acc_global) VDW_CUDA(cudaMalloc(&c->d_acc, sizeof(float) * 2 * 4 * g.N));
     rc = pipeline_make_twiddles(c);
@@ -183,7 +190,8 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     const int npairs = Nq * (Nq + 1) / 2;
     c->bytes = sizeof(float4) * (size_t)(c->p.Nk - 1) * npairs + sizeof(float2) * (n1 + n2 + n3) +
                sizeof(float2) * (spec_n + 3 * (size_t)n2 * g.ncols) + 5 * (size_t)g.N +
-               sizeof(double) * (c->nb_point + c->nb_pencil) + (c->acc_global ? 32 * (size_t)g.N : 0);
+               sizeof(double) * (c->nb_point + c->nb_pencil) + (c->acc_global ? 32 * (size_t)g.N : 0) +
+               4 * (size_t)g.N + sizeof(int);
     c->planned = 1;
     return VDW_OK;
 }
@@ -257,6 +265,16 @@ int vdw_profile_read(vdw_handle c, float* ms) {
         VDW_CUDA(cudaEventElapsedTime(&ms[i], c->ev[prev], c->ev[i + 1]));
         prev = i + 1;
     }
+    return VDW_OK;
+}
+
+int vdw_wait_status(vdw_handle c, int* gave_up) {
+    if (!c || !gave_up) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    int f = 0, l = 0;
+    VDW_CUDA(cudaMemcpy(&f, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (c->lrn_loaded) VDW_CUDA(cudaMemcpy(&l, c->la.err, sizeof(int), cudaMemcpyDeviceToHost));
+    *gave_up = (f || l) ? 1 : 0;
     return VDW_OK;
 }
 

@@ -107,6 +107,9 @@ struct vdw_ctx {
     int pencil_cols;            // columns per pencil block
     int acc_global;             // assembly accumulators in global memory
     int tk_smem;                // assembly keeps the plane's (t, k) in shared memory
+    int asm_dbuf;               // assembly double-buffers its planes (bulk asynchronous copies)
+    float* d_gg;                // [N] g of w = g grad n (assembly -> w plane transforms)
+    int* d_flags;               // [1] set when a bounded wait in a kernel gave up
     float* d_acc;               // [4][2N] their scratch (only when acc_global)
     // buffers of the host-pointer entry point (allocated on first use)
     float* d_in;                // [4N]

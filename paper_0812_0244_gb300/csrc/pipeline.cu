@@ -217,31 +217,68 @@ __global__ void __launch_bounds__(CONTRACT_THREADS, 1) k_pencil_contract(float2*
 // fields a = r, r + ASM_CTAS, ... and accumulates S0 = sum_a u_a p_a and
 // S1 = sum_a u_a p_a' over its fields; after a cluster barrier, block r sums
 // the partials of every block for the rows z = r (mod ASM_CTAS) through
-// distributed shared memory and finishes those points (v_loc, g); after a
-// second barrier, blocks 0..2 each gather g for the whole plane and transform
-// one component of w = g grad n.
-// mode 0: v_loc to v (if v), w to w_out; mode 1: v_loc to v, w(G) to wspec.
+// distributed shared memory and finishes those points: v_loc, and g with
+// w = g grad n.
+// With dbuf the spectrum plane of the next field arrives by a bulk
+// asynchronous copy (completion counted on an mbarrier) into a second buffer
+// while the current one is transformed and accumulated.
+// mode 0: v_loc to v (if v), w to w_out; mode 1: v_loc to v, g to g_out (the
+// plane transforms of w follow in k_w_planes).
 constexpr int ASM_CTAS = 4;
 constexpr int ASM_THREADS = 384;
+
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+}
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global memory into this block's shared memory, counted on bar.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+}
+// Bounded wait for the phase of the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int i = 0; i < (1 << 20); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 template <int CN1, int CN3>
 __global__ void __cluster_dims__(1, ASM_CTAS, 1) __launch_bounds__(ASM_THREADS, 1)
     k_assemble(const float2* __restrict__ spec, const float* __restrict__ n, const float* __restrict__ grad,
                const float* __restrict__ tk, const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
                const float2* __restrict__ tw, float* __restrict__ v, float* __restrict__ w_out,
-               float2* __restrict__ wspec, int mode, float* __restrict__ acc_global, int tk_smem) {
+               float* __restrict__ g_out, int mode, float* __restrict__ acc_global, int tk_smem, int dbuf,
+               int* __restrict__ wait_err) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ float2 sm[];
     __shared__ SplineSmem sp;
+    __shared__ uint64_t lbar[2];
     const int np = g.N1 * g.N3;
+    const int pe = g.N3 * g.Nh;  // complex values of a plane (ncols)
     const int y = blockIdx.x;
     const int rank = (int)cluster.block_rank();  // = blockIdx.y
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float2* plane = sm;
-    float2* tw1 = plane + g.N3 * g.Nh;
+    float2* plane0 = sm;
+    float2* plane1 = dbuf ? plane0 + pe : plane0;
+    float2* tw1 = plane0 + (dbuf ? 2 : 1) * pe;
     float2* tw3 = tw1 + g.N1;
-    // per-point partial sums of this block: shared memory when the plane leaves
+    // per-point partial sums of this block: shared memory when the planes leave
     // room for them, otherwise this block's slice of a global scratch buffer
     float* after = reinterpret_cast<float*>(tw3 + g.N3);
     float* S0 = acc_global ? acc_global + ((long long)y * ASM_CTAS + rank) * 2 * np : after;
@@ -251,6 +288,14 @@ __global__ void __cluster_dims__(1, ASM_CTAS, 1) __launch_bounds__(ASM_THREADS, 
     // once instead of once per field
     float* t_s = after;
     uint8_t* k_s = reinterpret_cast<uint8_t*>(t_s + np);
+    const uint32_t pbytes = (uint32_t)(sizeof(float2) * (size_t)pe);
+    if (threadIdx.x == 0 && dbuf) {
+        mbar_init1(&lbar[0]);
+        mbar_init1(&lbar[1]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && dbuf && rank < P.Nq)
+        bulk_load(plane0, spec + ((long long)rank * g.N2 + y) * g.ncols, pbytes, &lbar[0]);
     load_spline_smem(&sp, P);
     load_twiddles(tw1, tw, g.N1);
     load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
@@ -264,13 +309,26 @@ __global__ void __cluster_dims__(1, ASM_CTAS, 1) __launch_bounds__(ASM_THREADS, 
             }
         }
     }
-    const float* pf = reinterpret_cast<const float*>(plane);
-    for (int a = rank; a < P.Nq; a += ASM_CTAS) {
-        const float2* src = spec + ((long long)a * g.N2 + y) * g.ncols;
-        __syncthreads();
-        for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
-        __syncthreads();
+    int it = 0;
+    for (int a = rank; a < P.Nq; a += ASM_CTAS, ++it) {
+        float2* plane = (it & 1) ? plane1 : plane0;
+        if (dbuf) {
+            __syncthreads();  // the other buffer is free (and the setup above is done)
+            if (threadIdx.x == 0 && a + ASM_CTAS < P.Nq)
+                bulk_load((it & 1) ? plane0 : plane1, spec + ((long long)(a + ASM_CTAS) * g.N2 + y) * g.ncols,
+                          pbytes, &lbar[(it + 1) & 1]);
+            if (!mbar_wait_parity(&lbar[it & 1], (uint32_t)(it >> 1) & 1u)) {
+                atomicExch(wait_err, 1);
+                mbar_wait_parity(&lbar[it & 1], (uint32_t)(it >> 1) & 1u);
+            }
+        } else {
+            const float2* src = spec + ((long long)a * g.N2 + y) * g.ncols;
+            __syncthreads();
+            for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
+            __syncthreads();
+        }
         plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
+        const float* pf = reinterpret_cast<const float*>(plane);
         for (int z = warp; z < g.N3; z += nw) {
             const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
             const float* srow = pf + packed_row(z, g.Nh);
@@ -320,30 +378,40 @@ __global__ void __cluster_dims__(1, ASM_CTAS, 1) __launch_bounds__(ASM_THREADS, 
                 w_out[N + gi] = gg * gy;
                 w_out[2 * N + gi] = gg * gz;
             }
-            // g for this block's rows replaces its own S0 partials: other
-            // blocks read only their own rows of S0, which are untouched
-            S0[i] = gg;
+            if (mode == 1) g_out[gi] = gg;
         }
-    }
-    __threadfence_block();
-    cluster.sync();
-    if (mode == 1 && rank < 3) {
-        const int c = rank;
-        float* pw = reinterpret_cast<float*>(plane);
-        __syncthreads();
-        for (int z = warp; z < g.N3; z += nw) {
-            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-            const float* gsrc = S0r[z % ASM_CTAS] + z * g.N1;
-            float* dst = pw + packed_row(z, g.Nh);
-            for (int x = lane; x < g.N1; x += 32) dst[2 * x] = gsrc[x] * grad[c * N + row + x];
-        }
-        __syncthreads();
-        plane_forward<CN1, CN3>(plane, g, tw1, tw3);
-        float2* dst = wspec + ((long long)c * g.N2 + y) * g.ncols;
-        for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
     }
     // keep this block's shared memory alive until every block is done reading it
     cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
+// P3b: forward plane transforms of the three components of w = g grad n
+// ---------------------------------------------------------------------------
+template <int CN1, int CN3>
+__global__ void __launch_bounds__(PLANE_THREADS, 2) k_w_planes(const float* __restrict__ gfield,
+                                                                const float* __restrict__ grad, GridArgs g,
+                                                                const float2* __restrict__ tw,
+                                                                float2* __restrict__ wspec) {
+    extern __shared__ float2 sm[];
+    float2* plane = sm;
+    float2* tw1 = plane + g.N3 * g.Nh;
+    float2* tw3 = tw1 + g.N1;
+    const int y = blockIdx.x, c = blockIdx.y;
+    load_twiddles(tw1, tw, g.N1);
+    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    float* pf = reinterpret_cast<float*>(plane);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float* gc = grad + c * g.N;
+    for (int z = warp; z < g.N3; z += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+        float* dst = pf + packed_row(z, g.Nh);
+        for (int x = lane; x < g.N1; x += 32) dst[2 * x] = gfield[row + x] * gc[row + x];
+    }
+    __syncthreads();
+    plane_forward<CN1, CN3>(plane, g, tw1, tw3);
+    float2* dst = wspec + ((long long)c * g.N2 + y) * g.ncols;
+    for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -468,8 +536,8 @@ int make_line_plan(int n, LinePlan* lp) {
 }
 
 static size_t smem_plane(const GridArgs& g) { return sizeof(float2) * ((size_t)g.N3 * g.Nh + g.N1 + g.N3); }
-static size_t smem_assemble(const GridArgs& g, bool acc_in_smem, bool tk_in_smem) {
-    return sizeof(float2) * ((size_t)g.N3 * g.Nh + g.N1 + g.N3) +
+static size_t smem_assemble(const GridArgs& g, bool acc_in_smem, bool tk_in_smem, bool dbuf) {
+    return sizeof(float2) * ((size_t)(dbuf ? 2 : 1) * g.N3 * g.Nh + g.N1 + g.N3) +
            (acc_in_smem ? sizeof(float) * 2 * (size_t)g.N1 * g.N3 : 0) + (tk_in_smem ? 5 * (size_t)g.N1 * g.N3 : 0);
 }
 static size_t smem_pencil(const GridArgs& g, int nq, int C) { return sizeof(float2) * ((size_t)nq * C * g.N2 + g.N2); }
@@ -493,9 +561,12 @@ int pipeline_plan_check(vdw_ctx* c, size_t* sp, size_t* spen, size_t* sa, size_t
     c->pencil_cols = C;
     *sp = smem_plane(g);
     *spen = smem_pencil_run(g, nq, C);
-    c->acc_global = smem_assemble(g, true, false) > SMEM_MAX;
-    c->tk_smem = smem_assemble(g, !c->acc_global, true) <= SMEM_MAX;
-    *sa = smem_assemble(g, !c->acc_global, c->tk_smem);
+    // assembly: double-buffered planes if at all possible, then the partial
+    // sums in shared memory, then the (t, k) cache
+    c->asm_dbuf = smem_assemble(g, false, false, true) <= SMEM_MAX;
+    c->acc_global = smem_assemble(g, true, false, c->asm_dbuf) > SMEM_MAX;
+    c->tk_smem = smem_assemble(g, !c->acc_global, true, c->asm_dbuf) <= SMEM_MAX;
+    *sa = smem_assemble(g, !c->acc_global, c->tk_smem, c->asm_dbuf);
     *sd = smem_pencil_run(g, 3, DIV_COLS);
     if (*sp > SMEM_MAX || *spen > SMEM_MAX || *sa > SMEM_MAX || *sd > SMEM_MAX) return VDW_ERR_SIZE;
     return VDW_OK;
@@ -568,11 +639,13 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
         mark(3);
     }
     if (want_pot) {
-        const size_t sa = smem_assemble(g, !c->acc_global, c->tk_smem);
+        const size_t sa = smem_assemble(g, !c->acc_global, c->tk_smem, c->asm_dbuf);
         const int mode = (w != nullptr) ? 0 : 1;
-        k_assemble<CN1, CN3><<<dim3(g.N2, ASM_CTAS), ASM_THREADS, sa, s>>>(c->d_spec, n, grad, c->d_t, c->d_k, g, P,
-                                                                   c->d_tw, v, w, c->d_wspec, mode,
-                                                                   c->acc_global ? c->d_acc : nullptr, c->tk_smem);
+        k_assemble<CN1, CN3><<<dim3(g.N2, ASM_CTAS), ASM_THREADS, sa, s>>>(
+            c->d_spec, n, grad, c->d_t, c->d_k, g, P, c->d_tw, v, w, c->d_gg, mode, c->acc_global ? c->d_acc : nullptr,
+            c->tk_smem, c->asm_dbuf, c->d_flags);
+        if (mode == 1)
+            k_w_planes<CN1, CN3><<<dim3(g.N2, 3), PLANE_THREADS, sp, s>>>(c->d_gg, grad, g, c->d_tw, c->d_wspec);
         mark(4);
         if (mode == 1) {
             const size_t sd = smem_pencil_run(g, 3, DIV_COLS);
@@ -606,13 +679,14 @@ static int set_and_check(K kernel, const char* name, int smem, int threads) {
 template <int CN1, int CN2, int CN3>
 static int configure_sized(vdw_ctx* c) {
     const GridArgs& g = c->g;
-    const int sp = (int)smem_plane(g), sa = (int)smem_assemble(g, !c->acc_global, c->tk_smem);
+    const int sp = (int)smem_plane(g), sa = (int)smem_assemble(g, !c->acc_global, c->tk_smem, c->asm_dbuf);
     const int sd = (int)smem_pencil_run(g, 3, DIV_COLS), sc = (int)smem_pencil_run(g, c->p.Nq, c->pencil_cols);
     const int tc = contract_threads(g, c->pencil_cols);
     int rc = set_and_check(k_theta_plane<CN1, CN3>, "k_theta_plane", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_assemble<CN1, CN3>, "k_assemble", sa, ASM_THREADS);
     if (!rc) rc = set_and_check(k_pencil_div<CN2>, "k_pencil_div", sd, 256);
     if (!rc) rc = set_and_check(k_div_final<CN1, CN3>, "k_div_final", sp, PLANE_THREADS);
+    if (!rc) rc = set_and_check(k_w_planes<CN1, CN3>, "k_w_planes", sp, PLANE_THREADS);
     if (rc) return rc;
     switch (c->p.Nq) {
         case 20: rc = set_and_check(k_pencil_contract<20, CN2>, "k_pencil_contract", sc, tc); break;

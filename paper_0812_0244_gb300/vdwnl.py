@@ -74,7 +74,7 @@ EXPORTS = ["vdw_params_default", "vdw_kernel_table", "vdw_create", "vdw_plan", "
            "vdw_energy_potential_host", "vdw_last_invalid_points", "vdw_profile_enable", "vdw_profile_read",
            "vdw_delta_energy_noalloc", "vdw_spectral_gradient", "vdw_learned_param_count", "vdw_learned_load",
            "vdw_learned_energy_potential", "vdw_learned_param_grad", "vdw_learned_fit_grad",
-           "vdw_learned_channels", "vdw_learned_status", "vdw_basis_weights", "vdw_adam_step",
+           "vdw_learned_channels", "vdw_learned_status", "vdw_basis_weights", "vdw_adam_step", "vdw_wait_status",
            "vdw_workspace_bytes", "vdw_destroy", "vdw_error_string", "vdw_last_error"]
 
 LEARNED_M = 8
@@ -114,6 +114,7 @@ def lib():
     L.vdw_basis_weights.argtypes = [vp, vp, vp, vp, vp]
     L.vdw_adam_step.argtypes = [vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
+    L.vdw_wait_status.argtypes = [vp, P(ctypes.c_int)]
     L.vdw_workspace_bytes.argtypes = [vp, P(ctypes.c_size_t)]
     L.vdw_destroy.argtypes = [vp]
     L.vdw_error_string.argtypes = [ctypes.c_int]
@@ -362,6 +363,12 @@ class VdwNL:
         ms = (ctypes.c_float * 7)()
         _check(lib().vdw_profile_read(self._h, ms), "vdw_profile_read")
         return {name: float(t) for name, t in zip(self.STAGES, ms) if t >= 0}
+
+    def wait_status(self):
+        """1 if a bounded wait inside a kernel gave up since plan(), else 0."""
+        e = ctypes.c_int()
+        _check(lib().vdw_wait_status(self._h, ctypes.byref(e)), "vdw_wait_status")
+        return e.value
 
     def workspace_bytes(self):
         b = ctypes.c_size_t()

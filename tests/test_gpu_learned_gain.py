@@ -1,0 +1,43 @@
+"""What the trained network gains over the method without it.
+
+The stored model (paper_0812_0244_gb300/trained/learned_m8_tube.npz) was
+trained on the GPU by ``python -m paper_0812_0244_gb300.learned`` (the
+library's own forward, parameter-gradient and Adam kernels) on 200 tube
+densities (seeds 1000-1199).  On the 50 held-out densities (seeds 1200-1249)
+its energy error against the plain Nq = 20 path is compared with that of the
+plain method at equal cost: 8 channels on the same mesh, which is also the
+learned model's starting point."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.slow
+def test_trained_model_beats_plain_eight_channels():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0812_0244_gb300 import learned as LR
+    from paper_0812_0244_gb300 import synthetic as S
+    from paper_0812_0244_gb300 import vdwnl
+    assert os.path.exists(LR.TRAINED_PATH)
+    mdl = LR.load()
+    shape = (72, 180, 180)
+    _, L, _ = S.tube_density_torch(1200, shape=(8, 8, 8), device="cpu")
+    ctx20 = vdwnl.VdwNL(vdwnl.Params()).plan(shape, L)
+    p8 = vdwnl.Params(Nq=8, q_1=mdl["base"][0], lam=mdl["base"][1])
+    ctx8 = vdwnl.VdwNL(p8).plan(shape, L)
+    ctx = vdwnl.VdwNL(vdwnl.Params()).plan(shape, L)
+    params = torch.tensor(mdl["params"], dtype=torch.float32, device="cuda")
+    ctx.learned_load(params, mdl["J"], mdl["k_max"], mdl["feat"], mdl["base"])
+    test_s, _ = LR.make_samples([LR.tube_config(1200 + i) for i in range(50)], shape, ctx20)
+    err8 = LR.energy_error_per_atom(ctx8, test_s, learned=False) / LR.HA_PER_MEV
+    errl = LR.energy_error_per_atom(ctx, test_s) / LR.HA_PER_MEV
+    assert ctx.learned_status() == 0
+    mae8, mael = np.abs(err8).mean(), np.abs(errl).mean()
+    print("held-out MAE meV/atom: plain 8 channels %.4f, trained %.4f" % (mae8, mael))
+    assert mael < mae8
+    assert mael < 0.1
