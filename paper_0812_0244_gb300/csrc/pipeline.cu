@@ -67,36 +67,48 @@ __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, 
 // ---------------------------------------------------------------------------
 // P1: theta_a planes, forward plane transform
 // ---------------------------------------------------------------------------
+// Fields per block (one plane each in shared memory).  Two fields per block
+// share the loads of n, t, k but spill registers in the transforms and were
+// slower at 180 x 180 x 72 (0.47 ms against 0.43 ms).
+constexpr int THETA_FIELDS = 1;
+
 template <int CN1, int CN3>
 __global__ void __launch_bounds__(PLANE_THREADS, 2) k_theta_plane(const float* __restrict__ n, const float* __restrict__ tk,
                                                         const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
                                                         const float2* __restrict__ tw, float2* __restrict__ spec) {
     extern __shared__ float2 sm[];
     __shared__ SplineSmem sp;
-    float2* plane = sm;
-    float2* tw1 = plane + g.N3 * g.Nh;
+    const int pe = g.N3 * g.Nh;
+    float2* tw1 = sm + THETA_FIELDS * pe;
     float2* tw3 = tw1 + g.N1;
-    const int y = blockIdx.x, a = blockIdx.y;
+    const int y = blockIdx.x, a0 = blockIdx.y * THETA_FIELDS;
     load_twiddles(tw1, tw, g.N1);
     load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
     load_spline_smem(&sp, P);
     __syncthreads();
-    float* pf = reinterpret_cast<float*>(plane);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int z = warp; z < g.N3; z += nw) {
         const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-        float* dst = pf + packed_row(z, g.Nh);
+        const int off = packed_row(z, g.Nh);
         for (int x = lane; x < g.N1; x += 32) {
             const int k = kk[row + x];
-            float th = 0.f;
-            if (k != K_INVALID) th = n[row + x] * cardinal_value(&sp, a, k, tk[row + x]);
-            dst[2 * x] = th;
+            const float t = tk[row + x], ni = n[row + x];
+#pragma unroll
+            for (int f = 0; f < THETA_FIELDS; ++f) {
+                float th = 0.f;
+                if (k != K_INVALID) th = ni * cardinal_value(&sp, a0 + f, k, t);
+                reinterpret_cast<float*>(sm + f * pe)[off + 2 * x] = th;
+            }
         }
     }
     __syncthreads();
-    plane_forward<CN1, CN3>(plane, g, tw1, tw3);
-    float2* dst = spec + ((long long)a * g.N2 + y) * g.ncols;
-    for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
+#pragma unroll 1
+    for (int f = 0; f < THETA_FIELDS; ++f) {
+        float2* plane = sm + f * pe;
+        plane_forward<CN1, CN3>(plane, g, tw1, tw3);
+        float2* dst = spec + ((long long)(a0 + f) * g.N2 + y) * g.ncols;
+        for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -536,6 +548,9 @@ int make_line_plan(int n, LinePlan* lp) {
 }
 
 static size_t smem_plane(const GridArgs& g) { return sizeof(float2) * ((size_t)g.N3 * g.Nh + g.N1 + g.N3); }
+static size_t smem_theta(const GridArgs& g) {
+    return sizeof(float2) * ((size_t)THETA_FIELDS * g.N3 * g.Nh + g.N1 + g.N3);
+}
 static size_t smem_assemble(const GridArgs& g, bool acc_in_smem, bool tk_in_smem, bool dbuf) {
     return sizeof(float2) * ((size_t)(dbuf ? 2 : 1) * g.N3 * g.Nh + g.N1 + g.N3) +
            (acc_in_smem ? sizeof(float) * 2 * (size_t)g.N1 * g.N3 : 0) + (tk_in_smem ? 5 * (size_t)g.N1 * g.N3 : 0);
@@ -563,12 +578,24 @@ int pipeline_plan_check(vdw_ctx* c, size_t* sp, size_t* spen, size_t* sa, size_t
     *spen = smem_pencil_run(g, nq, C);
     // assembly: double-buffered planes if at all possible, then the partial
     // sums in shared memory, then the (t, k) cache
-    c->asm_dbuf = smem_assemble(g, false, false, true) <= SMEM_MAX;
-    c->acc_global = smem_assemble(g, true, false, c->asm_dbuf) > SMEM_MAX;
-    c->tk_smem = smem_assemble(g, !c->acc_global, true, c->asm_dbuf) <= SMEM_MAX;
+    // the first of these that fits (measured at 180 x 180 x 72: the (t, k) cache
+    // in shared memory matters more than double-buffered planes, and double
+    // buffering pays when the partial sums live in global memory)
+    static const bool opts[][3] = {  // double buffer, sums in shared memory, (t, k) cache
+        {false, true, true}, {true, true, false}, {true, false, true}, {true, false, false},
+        {false, true, false}, {false, false, true}, {false, false, false}};
+    for (const auto& o : opts) {
+        if (smem_assemble(g, o[1], o[2], o[0]) <= SMEM_MAX) {
+            c->asm_dbuf = o[0];
+            c->acc_global = !o[1];
+            c->tk_smem = o[2];
+            break;
+        }
+    }
     *sa = smem_assemble(g, !c->acc_global, c->tk_smem, c->asm_dbuf);
     *sd = smem_pencil_run(g, 3, DIV_COLS);
-    if (*sp > SMEM_MAX || *spen > SMEM_MAX || *sa > SMEM_MAX || *sd > SMEM_MAX) return VDW_ERR_SIZE;
+    if (*sp > SMEM_MAX || smem_theta(g) > SMEM_MAX || *spen > SMEM_MAX || *sa > SMEM_MAX || *sd > SMEM_MAX)
+        return VDW_ERR_SIZE;
     return VDW_OK;
 }
 
@@ -625,7 +652,8 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
     mark(0);
 
     const size_t sp = smem_plane(g);
-    k_theta_plane<CN1, CN3><<<dim3(g.N2, P.Nq), PLANE_THREADS, sp, s>>>(n, c->d_t, c->d_k, g, P, c->d_tw, c->d_spec);
+    k_theta_plane<CN1, CN3><<<dim3(g.N2, P.Nq / THETA_FIELDS), PLANE_THREADS, smem_theta(g), s>>>(
+        n, c->d_t, c->d_k, g, P, c->d_tw, c->d_spec);
     mark(1);
 
     int rc = launch_contract_nq<CN2>(c, s, want_pot ? 1 : 0);
@@ -682,7 +710,7 @@ static int configure_sized(vdw_ctx* c) {
     const int sp = (int)smem_plane(g), sa = (int)smem_assemble(g, !c->acc_global, c->tk_smem, c->asm_dbuf);
     const int sd = (int)smem_pencil_run(g, 3, DIV_COLS), sc = (int)smem_pencil_run(g, c->p.Nq, c->pencil_cols);
     const int tc = contract_threads(g, c->pencil_cols);
-    int rc = set_and_check(k_theta_plane<CN1, CN3>, "k_theta_plane", sp, PLANE_THREADS);
+    int rc = set_and_check(k_theta_plane<CN1, CN3>, "k_theta_plane", (int)smem_theta(g), PLANE_THREADS);
     if (!rc) rc = set_and_check(k_assemble<CN1, CN3>, "k_assemble", sa, ASM_THREADS);
     if (!rc) rc = set_and_check(k_pencil_div<CN2>, "k_pencil_div", sd, 256);
     if (!rc) rc = set_and_check(k_div_final<CN1, CN3>, "k_div_final", sp, PLANE_THREADS);

@@ -84,29 +84,36 @@ __device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz,
 struct SplineSmem {
     float qm[MAX_NQ];
     float Mq[MAX_NQ * MAX_NQ];
+    float ih[MAX_NQ];   // 1 / h_k, h_k = q_{k+1} - q_k
+    float h26[MAX_NQ];  // h_k^2 / 6
+    float h6[MAX_NQ];   // h_k / 6
 };
 
 __device__ __forceinline__ void load_spline_smem(SplineSmem* sp, const PointParams& P) {
-    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) sp->qm[i] = P.qm[i];
+    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) {
+        sp->qm[i] = P.qm[i];
+        const float h = (i + 1 < P.Nq) ? P.qm[i + 1] - P.qm[i] : 1.f;
+        sp->ih[i] = 1.f / h;
+        sp->h26[i] = h * h * (1.f / 6.f);
+        sp->h6[i] = h * (1.f / 6.f);
+    }
     for (int i = threadIdx.x; i < MAX_NQ * MAX_NQ; i += blockDim.x) sp->Mq[i] = P.Mq[i / MAX_NQ][i % MAX_NQ];
 }
 
 // p_a and dp_a/dq on interval k at local position t.
 __device__ __forceinline__ void cardinal(const SplineSmem* sp, int a, int k, float t, float& pa, float& dpa) {
-    const float h = sp->qm[k + 1] - sp->qm[k];
     const float A = 1.f - t, B = t;
     const float M0 = sp->Mq[a * MAX_NQ + k], M1 = sp->Mq[a * MAX_NQ + k + 1];
     const float y0 = (a == k) ? 1.f : 0.f, y1 = (a == k + 1) ? 1.f : 0.f;
-    pa = A * y0 + B * y1 + ((A * A * A - A) * M0 + (B * B * B - B) * M1) * (h * h * (1.f / 6.f));
-    dpa = (y1 - y0) / h - (3.f * A * A - 1.f) * (1.f / 6.f) * h * M0 + (3.f * B * B - 1.f) * (1.f / 6.f) * h * M1;
+    pa = A * y0 + B * y1 + ((A * A * A - A) * M0 + (B * B * B - B) * M1) * sp->h26[k];
+    dpa = (y1 - y0) * sp->ih[k] + ((3.f * B * B - 1.f) * M1 - (3.f * A * A - 1.f) * M0) * sp->h6[k];
 }
 
 __device__ __forceinline__ float cardinal_value(const SplineSmem* sp, int a, int k, float t) {
-    const float h = sp->qm[k + 1] - sp->qm[k];
     const float A = 1.f - t, B = t;
     const float M0 = sp->Mq[a * MAX_NQ + k], M1 = sp->Mq[a * MAX_NQ + k + 1];
     const float y0 = (a == k) ? 1.f : 0.f, y1 = (a == k + 1) ? 1.f : 0.f;
-    return A * y0 + B * y1 + ((A * A * A - A) * M0 + (B * B * B - B) * M1) * (h * h * (1.f / 6.f));
+    return A * y0 + B * y1 + ((A * A * A - A) * M0 + (B * B * B - B) * M1) * sp->h26[k];
 }
 
 }  // namespace vdw
