@@ -206,9 +206,11 @@ int vdw_spectral_gradient(vdw_handle h, const float* f, float* grad, void* strea
  * Features (s2 = |grad n|^2 n^(-8/3), a smooth form of |grad n| / n^(4/3)):
  *   x1 = (ln n - feat[0]) / feat[1],  x2 = (1/2 ln(s2 + feat[4]^2) - feat[2]) / feat[3]
  * Network: h1 = bf16(silu(W1 x + b1)), h2 = bf16(silu(W2 h1 + b2)),
- *   w = W3 h2 + b3; the weights are rounded to bf16, layers 2 and 3 (and the
- *   potential's Jacobian-vector product) run on the tensor cores with FP32
- *   accumulation.  Points with n <= n_min carry theta = 0.
+ *   w = W3 h2 + b3; the weights are rounded to bf16, layers 2 and 3 run on
+ *   the tensor cores with FP32 accumulation, together with the forward-mode
+ *   tangents d/dx1, d/dx2 that give the potential the network's Jacobian
+ *   (tangents rounded to bf16 where they enter a product).  Points with
+ *   n <= n_min carry theta = 0.
  * Parameters: one flat FP32 vector of vdw_learned_param_count(J) values, in
  *   the order W1[64][2], b1[64], W2[64][64], b2[64], W3[8][64], b3[8],
  *   K[36][J] (pairs m <= n, row-major), W[out][in].

@@ -38,10 +38,11 @@ with H = 64 hidden units and P = M(M+1)/2 pairs.
 
 Precision mirrored from the CUDA path: weights and the two hidden activations
 are rounded to bf16 (round to nearest, ties to even) before they enter a
-product, exactly where the tensor-core operands are bf16.  The potential's
-Jacobian-vector product rounds its operands (the cotangent u and the second
-layer's delta) to bf16 the same way unless ``vjp_bf16=False``, which gives the
-exact derivative of the model (used by the finite-difference pins).
+product, exactly where the tensor-core operands are bf16.  The potential
+needs the network's Jacobian dw/dx, formed by forward mode beside the
+forward pass; its tangents are rounded to bf16 where they enter a
+tensor-core product unless ``jac_bf16=False``, which gives the exact
+derivative of the model (used by the finite-difference pins).
 Parameter gradients are exact derivatives of the mirrored forward, treating
 each rounding as the identity (straight-through).
 """
@@ -207,16 +208,21 @@ def mlp_forward(x1, x2, mdl: LearnedModel):
     return dict(X=X, z1=z1, h1=h1, z2=z2, h2=h2, w=w, W1=W1, W2=W2, W3=W3)
 
 
-def mlp_vjp_inputs(f, u, vjp_bf16=True):
-    """c_j = sum_m u_m dw_m/dx_j for each point (2, m), given the forward f and
-    the cotangent u (M, m).  With vjp_bf16 the tensor-core operands (u and the
-    second layer's delta) are rounded to bf16 as the CUDA path does."""
-    r = bf16_round if vjp_bf16 else (lambda a: a)
-    g2 = f["W3"].T @ r(u)                         # (H, m)
-    d2 = g2 * silu_prime(f["z2"])
-    g1 = f["W2"].T @ r(d2)
-    d1 = g1 * silu_prime(f["z1"])
-    return f["W1"].T @ d1                         # (2, m)
+def mlp_jacobian(f, jac_bf16=True):
+    """J[m, j, point] = d w_m / d x_j by forward mode: tangents
+    dz1_j = W1[:, j], dh1_j = silu'(z1) dz1_j, dz2_j = W2 dh1_j,
+    dh2_j = silu'(z2) dz2_j, dw_j = W3 dh2_j.  With jac_bf16 the tangents that
+    enter a tensor-core product (dh1_j, dh2_j) are rounded to bf16 as the CUDA
+    path does; the activations' own bf16 rounding counts as the identity."""
+    r = bf16_round if jac_bf16 else (lambda a: a)
+    s1 = silu_prime(f["z1"])
+    s2 = silu_prime(f["z2"])
+    out = []
+    for j in range(2):
+        dh1 = r(s1 * f["W1"][:, j][:, None])
+        dh2 = r(s2 * (f["W2"] @ dh1))
+        out.append(f["W3"] @ dh2)
+    return np.stack(out, axis=1)  # (M, 2, m)
 
 
 # --------------------------------------------------------------------------
@@ -268,7 +274,7 @@ def kernel_eval(mdl: LearnedModel, kmod):
 # --------------------------------------------------------------------------
 
 
-def energy_potential(n, grad, cell, mdl: LearnedModel, T: V.KernelTable, want_v=True, vjp_bf16=True,
+def energy_potential(n, grad, cell, mdl: LearnedModel, T: V.KernelTable, want_v=True, jac_bf16=True,
                      want_grad=False):
     """E (= E_soft + Delta E), and optionally v and dE/dparams of the learned
     basis on the periodic grid (conventions of the plain oracle: theta(G) =
@@ -301,7 +307,8 @@ def energy_potential(n, grad, cell, mdl: LearnedModel, T: V.KernelTable, want_v=
     u = np.real(np.fft.ifftn(u_hat, axes=(1, 2, 3))) * N
     out["u"] = u
     if want_v:
-        c = mlp_vjp_inputs(f, u.reshape(mdl.M, -1), vjp_bf16).reshape((2,) + shape)
+        Jm = mlp_jacobian(f, jac_bf16)
+        c = np.einsum("mjp,mp->jp", Jm, u.reshape(mdl.M, -1)).reshape((2,) + shape)
         S0 = np.sum(u * w, axis=0)
         q4 = np.where(pw["ok"], q ** 4, 1.0)
         dE_n = T.C_s * (pw["n"] / q ** 3 - 1.5 * pw["n"] ** 2 / q4 * pw["dq_dn"])
@@ -355,12 +362,12 @@ def energy_grad(n, grad, cell, mdl, T):
 # --------------------------------------------------------------------------
 
 
-def loss(n, cell, mdl, T, E_ref, v_ref, natoms, a=1.0, b=1.0, vjp_bf16=False):
+def loss(n, cell, mdl, T, E_ref, v_ref, natoms, a=1.0, b=1.0, jac_bf16=False):
     """L = a ((E - E_ref)/natoms)^2 + b sum_i n_i (v_i - v_ref_i)^2 / sum_i n_i,
     with grad n = D n (spectral)."""
     L_ = V.check_cell(cell)
     grad = V.spectral_gradient(n, L_)
-    r = energy_potential(n, grad, L_, mdl, T, want_v=True, vjp_bf16=vjp_bf16)
+    r = energy_potential(n, grad, L_, mdl, T, want_v=True, jac_bf16=jac_bf16)
     dv = r["v"] - v_ref
     return a * ((r["E"] - E_ref) / natoms) ** 2 + b * float(np.sum(n * dv * dv) / np.sum(n)), r
 
@@ -376,7 +383,7 @@ def loss_grad(n, cell, mdl, T, E_ref, v_ref, natoms, a=1.0, b=1.0, rel_step=1e-3
     N = n.size
     dOmega = float(np.prod(L_)) / N
     grad = V.spectral_gradient(n, L_)
-    r = energy_potential(n, grad, L_, mdl, T, want_v=True, vjp_bf16=False, want_grad=True)
+    r = energy_potential(n, grad, L_, mdl, T, want_v=True, jac_bf16=False, want_grad=True)
     lam = n * (r["v"] - v_ref)
     rel = np.max(np.abs(lam / n))
     eps = rel_step / rel if rel > 0 else 0.0

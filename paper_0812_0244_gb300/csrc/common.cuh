@@ -71,8 +71,6 @@ struct LearnedArgs {
     const float* b3;        // [M]
     const uint16_t* w2f;    // forward operand W2 [H out][H in]
     const uint16_t* w3f;    // forward operand W3 [16 (M padded)][H]
-    const uint16_t* w3t;    // transposed-product operand W3^T [H][16]
-    const uint16_t* w2t;    // transposed-product operand W2^T [H][H]
     const float* w2r;       // W2 bf16-rounded values, row-major [H][H] (CUDA-core kernels)
     const float* w3r;       // W3 bf16-rounded values, row-major [M][H]
     const float4* knots;    // [J-1][P]: cubic coefficients in t of the Catmull-Rom piece on interval j
@@ -124,6 +122,7 @@ struct vdw_ctx {
     void* d_lrn;                // one allocation behind the LearnedArgs pointers
     vdw::LearnedArgs la;
     float* d_U;                 // [M][N] real-space u_m for the parameter gradient (on first use)
+    float* d_lw;                // [3M][N] channel weights and network Jacobian for the assembly (on first use)
     double* d_gK;               // [P][J] knot-gradient accumulator (on first use)
     // per-stage timing (vdw_profile_enable)
     int prof;
@@ -151,6 +150,8 @@ int pipeline_make_twiddles(vdw_ctx* c);
 int pipeline_configure(vdw_ctx* c);
 // the divergence term of a potential (w(G) in d_wspec) and the energy reduction
 int pipeline_divergence(vdw_ctx* c, float* v, cudaStream_t s);
+// forward plane transforms of w = g grad n with g in d_gg (into d_wspec)
+int pipeline_w_planes(vdw_ctx* c, const float* grad, cudaStream_t s);
 int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, double* E, cudaStream_t s);
 
 // learned reduced basis (learned.cu)

@@ -56,6 +56,12 @@ __device__ __forceinline__ float silu_prime(float z) {
     const float s = __fdividef(1.f, 1.f + __expf(fminf(-z, 80.f)));
     return s * (1.f + z * (1.f - s));
 }
+// both from one exponential
+__device__ __forceinline__ void silu_both(float z, float& f, float& fp) {
+    const float s = __fdividef(1.f, 1.f + __expf(fminf(-z, 80.f)));
+    f = z * s;
+    fp = s * (1.f + z * (1.f - s));
+}
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
@@ -127,45 +133,34 @@ __device__ __forceinline__ bool base_weights(float q, const LearnedArgs& la, flo
 // ---------------------------------------------------------------------------
 // shared memory of the tensor-core network
 // ---------------------------------------------------------------------------
-// forward operands and the small layers; the transposed operands of the
-// Jacobian-vector product follow only in the kernels that need them
+// forward operands and the small layers
 struct __align__(128) MlpShared {
     uint16_t w2f[LRN_H * LRN_H];
     uint16_t w3f[LRN_N3 * LRN_H];
     float w1[2 * LRN_H], b1[LRN_H], b2[LRN_H], b3[LRN_M];
 };
-struct __align__(128) MlpShared2 {
-    uint16_t w3t[LRN_H * LRN_N3];
-    uint16_t w2t[LRN_H * LRN_H];
-};
-// One warpgroup's activation operand; the cotangent operand of the
-// Jacobian-vector product ([128][16]) reuses its first 4 KB once the forward
-// layers are done with it.
+// One warpgroup's activation operand.
 struct __align__(128) MlpWG {
     uint16_t A[L_TILE * LRN_H];
-    __device__ uint16_t* U() { return A; }
+};
+// One warpgroup's operands of the forward pass with its two tangents.
+struct __align__(128) MlpWG3 {
+    uint16_t A[3][L_TILE * LRN_H];
 };
 struct MlpCtl {
     uint64_t bar[2];
     uint32_t tmem;
-    int abort[2];  // per warpgroup: a wait gave up
+    uint32_t wgcols;  // tensor-memory columns per warpgroup
+    int abort[2];     // per warpgroup: a wait gave up
 };
 
-__device__ void mlp_load_weights(MlpShared* S, MlpShared2* S2, const LearnedArgs& la) {
+__device__ void mlp_load_weights(MlpShared* S, const LearnedArgs& la) {
     const uint4* s1 = reinterpret_cast<const uint4*>(la.w2f);
     uint4* d1 = reinterpret_cast<uint4*>(S->w2f);
     for (int i = threadIdx.x; i < LRN_H * LRN_H / 8; i += blockDim.x) d1[i] = s1[i];
     const uint4* s2 = reinterpret_cast<const uint4*>(la.w3f);
     uint4* d2 = reinterpret_cast<uint4*>(S->w3f);
     for (int i = threadIdx.x; i < LRN_N3 * LRN_H / 8; i += blockDim.x) d2[i] = s2[i];
-    if (S2) {
-        const uint4* s3 = reinterpret_cast<const uint4*>(la.w3t);
-        uint4* d3 = reinterpret_cast<uint4*>(S2->w3t);
-        for (int i = threadIdx.x; i < LRN_H * LRN_N3 / 8; i += blockDim.x) d3[i] = s3[i];
-        const uint4* s4 = reinterpret_cast<const uint4*>(la.w2t);
-        uint4* d4 = reinterpret_cast<uint4*>(S2->w2t);
-        for (int i = threadIdx.x; i < LRN_H * LRN_H / 8; i += blockDim.x) d4[i] = s4[i];
-    }
     for (int i = threadIdx.x; i < 2 * LRN_H; i += blockDim.x) S->w1[i] = la.w1[i];
     for (int i = threadIdx.x; i < LRN_H; i += blockDim.x) {
         S->b1[i] = la.b1[i];
@@ -174,14 +169,16 @@ __device__ void mlp_load_weights(MlpShared* S, MlpShared2* S2, const LearnedArgs
     for (int i = threadIdx.x; i < LRN_M; i += blockDim.x) S->b3[i] = la.b3[i];
 }
 
-// Block setup: barriers, tensor memory (256 columns: 128 per warpgroup).
-__device__ void mlp_setup(MlpCtl* ctl) {
+// Block setup: barriers, tensor memory (2 wgcols columns: wgcols per
+// warpgroup; a power of two of at least 32).
+__device__ void mlp_setup(MlpCtl* ctl, uint32_t wgcols) {
     if (threadIdx.x == 0) {
         tc::mbar_init(&ctl->bar[0], 1);
         tc::mbar_init(&ctl->bar[1], 1);
         ctl->abort[0] = ctl->abort[1] = 0;
+        ctl->wgcols = wgcols;
     }
-    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&ctl->tmem, 256);
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&ctl->tmem, 2 * wgcols);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -191,22 +188,26 @@ __device__ void mlp_setup(MlpCtl* ctl) {
 __device__ void mlp_teardown(MlpCtl* ctl) {
     tc::fence_before_sync();
     __syncthreads();
-    if ((threadIdx.x >> 5) == 0) tc::tmem_free(ctl->tmem, 256);
+    if ((threadIdx.x >> 5) == 0) tc::tmem_free(ctl->tmem, 2 * ctl->wgcols);
 }
 
-// Issue K/16 MMAs of A (K-wide) x B^T into column col of this warpgroup's
-// tensor memory, wait for them, and agree across the warpgroup on success.
-__device__ __forceinline__ bool wg_mma(MlpCtl* ctl, int wg, int r, uint32_t& phase, const uint16_t* A,
-                                       const uint16_t* B, int K, int N, uint32_t col, int* err) {
+// Issue, for each of nA operands A[i] (K-wide), the K/16 MMAs of A[i] x B^T
+// into column col[i] of this warpgroup's tensor memory; wait for all of them,
+// and agree across the warpgroup on success.
+__device__ __forceinline__ bool wg_mma_n(MlpCtl* ctl, int wg, int r, uint32_t& phase, const uint16_t* const* A,
+                                         const uint32_t* col, int nA, const uint16_t* B, int K, int N, int* err) {
     tc::fence_async_smem();
     tc::fence_before_sync();
     wg_bar(wg);
     if (r == 0) {
         tc::fence_after_sync();
-        const uint32_t a = tc::smem_u32(A), b = tc::smem_u32(B);
-        const uint32_t d = ctl->tmem + (uint32_t)(wg * 128) + col;
-        for (int k = 0; k < K / 16; ++k)
-            tc::mma_bf16(d, tc::operand_desc(a, K, k), tc::operand_desc(b, K, k), tc::idesc_bf16(128, N), k > 0);
+        const uint32_t b = tc::smem_u32(B);
+        for (int i = 0; i < nA; ++i) {
+            const uint32_t a = tc::smem_u32(A[i]);
+            const uint32_t d = ctl->tmem + (uint32_t)wg * ctl->wgcols + col[i];
+            for (int k = 0; k < K / 16; ++k)
+                tc::mma_bf16(d, tc::operand_desc(a, K, k), tc::operand_desc(b, K, k), tc::idesc_bf16(128, N), k > 0);
+        }
         tc::mma_commit(&ctl->bar[wg]);
     }
     const bool ok = tc::mbar_wait(&ctl->bar[wg], phase);
@@ -220,10 +221,15 @@ __device__ __forceinline__ bool wg_mma(MlpCtl* ctl, int wg, int r, uint32_t& pha
     return ctl->abort[wg] == 0;
 }
 
+__device__ __forceinline__ bool wg_mma(MlpCtl* ctl, int wg, int r, uint32_t& phase, const uint16_t* A,
+                                       const uint16_t* B, int K, int N, uint32_t col, int* err) {
+    return wg_mma_n(ctl, wg, r, phase, &A, &col, 1, B, K, N, err);
+}
+
 // tensor-memory address of this thread's lane, column col of its warpgroup
 __device__ __forceinline__ uint32_t lane_addr(const MlpCtl* ctl, int wg, uint32_t col) {
     const int warp = threadIdx.x >> 5;
-    return ctl->tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(wg * 128) + col;
+    return ctl->tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)wg * ctl->wgcols + col;
 }
 
 // Forward network on the warpgroup's tile (row r = this thread's point):
@@ -259,45 +265,71 @@ __device__ bool mlp_forward(MlpShared* S, MlpWG* W, MlpCtl* ctl, int wg, int r, 
     return true;
 }
 
-// Jacobian-vector product of the network with the cotangent u (8 values):
-// c_j = sum_m u_m d w_m / d x_j.  Needs the forward's layer-2 accumulator in
-// columns [0, 64); uses [64, 128) and then [0, 64) again.
-__device__ bool mlp_vjp(MlpShared* S, MlpShared2* S2, MlpWG* W, MlpCtl* ctl, int wg, int r, uint32_t& phase,
-                        float x1, float x2, const float* u, float& c1, float& c2, int* err) {
-    float uu[16];
+// Forward network with its Jacobian by forward mode (two tangents, one per
+// feature), on the warpgroup's tile: layer 1 and its tangents on the CUDA
+// cores, then layers 2 and 3 on the tensor cores for the activation and both
+// tangents at once (one wait per layer).  Tangents enter the products as bf16
+// like the activations.  Tensor memory (256 columns per warpgroup): layer 2
+// in [0, 64), [64, 128), [128, 192); layer 3 in [0, 16), [16, 32), [32, 48).
+// Returns o (8 outputs) and J1, J2 (d o / d x1, d o / d x2).
+__device__ bool mlp_forward_jac(MlpShared* S, MlpWG3* W, MlpCtl* ctl, int wg, int r, uint32_t& phase, float x1,
+                                float x2, float* o, float* J1, float* J2, int* err) {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) uu[m] = m < LRN_M ? u[m] : 0.f;
-    store8_bf16(W->U() + tc::kmaj(r, 0, LRN_N3), uu);
-    store8_bf16(W->U() + tc::kmaj(r, 8, LRN_N3), uu + 8);
-    // G2 = U W3 (tile x 64) into columns [64, 128)
-    if (!wg_mma(ctl, wg, r, phase, W->U(), S2->w3t, LRN_N3, LRN_H, 64, err)) return false;
+    for (int c = 0; c < LRN_H / 8; ++c) {
+        float h[8], t1[8], t2[8];
 #pragma unroll
-    for (int c = 0; c < LRN_H / 16; ++c) {
-        float z[16], g[16];
-        tc::tmem_ld16(lane_addr(ctl, wg, 16 * c), z);
-        tc::tmem_ld16(lane_addr(ctl, wg, 64 + 16 * c), g);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) g[q] *= silu_prime(z[q] + S->b2[16 * c + q]);
-        store8_bf16(W->A + tc::kmaj(r, 16 * c, LRN_H), g);
-        store8_bf16(W->A + tc::kmaj(r, 16 * c + 8, LRN_H), g + 8);
+        for (int q = 0; q < 8; ++q) {
+            const int j = 8 * c + q;
+            const float z = fmaf(S->w1[2 * j], x1, fmaf(S->w1[2 * j + 1], x2, S->b1[j]));
+            float sp;
+            silu_both(z, h[q], sp);
+            t1[q] = sp * S->w1[2 * j];
+            t2[q] = sp * S->w1[2 * j + 1];
+        }
+        store8_bf16(W->A[0] + tc::kmaj(r, 8 * c, LRN_H), h);
+        store8_bf16(W->A[1] + tc::kmaj(r, 8 * c, LRN_H), t1);
+        store8_bf16(W->A[2] + tc::kmaj(r, 8 * c, LRN_H), t2);
     }
-    // G1 = delta2 W2 (tile x 64) into columns [0, 64)
-    if (!wg_mma(ctl, wg, r, phase, W->A, S2->w2t, LRN_H, LRN_H, 0, err)) return false;
-    c1 = 0.f;
-    c2 = 0.f;
+    {
+        const uint16_t* As[3] = {W->A[0], W->A[1], W->A[2]};
+        const uint32_t cols[3] = {0, 64, 128};
+        if (!wg_mma_n(ctl, wg, r, phase, As, cols, 3, S->w2f, LRN_H, LRN_H, err)) return false;
+    }
 #pragma unroll
     for (int c = 0; c < LRN_H / 16; ++c) {
-        float g[16];
-        tc::tmem_ld16(lane_addr(ctl, wg, 16 * c), g);
+        float z[16], d1[16], d2[16];
+        tc::tmem_ld16(lane_addr(ctl, wg, 16 * c), z);
+        tc::tmem_ld16(lane_addr(ctl, wg, 64 + 16 * c), d1);
+        tc::tmem_ld16(lane_addr(ctl, wg, 128 + 16 * c), d2);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-            const int j = 16 * c + q;
-            const float z1 = fmaf(S->w1[2 * j], x1, fmaf(S->w1[2 * j + 1], x2, S->b1[j]));
-            const float d1 = g[q] * silu_prime(z1);
-            c1 = fmaf(S->w1[2 * j], d1, c1);
-            c2 = fmaf(S->w1[2 * j + 1], d1, c2);
+            float sp;
+            silu_both(z[q] + S->b2[16 * c + q], z[q], sp);
+            d1[q] *= sp;
+            d2[q] *= sp;
         }
+        store8_bf16(W->A[0] + tc::kmaj(r, 16 * c, LRN_H), z);
+        store8_bf16(W->A[0] + tc::kmaj(r, 16 * c + 8, LRN_H), z + 8);
+        store8_bf16(W->A[1] + tc::kmaj(r, 16 * c, LRN_H), d1);
+        store8_bf16(W->A[1] + tc::kmaj(r, 16 * c + 8, LRN_H), d1 + 8);
+        store8_bf16(W->A[2] + tc::kmaj(r, 16 * c, LRN_H), d2);
+        store8_bf16(W->A[2] + tc::kmaj(r, 16 * c + 8, LRN_H), d2 + 8);
     }
+    {
+        const uint16_t* As[3] = {W->A[0], W->A[1], W->A[2]};
+        const uint32_t cols[3] = {0, 16, 32};
+        if (!wg_mma_n(ctl, wg, r, phase, As, cols, 3, S->w3f, LRN_H, LRN_N3, err)) return false;
+    }
+    float v[16];
+    tc::tmem_ld16(lane_addr(ctl, wg, 0), v);
+#pragma unroll
+    for (int m = 0; m < LRN_M; ++m) o[m] = v[m] + S->b3[m];
+    tc::tmem_ld16(lane_addr(ctl, wg, 16), v);
+#pragma unroll
+    for (int m = 0; m < LRN_M; ++m) J1[m] = v[m];
+    tc::tmem_ld16(lane_addr(ctl, wg, 32), v);
+#pragma unroll
+    for (int m = 0; m < LRN_M; ++m) J2[m] = v[m];
     return true;
 }
 
@@ -320,8 +352,6 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
     float* w3r = const_cast<float*>(la.w3r);
     uint16_t* w2f = const_cast<uint16_t*>(la.w2f);
     uint16_t* w3f = const_cast<uint16_t*>(la.w3f);
-    uint16_t* w3t = const_cast<uint16_t*>(la.w3t);
-    uint16_t* w2t = const_cast<uint16_t*>(la.w2t);
     float4* kn = const_cast<float4*>(la.knots);
     const int t = threadIdx.x + blockIdx.x * blockDim.x, nt = blockDim.x * gridDim.x;
     auto bfu = [](float x) { return (uint16_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)); };
@@ -336,14 +366,12 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
         const float x = flat[LRN_OFF_W2 + i];
         w2r[i] = bf16r(x);
         w2f[tc::kmaj(o, j, LRN_H)] = bfu(x);
-        w2t[tc::kmaj(j, o, LRN_H)] = bfu(x);
     }
     for (int i = t; i < LRN_N3 * LRN_H; i += nt) {
         const int m = i / LRN_H, j = i % LRN_H;  // W3[m][j], rows m >= M are zero
         const float x = m < LRN_M ? flat[LRN_OFF_W3 + m * LRN_H + j] : 0.f;
         if (m < LRN_M) w3r[m * LRN_H + j] = bf16r(x);
         w3f[tc::kmaj(m, j, LRN_H)] = bfu(x);
-        w3t[tc::kmaj(j, m, LRN_N3)] = bfu(x);
     }
     // Catmull-Rom piece on [k_j, k_j+1] from knots j-1 .. j+2: K is even in k
     // (K_-1 = K_1) and continues linearly past the last knot
@@ -363,12 +391,14 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
 // L1: network, channels, forward plane transforms
 // ---------------------------------------------------------------------------
 // Tile T (128 consecutive points of the plane, index i = z N1 + x) belongs to
-// block (T / 2) mod 8, warpgroup T mod 2.
+// block (T / 2) mod 8, warpgroup T mod 2.  With lw the channel weights and
+// the network's Jacobian are also stored for the assembly: lw [24][N] holds
+// w_m, then d o_m / d x1, then d o_m / d x2.
 template <int CN1, int CN3>
-__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 2)
+__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
     k_learned_theta(const float* __restrict__ n, const float* __restrict__ grad, GridArgs g, PointParams P,
                     LearnedArgs la, const float2* __restrict__ tw, float2* __restrict__ spec,
-                    double* __restrict__ epart, unsigned long long* __restrict__ invalid) {
+                    double* __restrict__ epart, unsigned long long* __restrict__ invalid, float* __restrict__ lw) {
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ MlpCtl ctl;
@@ -378,16 +408,16 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 2)
     float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
     MlpShared* S = reinterpret_cast<MlpShared*>(smraw + plane_bytes(g.N3, g.Nh, g.N1));
-    MlpWG* Wb = reinterpret_cast<MlpWG*>(reinterpret_cast<unsigned char*>(S) + sizeof(MlpShared));
+    MlpWG3* Wb = reinterpret_cast<MlpWG3*>(reinterpret_cast<unsigned char*>(S) + sizeof(MlpShared));
     const int y = blockIdx.x;
     const int rank = (int)cluster.block_rank();
     const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
-    MlpWG* W = Wb + wg;
+    MlpWG3* W = Wb + wg;
     load_twiddles(tw1, tw, g.N1);
     load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
-    mlp_load_weights(S, nullptr, la);
+    mlp_load_weights(S, la);
     for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
-    mlp_setup(&ctl);
+    mlp_setup(&ctl, 256);
     float* pf = reinterpret_cast<float*>(plane);
     float* rem[L_CTAS];
 #pragma unroll
@@ -424,12 +454,20 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 2)
                 if (la.base) base_weights(qp.q, la, pb, dpb);
             }
         }
-        float o[LRN_M];
-        if (!mlp_forward(S, W, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, la.err)) break;
+        float o[LRN_M], J1[LRN_M], J2[LRN_M];
+        if (!mlp_forward_jac(S, W, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, J1, J2, la.err)) break;
         if (in) {
             const int off = packed_row(z, g.Nh) + 2 * x;
 #pragma unroll
             for (int m = 0; m < LRN_M; ++m) rem[m][off] = ok ? ni * (o[m] + pb[m]) : 0.f;
+            if (lw) {
+#pragma unroll
+                for (int m = 0; m < LRN_M; ++m) {
+                    lw[m * N + gi] = ok ? o[m] + pb[m] : 0.f;
+                    lw[(LRN_M + m) * N + gi] = J1[m];
+                    lw[(2 * LRN_M + m) * N + gi] = J2[m];
+                }
+            }
         }
     }
     mlp_teardown(&ctl);
@@ -578,38 +616,34 @@ __global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ s
 }
 
 // ---------------------------------------------------------------------------
-// L3: inverse plane transforms of u_m, network Jacobian, assembly of Eq. (Vi)
+// L3: inverse plane transforms of u_m, assembly of Eq. (Vi)
 // ---------------------------------------------------------------------------
-// mode 0: v_loc to v, w = g grad n to w_out; mode 1: v_loc to v, w(G) to wspec;
-// mode 2: only the real-space u_m to U (parameter gradient).
+// Block m inverse-transforms u_m; after a cluster barrier block r finishes the
+// rows z = r (mod 8) of the plane from the 8 u values of each point (through
+// distributed shared memory), the channel weights and the network's Jacobian
+// stored by L1 (lw), and the spline base.
+// mode 0: v_loc to v, w = g grad n to w_out; mode 1: v_loc to v, g to g_out
+// (the plane transforms of w follow in k_w_planes); mode 2: only the
+// real-space u_m to U (parameter gradient).
 template <int CN1, int CN3>
-__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
+__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 2)
     k_learned_assemble(const float2* __restrict__ spec, const float* __restrict__ n, const float* __restrict__ grad,
                        GridArgs g, PointParams P, LearnedArgs la, const float2* __restrict__ tw,
-                       float* __restrict__ v, float* __restrict__ w_out, float2* __restrict__ wspec,
-                       float* __restrict__ U, int mode) {
+                       const float* __restrict__ lw, float* __restrict__ v, float* __restrict__ w_out,
+                       float* __restrict__ g_out, float* __restrict__ U, int mode) {
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ MlpCtl ctl;
     __shared__ float qm[MAX_NQ];
     float2* plane = reinterpret_cast<float2*>(smraw);
     float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
-    MlpShared* S = reinterpret_cast<MlpShared*>(smraw + plane_bytes(g.N3, g.Nh, g.N1));
-    MlpShared2* S2 = reinterpret_cast<MlpShared2*>(reinterpret_cast<unsigned char*>(S) + sizeof(MlpShared));
-    MlpWG* Wb = reinterpret_cast<MlpWG*>(reinterpret_cast<unsigned char*>(S2) + sizeof(MlpShared2));
-    float* gg_s = reinterpret_cast<float*>(Wb + 2);  // g of this block's tiles
     const int y = blockIdx.x;
     const int rank = (int)cluster.block_rank();
-    const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    MlpWG* W = Wb + wg;
     const long long N = g.N;
     load_twiddles(tw1, tw, g.N1);
     load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
-    if (mode != 2) mlp_load_weights(S, S2, la);
     for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
-    // u_m of this block's channel
     const float2* src = spec + ((long long)rank * g.N2 + y) * g.ncols;
     for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     __syncthreads();
@@ -623,99 +657,59 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
         }
         return;
     }
-    mlp_setup(&ctl);
     const float* rem[L_CTAS];
 #pragma unroll
     for (int m = 0; m < L_CTAS; ++m) rem[m] = cluster.map_shared_rank(pf, m);
     cluster.sync();  // every channel's u is in place
-    const int np = g.N1 * g.N3;
-    const int ntiles = (np + L_TILE - 1) / L_TILE;
-    uint32_t phase = 0;
-    for (int T = 2 * rank + wg; T < ntiles; T += 2 * L_CTAS) {
-        const int i = T * L_TILE + r;
-        const bool in = i < np;
-        const int z = in ? i / g.N1 : 0, x = in ? i - z * g.N1 : 0;
-        const long long gi = (long long)g.N1 * (y + (long long)g.N2 * z) + x;
-        float ni = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-        float u[LRN_M];
-        if (in) {
-            ni = n[gi];
-            gx = grad[gi];
-            gy = grad[N + gi];
-            gz = grad[2 * N + gi];
-            const int off = packed_row(z, g.Nh) + 2 * x;
+    for (int z = rank + L_CTAS * warp; z < g.N3; z += L_CTAS * nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+        const int off0 = packed_row(z, g.Nh);
+        for (int x = lane; x < g.N1; x += 32) {
+            const long long gi = row + x;
+            const float ni = n[gi];
+            const float gx = grad[gi], gy = grad[N + gi], gz = grad[2 * N + gi];
+            const Feat f = features(ni, gx, gy, gz, la, P.n_min);
+            float vl = 0.f, gg = 0.f;
+            if (f.ok) {
+                float u[LRN_M];
 #pragma unroll
-            for (int m = 0; m < LRN_M; ++m) u[m] = rem[m][off];
-        } else {
+                for (int m = 0; m < LRN_M; ++m) u[m] = rem[m][off0 + 2 * x];
+                const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
+                float dEn = 0.f, dEg = 0.f, bn = 0.f, bg = 0.f;
+                float pb[LRN_M], dpb[LRN_M];
 #pragma unroll
-            for (int m = 0; m < LRN_M; ++m) u[m] = 0.f;
-        }
-        const Feat f = features(ni, gx, gy, gz, la, P.n_min);
-        const bool ok = in && f.ok;
-        const float x1 = ok ? f.x1 : 0.f, x2 = ok ? f.x2 : 0.f;
-        float o[LRN_M];
-        if (!mlp_forward(S, W, &ctl, wg, r, phase, x1, x2, o, la.err)) break;
-        float c1 = 0.f, c2 = 0.f;
-        if (!mlp_vjp(S, S2, W, &ctl, wg, r, phase, x1, x2, u, c1, c2, la.err)) break;
-        float vl = 0.f, gg = 0.f;
-        if (ok) {
-            const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
-            float dEn = 0.f, dEg = 0.f, bn = 0.f, bg = 0.f;
-            float pb[LRN_M], dpb[LRN_M];
-#pragma unroll
-            for (int m = 0; m < LRN_M; ++m) pb[m] = dpb[m] = 0.f;
-            if (qp.k != K_INVALID) {
-                const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
-                const float cn = 1.5f * P.C_s * ni * ni / q4;
-                dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
-                dEg = -cn * qp.dq_dg;
-                if (la.base && base_weights(q, la, pb, dpb)) {
-                    bn = qp.dq_dn;
-                    bg = qp.dq_dg;
+                for (int m = 0; m < LRN_M; ++m) pb[m] = dpb[m] = 0.f;
+                if (qp.k != K_INVALID) {
+                    const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
+                    const float cn = 1.5f * P.C_s * ni * ni / q4;
+                    dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
+                    dEg = -cn * qp.dq_dg;
+                    if (la.base && base_weights(q, la, pb, dpb)) {
+                        bn = qp.dq_dn;
+                        bg = qp.dq_dg;
+                    }
                 }
-            }
-            float s0 = 0.f, s1 = 0.f;
+                float s0 = 0.f, s1 = 0.f, c1 = 0.f, c2 = 0.f;
 #pragma unroll
-            for (int m = 0; m < LRN_M; ++m) {
-                s0 = fmaf(u[m], o[m] + pb[m], s0);
-                s1 = fmaf(u[m], dpb[m], s1);
+                for (int m = 0; m < LRN_M; ++m) {
+                    s0 = fmaf(u[m], lw[m * N + gi], s0);
+                    s1 = fmaf(u[m], dpb[m], s1);
+                    c1 = fmaf(u[m], lw[(LRN_M + m) * N + gi], c1);
+                    c2 = fmaf(u[m], lw[(2 * LRN_M + m) * N + gi], c2);
+                }
+                vl = s0 + ni * (c1 * f.dx1_dn + c2 * f.dx2_dn + s1 * bn) + dEn;
+                gg = ni * (c2 * f.gx2 + s1 * bg) + dEg;
             }
-            vl = s0 + ni * (c1 * f.dx1_dn + c2 * f.dx2_dn + s1 * bn) + dEn;
-            gg = ni * (c2 * f.gx2 + s1 * bg) + dEg;
-        }
-        if (in) {
             if (v) v[gi] = vl;
             if (mode == 0 && w_out) {
                 w_out[gi] = gg * gx;
                 w_out[N + gi] = gg * gy;
                 w_out[2 * N + gi] = gg * gz;
             }
+            if (mode == 1) g_out[gi] = gg;
         }
-        gg_s[(T >> 4) * 2 * L_TILE + (T & 1) * L_TILE + r] = gg;
     }
-    mlp_teardown(&ctl);
-    cluster.sync();  // g of every tile is in place; u planes no longer read
-    if (mode == 1 && rank < 3) {
-        const int c = rank;
-        const float* ggr[L_CTAS];
-#pragma unroll
-        for (int m = 0; m < L_CTAS; ++m) ggr[m] = cluster.map_shared_rank(gg_s, m);
-        for (int z = warp; z < g.N3; z += nw) {
-            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-            float* dst = pf + packed_row(z, g.Nh);
-            for (int x = lane; x < g.N1; x += 32) {
-                const int i = z * g.N1 + x;
-                const int T = i / L_TILE, rr = i - T * L_TILE;
-                const float ggv = ggr[(T >> 1) & (L_CTAS - 1)][(T >> 4) * 2 * L_TILE + (T & 1) * L_TILE + rr];
-                dst[2 * x] = ggv * grad[c * N + row + x];
-            }
-        }
-        __syncthreads();
-        plane_forward<CN1, CN3>(plane, g, tw1, tw3);
-        float2* dst = wspec + ((long long)c * g.N2 + y) * g.ncols;
-        for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
-    }
-    cluster.sync();  // keep g alive until every block is done reading it
+    cluster.sync();  // keep u alive until every block is done reading it
 }
 
 // ---------------------------------------------------------------------------
@@ -733,8 +727,8 @@ __global__ void __launch_bounds__(L_THREADS, 1) k_learned_channels(const float* 
     MlpShared* S = reinterpret_cast<MlpShared*>(smraw);
     MlpWG* Wb = reinterpret_cast<MlpWG*>(smraw + sizeof(MlpShared));
     const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
-    mlp_load_weights(S, nullptr, la);
-    mlp_setup(&ctl);
+    mlp_load_weights(S, la);
+    mlp_setup(&ctl, 128);
     uint32_t phase = 0;
     const long long ntiles = (N + L_TILE - 1) / L_TILE;
     for (long long T = 2 * (long long)blockIdx.x + wg; T < ntiles; T += 2 * (long long)gridDim.x) {
@@ -1042,11 +1036,8 @@ __global__ void k_adam(float* __restrict__ p, const double* __restrict__ g, floa
 // host side
 // ---------------------------------------------------------------------------
 size_t smem_cluster(const GridArgs& g, bool assemble) {
-    const int np = g.N1 * g.N3;
-    const int ntiles = (np + L_TILE - 1) / L_TILE;
-    const size_t gg = assemble ? sizeof(float) * (size_t)((ntiles + 2 * L_CTAS - 1) / (2 * L_CTAS)) * 2 * L_TILE : 0;
-    return plane_bytes(g.N3, g.Nh, g.N1) + sizeof(MlpShared) + (assemble ? sizeof(MlpShared2) : 0) +
-           2 * sizeof(MlpWG) + gg;
+    // the assembly holds one plane; the network side also its operands
+    return plane_bytes(g.N3, g.Nh, g.N1) + (assemble ? 0 : sizeof(MlpShared) + 2 * sizeof(MlpWG3));
 }
 int contract_cols(const GridArgs& g) {
     int C = 8;
@@ -1152,10 +1143,10 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
         cudaEventRecord(c->ev[0], s);
     }
     VDW_CUDA(cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long), s));
-    k_learned_theta<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, false), s>>>(
-        n, grad, g, P, la, c->d_tw, c->d_spec, ep, c->d_invalid);
-    mark(1);
     const bool want_pot = (v != nullptr) || (w != nullptr);
+    k_learned_theta<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, false), s>>>(
+        n, grad, g, P, la, c->d_tw, c->d_spec, ep, c->d_invalid, (want_pot && kind != RUN_GRAD) ? c->d_lw : nullptr);
+    mark(1);
     if (kind == RUN_GRAD) {
         VDW_CUDA(cudaMemsetAsync(c->d_gK, 0, sizeof(double) * LRN_P * c->lrn_J, s));
         k_learned_contract<CN2, true><<<nb_c, 256, smem_contract(g, C, true, c->lrn_J), s>>>(
@@ -1172,7 +1163,7 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     }
     if (kind == RUN_GRAD) {
         k_learned_assemble<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, true), s>>>(
-            c->d_spec, n, grad, g, P, la, c->d_tw, nullptr, nullptr, nullptr, c->d_U, 2);
+            c->d_spec, n, grad, g, P, la, c->d_tw, nullptr, nullptr, nullptr, nullptr, c->d_U, 2);
         const double dOmega = Omega / (double)g.N;
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
@@ -1183,7 +1174,11 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     } else if (want_pot) {
         const int mode = (w != nullptr) ? 0 : 1;
         k_learned_assemble<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, true), s>>>(
-            c->d_spec, n, grad, g, P, la, c->d_tw, v, w, c->d_wspec, nullptr, mode);
+            c->d_spec, n, grad, g, P, la, c->d_tw, c->d_lw, v, w, c->d_gg, nullptr, mode);
+        if (mode == 1) {
+            int rc = pipeline_w_planes(c, grad, s);
+            if (rc) return rc;
+        }
         mark(4);
         if (mode == 1) {
             int rc = pipeline_divergence(c, v, s);
@@ -1228,7 +1223,7 @@ bool lrn_ready(vdw_ctx* c) {
 
 // Size of the learned context's allocation and its layout (256-byte aligned pieces).
 struct LrnLayout {
-    size_t epart, w1, b1, b2, b3, w2r, w3r, w2f, w3f, w3t, w2t, knots, err, gK, total;
+    size_t epart, w1, b1, b2, b3, w2r, w3r, w2f, w3f, knots, err, gK, total;
 };
 static LrnLayout lrn_layout(const GridArgs& g, int J) {
     LrnLayout L{};
@@ -1247,8 +1242,6 @@ static LrnLayout lrn_layout(const GridArgs& g, int J) {
     L.w3r = take(sizeof(float) * LRN_M * LRN_H);
     L.w2f = take(2 * LRN_H * LRN_H);
     L.w3f = take(2 * LRN_N3 * LRN_H);
-    L.w3t = take(2 * LRN_H * LRN_N3);
-    L.w2t = take(2 * LRN_H * LRN_H);
     L.knots = take(sizeof(float4) * (size_t)(J - 1) * LRN_P);
     L.err = take(sizeof(int));
     L.gK = take(sizeof(double) * (size_t)LRN_P * J);
@@ -1259,14 +1252,17 @@ static LrnLayout lrn_layout(const GridArgs& g, int J) {
 void learned_free(vdw_ctx* c) {
     cudaFree(c->d_lrn);
     cudaFree(c->d_U);
+    cudaFree(c->d_lw);
     c->d_lrn = nullptr;
     c->d_U = nullptr;
+    c->d_lw = nullptr;
     c->d_gK = nullptr;
     c->lrn_loaded = 0;
 }
 
 int learned_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s) {
     if (!lrn_ready(c)) return VDW_ERR_STATE;
+    if ((v || w) && !c->d_lw) VDW_CUDA(cudaMalloc(&c->d_lw, sizeof(float) * 3 * LRN_M * (size_t)c->g.N));
     return run_any(c, n, grad, E, v, w, RUN_ENERGY, 0.0, nullptr, s);
 }
 
@@ -1312,8 +1308,6 @@ int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], do
         la.w3r = reinterpret_cast<float*>(b + L.w3r);
         la.w2f = reinterpret_cast<uint16_t*>(b + L.w2f);
         la.w3f = reinterpret_cast<uint16_t*>(b + L.w3f);
-        la.w3t = reinterpret_cast<uint16_t*>(b + L.w3t);
-        la.w2t = reinterpret_cast<uint16_t*>(b + L.w2t);
         la.knots = reinterpret_cast<float4*>(b + L.knots);
         la.err = reinterpret_cast<int*>(b + L.err);
         c->d_gK = reinterpret_cast<double*>(b + L.gK);
@@ -1367,8 +1361,7 @@ int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], do
 int vdw_learned_energy_potential(vdw_handle c, const float* n, const float* grad, double* E, float* v, float* w,
                                  void* stream) {
     if (!c || !n || !grad) return VDW_ERR_ARG;
-    if (!lrn_ready(c)) return VDW_ERR_STATE;
-    return run_any(c, n, grad, E, v, w, RUN_ENERGY, 0.0, nullptr, (cudaStream_t)stream);
+    return learned_run(c, n, grad, E, v, w, (cudaStream_t)stream);
 }
 
 int vdw_learned_param_grad(vdw_handle c, const float* n, const float* grad, double coef, double* g_params, double* E,

@@ -761,6 +761,21 @@ static void launch_divergence(vdw_ctx* c, float* v, cudaStream_t s) {
     k_div_final<CN1, CN3><<<g.N2, PLANE_THREADS, smem_plane(g), s>>>(c->d_wspec, g, c->d_tw, v);
 }
 
+template <int CN1, int CN3>
+static void launch_w_planes(vdw_ctx* c, const float* grad, cudaStream_t s) {
+    const GridArgs& g = c->g;
+    k_w_planes<CN1, CN3><<<dim3(g.N2, 3), PLANE_THREADS, smem_plane(g), s>>>(c->d_gg, grad, g, c->d_tw, c->d_wspec);
+}
+
+int pipeline_w_planes(vdw_ctx* c, const float* grad, cudaStream_t s) {
+    const GridArgs& g = c->g;
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) launch_w_planes<180, 72>(c, grad, s);
+    else if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) launch_w_planes<256, 96>(c, grad, s);
+    else launch_w_planes<0, 0>(c, grad, s);
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
 int pipeline_divergence(vdw_ctx* c, float* v, cudaStream_t s) {
     const GridArgs& g = c->g;
     if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) launch_divergence<180, 180, 72>(c, v, s);

@@ -95,7 +95,7 @@ def test_energy_and_potential_match_oracle(torch_cuda, table, case):
     E = E.cpu().numpy()
     v = v.cpu().numpy()
     assert ctx.learned_status() == 0
-    ref = LO.energy_potential(n64, g64, L, mdl, table, vjp_bf16=True)
+    ref = LO.energy_potential(n64, g64, L, mdl, table, jac_bf16=True)
     assert abs(E[2] - ref["dE"]) <= 1e-6 * abs(ref["dE"]) + 1e-9
     assert abs(E[1] - ref["E_soft"]) <= 1e-5 * abs(ref["E_soft"]) + 1e-7, (E, ref["E_soft"])
     assert abs(E[0] - ref["E"]) <= 1e-5 * abs(ref["E_soft"]) + 1e-6
@@ -217,7 +217,7 @@ def test_learned_full_tube_matches_oracle(torch_cuda, table):
     E = E.cpu().numpy()
     v = v.cpu().numpy()
     assert ctx.learned_status() == 0
-    ref = LO.energy_potential(n64, g64, L, mdl, table, vjp_bf16=True)
+    ref = LO.energy_potential(n64, g64, L, mdl, table, jac_bf16=True)
     assert abs(E[1] - ref["E_soft"]) <= 1e-5 * abs(ref["E_soft"]) + 1e-7, (E, ref["E_soft"])
     assert abs(E[2] - ref["dE"]) <= 1e-6 * abs(ref["dE"])
     err = np.abs(v - ref["v"])

@@ -147,9 +147,9 @@ def test_learned_potential_matches_finite_differences(table, monkeypatch, base):
     then compared with the exact one."""
     n, g, L = _tiny()
     mdl = LO.random_model(6, base=base)
-    rb = LO.energy_potential(n, g, L, mdl, table, vjp_bf16=True)
+    rb = LO.energy_potential(n, g, L, mdl, table, jac_bf16=True)
     monkeypatch.setattr(LO, "bf16_round", lambda a: np.asarray(a, np.float64))
-    r = LO.energy_potential(n, g, L, mdl, table, vjp_bf16=False)
+    r = LO.energy_potential(n, g, L, mdl, table, jac_bf16=False)
     dOmega = float(np.prod(L)) / n.size
     rng = np.random.default_rng(3)
     vmax = np.abs(r["v"]).max()
@@ -165,7 +165,7 @@ def test_learned_potential_matches_finite_differences(table, monkeypatch, base):
         assert abs(fd - r["v"][pt]) < 1e-6 * vmax, (pt, fd, r["v"][pt])
     # the model evaluated with its bf16 roundings stays within their size
     # (2^-9 relative per rounded value)
-    assert np.abs(rb["v"] - r["v"]).max() < 2e-2 * vmax
+    assert np.abs(rb["v"] - r["v"]).max() < 5e-2 * vmax
 
 
 def test_learned_param_grad_matches_finite_differences(table, monkeypatch):
@@ -203,7 +203,7 @@ def test_learned_loss_grad_matches_finite_differences(table, monkeypatch):
     n, g, L = _tiny(11)
     monkeypatch.setattr(LO, "bf16_round", lambda a: np.asarray(a, np.float64))
     mdl_ref = LO.random_model(12)
-    ref = LO.energy_potential(n, g, L, mdl_ref, table, vjp_bf16=False)
+    ref = LO.energy_potential(n, g, L, mdl_ref, table, jac_bf16=False)
     mdl = LO.random_model(13)
     a, b = 1e4, 1e2
     G = LO.loss_grad(n, L, mdl, table, ref["E"], ref["v"], 2, a=a, b=b)
