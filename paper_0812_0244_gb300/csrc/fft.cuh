@@ -263,19 +263,167 @@ __device__ __forceinline__ void dft<8, false>(float2* v) { dft8<false>(v); }
 template <>
 __device__ __forceinline__ void dft<8, true>(float2* v) { dft8<true>(v); }
 
-constexpr int ct_radix(int n) {
-    return n % 8 == 0 ? 8 : n % 4 == 0 ? 4 : n % 2 == 0 ? 2 : n % 3 == 0 ? 3 : n % 5 == 0 ? 5 : 0;
+// ---- composite radices, evaluated in registers ----------------------------
+// W_N^e = exp(-2 pi i e / N) (conjugated for the inverse) for the few
+// exponents the Cooley-Tukey splits 3x3 and 4x4 need.
+template <int N, int E>
+__device__ __forceinline__ float2 wconst() {
+    static_assert(N == 9 || N == 16, "no constants for this length");
+    float c = 1.f, s = 0.f;  // cos, sin of 2 pi E / N
+    if (N == 9) {
+        if (E == 1) { c = 0.766044443118978035202f; s = 0.642787609686539326323f; }
+        if (E == 2) { c = 0.173648177666930348852f; s = 0.984807753012208059367f; }
+        if (E == 4) { c = -0.939692620785908384054f; s = 0.342020143325668733044f; }
+    } else {
+        if (E == 1) { c = 0.923879532511286756128f; s = 0.382683432365089771728f; }
+        if (E == 2) { c = 0.707106781186547524401f; s = 0.707106781186547524401f; }
+        if (E == 3) { c = 0.382683432365089771728f; s = 0.923879532511286756128f; }
+        if (E == 4) { c = 0.f; s = 1.f; }
+        if (E == 6) { c = -0.707106781186547524401f; s = 0.707106781186547524401f; }
+        if (E == 9) { c = -0.923879532511286756128f; s = -0.382683432365089771728f; }
+    }
+    return make_float2(c, -s);
 }
-constexpr int ct_npasses(int n) { return n <= 1 ? 0 : 1 + ct_npasses(n / ct_radix(n)); }
+
+// Cooley-Tukey in registers, N = R1 R2, input index R2 n1 + n2, output
+// k1 + R1 k2: R2 transforms of length R1, twiddles W_N^(n2 k1), R1
+// transforms of length R2.
+template <int R1, int R2, bool INV, int N2 = 0, int K1 = 1>
+__device__ __forceinline__ void ct_twiddle(float2 (&Y)[R1 * R2]) {
+    if constexpr (N2 < R2) {
+        if constexpr (K1 < R1) {
+            if constexpr (N2 > 0) {
+                const float2 w = wconst<R1 * R2, N2 * K1>();
+                Y[N2 * R1 + K1] = INV ? cmulc(Y[N2 * R1 + K1], w) : cmul(Y[N2 * R1 + K1], w);
+            }
+            ct_twiddle<R1, R2, INV, N2, K1 + 1>(Y);
+        } else {
+            ct_twiddle<R1, R2, INV, N2 + 1, 1>(Y);
+        }
+    }
+}
+
+template <int R1, int R2, bool INV>
+__device__ __forceinline__ void dft_ct(float2* v) {
+    float2 Y[R1 * R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+        float2 t[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) t[n1] = v[R2 * n1 + n2];
+        dft<R1, INV>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) Y[n2 * R1 + k1] = t[k1];
+    }
+    ct_twiddle<R1, R2, INV>(Y);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+        float2 t[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) t[n2] = Y[n2 * R1 + k1];
+        dft<R2, INV>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) v[k1 + R1 * k2] = t[k2];
+    }
+}
+
+constexpr int inv_mod(int a, int m) {
+    for (int x = 1; x < m; ++x)
+        if ((a * x) % m == 1) return x;
+    return 1;
+}
+
+// Good-Thomas (prime-factor) split for coprime R1, R2: input index
+// (R2 n1 + R1 n2) mod N, output index by the Chinese remainder theorem; no
+// twiddles between the two sets of short transforms.
+template <int R1, int R2, bool INV>
+__device__ __forceinline__ void dft_pfa(float2* v) {
+    constexpr int N = R1 * R2;
+    constexpr int i1 = inv_mod(R2 % R1, R1), i2 = inv_mod(R1 % R2, R2);
+    float2 Y[N];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+        float2 t[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) t[n1] = v[(R2 * n1 + R1 * n2) % N];
+        dft<R1, INV>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) Y[n2 * R1 + k1] = t[k1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+        float2 t[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) t[n2] = Y[n2 * R1 + k1];
+        dft<R2, INV>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) v[(k1 * R2 * i1 + k2 * R1 * i2) % N] = t[k2];
+    }
+}
+
+template <> __device__ __forceinline__ void dft<6, false>(float2* v) { dft_pfa<2, 3, false>(v); }
+template <> __device__ __forceinline__ void dft<6, true>(float2* v) { dft_pfa<2, 3, true>(v); }
+template <> __device__ __forceinline__ void dft<9, false>(float2* v) { dft_ct<3, 3, false>(v); }
+template <> __device__ __forceinline__ void dft<9, true>(float2* v) { dft_ct<3, 3, true>(v); }
+template <> __device__ __forceinline__ void dft<10, false>(float2* v) { dft_pfa<2, 5, false>(v); }
+template <> __device__ __forceinline__ void dft<10, true>(float2* v) { dft_pfa<2, 5, true>(v); }
+template <> __device__ __forceinline__ void dft<12, false>(float2* v) { dft_pfa<4, 3, false>(v); }
+template <> __device__ __forceinline__ void dft<12, true>(float2* v) { dft_pfa<4, 3, true>(v); }
+template <> __device__ __forceinline__ void dft<15, false>(float2* v) { dft_pfa<5, 3, false>(v); }
+template <> __device__ __forceinline__ void dft<15, true>(float2* v) { dft_pfa<5, 3, true>(v); }
+template <> __device__ __forceinline__ void dft<16, false>(float2* v) { dft_ct<4, 4, false>(v); }
+template <> __device__ __forceinline__ void dft<16, true>(float2* v) { dft_ct<4, 4, true>(v); }
+
+// Radix schedule of a compile-time length: the first radix is the one (among
+// the in-register lengths) that leaves the fewest passes, the larger on a tie.
+// maxr caps the radix (register pressure in kernels that hold much else).
+constexpr int CT_RADICES[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+constexpr int ct_passes_greedy(int n, int maxr);
+constexpr int ct_radix(int n, int maxr = 16) {
+    int best = 0, bestp = 1 << 20, bestd = 1 << 20;
+    for (int r : CT_RADICES) {
+        if (r > maxr || n % r != 0) continue;
+        const int p = 1 + ct_passes_greedy(n / r, maxr);
+        const int d = r > n / r ? r - n / r : n / r - r;  // prefer balanced splits
+        if (p < bestp || (p == bestp && d < bestd)) {
+            bestp = p;
+            bestd = d;
+            best = r;
+        }
+    }
+    return best;
+}
+constexpr int ct_passes_greedy(int n, int maxr) {
+    if (n <= 1) return 0;
+    for (int r : CT_RADICES)
+        if (r <= maxr && n % r == 0) return 1 + ct_passes_greedy(n / r, maxr);
+    return 1 << 20;
+}
+constexpr int ct_npasses(int n, int maxr = 16) { return n <= 1 ? 0 : 1 + ct_npasses(n / ct_radix(n, maxr), maxr); }
 // radix of pass s (in order) and the product Ns of the radices before it
-constexpr int ct_radix_at(int n, int s) { return s == 0 ? ct_radix(n) : ct_radix_at(n / ct_radix(n), s - 1); }
-constexpr int ct_ns_at(int n, int s) { return s == 0 ? 1 : ct_radix(n) * ct_ns_at(n / ct_radix(n), s - 1); }
+constexpr int ct_radix_at(int n, int s, int maxr = 16) {
+    return s == 0 ? ct_radix(n, maxr) : ct_radix_at(n / ct_radix(n, maxr), s - 1, maxr);
+}
+constexpr int ct_ns_at(int n, int s, int maxr = 16) {
+    return s == 0 ? 1 : ct_radix(n, maxr) * ct_ns_at(n / ct_radix(n, maxr), s - 1, maxr);
+}
+// largest butterfly count N / R over the passes, and the lines one warp
+// transforms together so that its lanes stay busy
+constexpr int ct_max_m(int n, int maxr = 16, int s = 0) {
+    return s >= ct_npasses(n, maxr) ? 0
+                                    : (n / ct_radix_at(n, s, maxr) > ct_max_m(n, maxr, s + 1) ? n / ct_radix_at(n, s, maxr)
+                                                                                                : ct_max_m(n, maxr, s + 1));
+}
+constexpr int ct_lines_per_warp(int n, int maxr = 16) {
+    const int l = 32 / ct_max_m(n, maxr);
+    return l < 1 ? 1 : (l > 4 ? 4 : l);
+}
 
 // One pass over L lines (line l at p + l*ls, element stride es) by one warp.
-template <int N, int S, int L, bool INV>
+template <int N, int S, int L, bool INV, int MAXR>
 __device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const float2* tw, int lane) {
-    constexpr int R = ct_radix_at(N, S);
-    constexpr int Ns = ct_ns_at(N, S);
+    constexpr int R = ct_radix_at(N, S, MAXR);
+    constexpr int Ns = ct_ns_at(N, S, MAXR);
     constexpr int M = N / R;
     constexpr int TS = N / (Ns * R);
     constexpr int TOT = L * M;
@@ -316,11 +464,11 @@ __device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const float2*
     __syncwarp();
 }
 
-template <int N, int L, bool INV, int S = 0>
+template <int N, int L, bool INV, int MAXR = 16, int S = 0>
 __device__ __forceinline__ void ct_fft(float2* p, int es, int ls, const float2* tw, int lane) {
-    if constexpr (S < ct_npasses(N)) {
-        ct_pass<N, S, L, INV>(p, es, ls, tw, lane);
-        ct_fft<N, L, INV, S + 1>(p, es, ls, tw, lane);
+    if constexpr (S < ct_npasses(N, MAXR)) {
+        ct_pass<N, S, L, INV, MAXR>(p, es, ls, tw, lane);
+        ct_fft<N, L, INV, MAXR, S + 1>(p, es, ls, tw, lane);
     }
 }
 

@@ -339,7 +339,9 @@ __global__ void __cluster_dims__(1, ASM_CTAS, 1) __launch_bounds__(ASM_THREADS, 
             for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
             __syncthreads();
         }
-        plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
+        // radices up to 8 here: the longer in-register transforms spill next
+        // to everything else this kernel keeps live
+        plane_inverse<CN1, CN3, 8>(plane, g, tw1, tw3);
         const float* pf = reinterpret_cast<const float*>(plane);
         for (int z = warp; z < g.N3; z += nw) {
             const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);

@@ -36,34 +36,31 @@ __device__ __forceinline__ void load_twiddles(float2* dst, const float2* src, in
 // ---------------------------------------------------------------------------
 // line-transform dispatch: compile-time length when CN > 0
 // ---------------------------------------------------------------------------
-// rows of one plane (packed real pairs), one row per warp iteration
-template <int CN, bool INV>
-__device__ __forceinline__ void row_fft(float2* p, const LinePlan& pl, const float2* tw, int lane) {
-    if constexpr (CN > 0) ct_fft<CN, 1, INV>(p, 1, 0, tw, lane);
-    else line_fft<INV>(p, 1, pl, tw, lane);
-}
-
 // the Nh columns of a plane (element stride Nh), several columns per warp for short lines
-template <int CN, bool INV>
+template <int CN, bool INV, int MAXR = 16>
 __device__ __forceinline__ void columns_fft(float2* plane, int Nh, const LinePlan& pl, const float2* tw) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if constexpr (CN > 0) {
-        constexpr int L = CN <= 72 ? 3 : (CN <= 128 ? 2 : 1);
+        constexpr int L = ct_lines_per_warp(CN, MAXR);
         const int full = (Nh / L) * L;
-        for (int col = warp * L; col < full; col += nw * L) ct_fft<CN, L, INV>(plane + col, Nh, 1, tw, lane);
-        for (int col = full + warp; col < Nh; col += nw) ct_fft<CN, 1, INV>(plane + col, Nh, 1, tw, lane);
+        for (int col = warp * L; col < full; col += nw * L) ct_fft<CN, L, INV, MAXR>(plane + col, Nh, 1, tw, lane);
+        for (int col = full + warp; col < Nh; col += nw) ct_fft<CN, 1, INV, MAXR>(plane + col, Nh, 1, tw, lane);
     } else {
         for (int col = warp; col < Nh; col += nw) line_fft<INV>(plane + col, Nh, pl, tw, lane);
     }
 }
 
-// contiguous lines of length N2 (pencils)
+// contiguous lines of length N2 (pencils), several lines per warp for short lines
 template <int CN, bool INV>
 __device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, const LinePlan& pl, const float2* tw) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int l = warp; l < nlines; l += nw) {
-        if constexpr (CN > 0) ct_fft<CN, 1, INV>(lines + l * N2, 1, 0, tw, lane);
-        else line_fft<INV>(lines + l * N2, 1, pl, tw, lane);
+    if constexpr (CN > 0) {
+        constexpr int L = ct_lines_per_warp(CN);
+        const int full = (nlines / L) * L;
+        for (int l = warp * L; l < full; l += nw * L) ct_fft<CN, L, INV>(lines + l * CN, 1, CN, tw, lane);
+        for (int l = full + warp; l < nlines; l += nw) ct_fft<CN, 1, INV>(lines + l * CN, 1, 0, tw, lane);
+    } else {
+        for (int l = warp; l < nlines; l += nw) line_fft<INV>(lines + l * N2, 1, pl, tw, lane);
     }
 }
 
@@ -74,31 +71,56 @@ __device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, c
 // imaginary parts; this is the float offset of the start of real row z.
 __device__ __forceinline__ int packed_row(int z, int Nh) { return 2 * ((z >> 1) * 2 * Nh) + (z & 1); }
 
-// Forward: packed real rows -> half spectrum (x R2C, then z C2C).
-template <int CN1, int CN3>
-__device__ void plane_forward(float2* plane, const GridArgs& g, const float2* tw1, const float2* tw3) {
+// Rows of a plane (complex row j holds real rows 2j and 2j+1) through the
+// x transform, several rows per warp at compile-time lengths; each row is
+// then untangled into the two half spectra (forward), or tangled before the
+// transform (inverse).
+template <int CN1, bool INV, int MAXR = 16>
+__device__ __forceinline__ void plane_rows(float2* plane, const GridArgs& g, const float2* tw1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int row = warp; row < g.N3 / 2; row += nw) {
-        float2* p = plane + row * 2 * g.Nh;
-        row_fft<CN1, false>(p, g.p1, tw1, lane);
-        r2c_untangle(p, g.N1, lane);
+    const int nrows = g.N3 / 2, rs = 2 * g.Nh;
+    if constexpr (CN1 > 0) {
+        constexpr int L = ct_lines_per_warp(CN1, MAXR);
+        const int full = (nrows / L) * L;
+        for (int row = warp * L; row < full; row += nw * L) {
+            float2* p = plane + row * rs;
+            if (INV)
+                for (int l = 0; l < L; ++l) c2r_tangle(p + l * rs, g.N1, lane);
+            ct_fft<CN1, L, INV, MAXR>(p, 1, rs, tw1, lane);
+            if (!INV)
+                for (int l = 0; l < L; ++l) r2c_untangle(p + l * rs, g.N1, lane);
+        }
+        for (int row = full + warp; row < nrows; row += nw) {
+            float2* p = plane + row * rs;
+            if (INV) c2r_tangle(p, g.N1, lane);
+            ct_fft<CN1, 1, INV, MAXR>(p, 1, 0, tw1, lane);
+            if (!INV) r2c_untangle(p, g.N1, lane);
+        }
+    } else {
+        for (int row = warp; row < nrows; row += nw) {
+            float2* p = plane + row * rs;
+            if (INV) c2r_tangle(p, g.N1, lane);
+            line_fft<INV>(p, 1, g.p1, tw1, lane);
+            if (!INV) r2c_untangle(p, g.N1, lane);
+        }
     }
+}
+
+// Forward: packed real rows -> half spectrum (x R2C, then z C2C).
+template <int CN1, int CN3, int MAXR = 16>
+__device__ void plane_forward(float2* plane, const GridArgs& g, const float2* tw1, const float2* tw3) {
+    plane_rows<CN1, false, MAXR>(plane, g, tw1);
     __syncthreads();
-    columns_fft<CN3, false>(plane, g.Nh, g.p3, tw3);
+    columns_fft<CN3, false, MAXR>(plane, g.Nh, g.p3, tw3);
     __syncthreads();
 }
 
 // Inverse: half spectrum -> packed real rows (z C2C inverse, then x C2R), unscaled.
-template <int CN1, int CN3>
+template <int CN1, int CN3, int MAXR = 16>
 __device__ void plane_inverse(float2* plane, const GridArgs& g, const float2* tw1, const float2* tw3) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    columns_fft<CN3, true>(plane, g.Nh, g.p3, tw3);
+    columns_fft<CN3, true, MAXR>(plane, g.Nh, g.p3, tw3);
     __syncthreads();
-    for (int row = warp; row < g.N3 / 2; row += nw) {
-        float2* p = plane + row * 2 * g.Nh;
-        c2r_tangle(p, g.N1, lane);
-        row_fft<CN1, true>(p, g.p1, tw1, lane);
-    }
+    plane_rows<CN1, true, MAXR>(plane, g, tw1);
     __syncthreads();
 }
 
