@@ -377,6 +377,24 @@ def main():
     except Exception:
         cufft_ms = None
 
+    # the same call with the finite-difference gradient (the paper's own
+    # operator; the chain term is a stencil instead of three transforms)
+    fd_ms = None
+    try:
+        Kf = min(K, 100)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * Kf)]
+        for _ in range(3):
+            ctx.energy_potential_fd(n, g, E, v)
+        for i in range(Kf):
+            flush.zero_()
+            ev[2 * i].record(stream)
+            ctx.energy_potential_fd(n, g, E, v)
+            ev[2 * i + 1].record(stream)
+        torch.cuda.synchronize()
+        fd_ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(Kf)) / Kf
+    except Exception:
+        fd_ms = None
+
     # learned reduced basis (M = 8 channels) on the same density: the trained
     # model if one is stored in the package, else its initialisation
     learned = None
@@ -434,6 +452,9 @@ def main():
                                         % (params.Nq + 3, params.Nq + 1)},
             "clocks": clocks,
             "learned_m8": learned,
+            "fd_gradient_variant": {"ms_per_step": fd_ms, "value": (N / (fd_ms * 1e-3)) if fd_ms else None,
+                                    "unit": UNIT, "what": "vdw_energy_potential_fd: central-difference gradient, "
+                                                          "chain term by stencil"},
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu

@@ -134,6 +134,17 @@ int vdw_plan(vdw_handle h, int n1, int n2, int n3, const double L[3]);
 int vdw_energy_potential(vdw_handle h, const float* n, const float* grad,
                          double* E, float* v, float* w, void* stream);
 
+/* The same energy with the finite-difference gradient of the paper's own
+ * implementation: grad n by second-order central differences on the periodic
+ * grid, (f(r + h_c e_c) - f(r - h_c e_c)) / (2 h_c).  grad (device [3][N])
+ * must hold that gradient, or be NULL for the library to compute it.  v (or
+ * NULL for the energy alone) is v_nl of Eq. (Vi) under this operator:
+ * v = v_loc - sum_c D_c w_c with D the same stencil (it is antisymmetric), so
+ * v is the exact derivative of E(n, D n); the chain term costs one stencil
+ * pass instead of the three spectral transforms of vdw_energy_potential.
+ * Asynchronous on stream. */
+int vdw_energy_potential_fd(vdw_handle h, const float* n, const float* grad, double* E, float* v, void* stream);
+
 /* The same computation on host buffers (n[N], grad[3N] in; E[3], v[N] out):
  * copies the inputs to context-owned device buffers (allocated on first use),
  * runs vdw_energy_potential with the full potential, copies E and v back and

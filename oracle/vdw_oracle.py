@@ -552,6 +552,25 @@ def spectral_divergence(w, L):
     return np.real(np.fft.ifftn(acc))
 
 
+def stencil_gradient(n, L):
+    """grad n by second-order central differences on the periodic grid, the
+    finite-difference gradient the paper's implementation uses (text before
+    Eq. Vi): (f(r + h_c e_c) - f(r - h_c e_c)) / (2 h_c)."""
+    L = check_cell(L)
+    N3, N2, N1 = n.shape
+    h = (L[0] / N1, L[1] / N2, L[2] / N3)
+    return np.stack([(np.roll(n, -1, axis=2) - np.roll(n, 1, axis=2)) / (2 * h[0]),
+                     (np.roll(n, -1, axis=1) - np.roll(n, 1, axis=1)) / (2 * h[1]),
+                     (np.roll(n, -1, axis=0) - np.roll(n, 1, axis=0)) / (2 * h[2])])
+
+
+def stencil_divergence(w, L):
+    """sum_c D_c w_c with the central-difference operator of stencil_gradient.
+    That operator is antisymmetric, so the chain term of Eq. (Vi),
+    sum_j w_j . dgrad_j/dn_i = (D^T w)_i, equals minus this divergence."""
+    return sum(stencil_gradient(w[c], L)[c] for c in range(3))
+
+
 # --------------------------------------------------------------------------
 # Pointwise part: q, theta_a and their derivatives
 # --------------------------------------------------------------------------
@@ -606,7 +625,7 @@ def contract(theta_hat, Khat):
     return u.reshape(theta_hat.shape), esum
 
 
-def energy_potential(n, grad, cell, T: KernelTable, kernel_hat=None, want_v=True):
+def energy_potential(n, grad, cell, T: KernelTable, kernel_hat=None, want_v=True, gradient="spectral"):
     """E_c^nl and v_nl on the periodic grid.
 
     Steps in the paper's order: theta_a = n p_a(q0) (after Eq. Eoffk);
@@ -619,6 +638,10 @@ def energy_potential(n, grad, cell, T: KernelTable, kernel_hat=None, want_v=True
 
     Discrete conventions (reading): theta(G) = (1/N) sum_i theta_i
     exp(-i G.r_i), G = 2 pi m / L per axis, m in numpy's FFT order.
+
+    gradient: "spectral" (grad n = D n with the spectral D) or "stencil"
+    (grad n from central differences, stencil_gradient); v is the exact
+    derivative of E under that operator.
 
     kernel_hat: optional callable (s, e) -> (Nq, Nq, e-s) replacing
     phi_ab(|G|) on the flattened G index range [s, e) (used by the identity
@@ -662,7 +685,9 @@ def energy_potential(n, grad, cell, T: KernelTable, kernel_hat=None, want_v=True
     v_loc = np.where(pw["ok"], v_loc, 0.0)
     g = nn * S1 * pw["dq_dg"] + dE_g
     w = np.where(pw["ok"], g, 0.0)[None] * np.asarray(grad, np.float64)
-    v = v_loc - spectral_divergence(w, L)
+    # the chain term of Eq. (Vi) under the gradient operator the caller used
+    div = stencil_divergence(w, L) if gradient == "stencil" else spectral_divergence(w, L)
+    v = v_loc - div
     out.update(v=v, v_loc=v_loc, w=w, u=u)
     return out
 

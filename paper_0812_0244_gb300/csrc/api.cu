@@ -210,6 +210,18 @@ int vdw_energy_potential(vdw_handle c, const float* n, const float* grad, double
     return pipeline_run(c, n, grad, E, v, w, (cudaStream_t)stream);
 }
 
+int vdw_energy_potential_fd(vdw_handle c, const float* n, const float* grad, double* E, float* v, void* stream) {
+    if (!c || !n) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    if (!grad) {
+        if (!c->d_gtmp) VDW_CUDA(cudaMalloc(&c->d_gtmp, sizeof(float) * 3 * (size_t)c->g.N));
+        const int rc = pipeline_stencil_gradient(c, n, c->d_gtmp, (cudaStream_t)stream);
+        if (rc) return rc;
+        grad = c->d_gtmp;
+    }
+    return pipeline_run(c, n, grad, E, v, nullptr, (cudaStream_t)stream, 1);
+}
+
 int vdw_energy_potential_host(vdw_handle c, const float* n, const float* grad, double* E, float* v, void* stream) {
     if (!c || !n || !grad) return VDW_ERR_ARG;
     if (!c->planned) return VDW_ERR_STATE;

@@ -143,7 +143,9 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // pipeline launchers (pipeline.cu)
 int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w,
-                 cudaStream_t s);
+                 cudaStream_t s, int fd = 0);
+// central-difference gradient of a field (into grad [3][N])
+int pipeline_stencil_gradient(vdw_ctx* c, const float* f, float* grad, cudaStream_t s);
 int pipeline_plan_check(vdw_ctx* c, size_t* smem_plane, size_t* smem_pencil, size_t* smem_assemble,
                         size_t* smem_div);
 int pipeline_make_twiddles(vdw_ctx* c);

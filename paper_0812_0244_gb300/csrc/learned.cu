@@ -63,10 +63,10 @@ __device__ __forceinline__ void silu_both(float z, float& f, float& fp) {
     fp = s * (1.f + z * (1.f - s));
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+// two values -> bf16x2 (a in the low half), one conversion instruction
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
-    const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
-    return lo | (hi << 16);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
 }
 // 8 values -> one 16-byte core-matrix row
 __device__ __forceinline__ void store8_bf16(uint16_t* dst, const float* v) {

@@ -508,6 +508,51 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_div_final(const float2* __
 }
 
 // ---------------------------------------------------------------------------
+// finite-difference gradient (the paper's own): central differences on the
+// periodic grid, and the chain term of Eq. (Vi) as the transposed stencil
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_stencil_gradient(const float* __restrict__ f, GridArgs g, float3 ih2,
+                                                          float* __restrict__ grad) {
+    const long long N = g.N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.N1);
+        const long long r = i / g.N1;
+        const int y = (int)(r % g.N2), z = (int)(r / g.N2);
+        const long long rowz = (long long)z * g.N2;
+        const long long xm = i - x + (x == 0 ? g.N1 - 1 : x - 1), xp = i - x + (x == g.N1 - 1 ? 0 : x + 1);
+        const long long ym = ((rowz + (y == 0 ? g.N2 - 1 : y - 1)) * g.N1) + x;
+        const long long yp = ((rowz + (y == g.N2 - 1 ? 0 : y + 1)) * g.N1) + x;
+        const long long zm = (((long long)(z == 0 ? g.N3 - 1 : z - 1) * g.N2 + y) * g.N1) + x;
+        const long long zp = (((long long)(z == g.N3 - 1 ? 0 : z + 1) * g.N2 + y) * g.N1) + x;
+        grad[i] = (f[xp] - f[xm]) * ih2.x;
+        grad[N + i] = (f[yp] - f[ym]) * ih2.y;
+        grad[2 * N + i] = (f[zp] - f[zm]) * ih2.z;
+    }
+}
+
+// v -= sum_c D_c (g grad_c n): with the antisymmetric central-difference D,
+// D^T w = -D w (w = g grad n, g from the assembly)
+__global__ void __launch_bounds__(256) k_stencil_div_sub(const float* __restrict__ gg, const float* __restrict__ grad,
+                                                         GridArgs g, float3 ih2, float* __restrict__ v) {
+    const long long N = g.N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % g.N1);
+        const long long r = i / g.N1;
+        const int y = (int)(r % g.N2), z = (int)(r / g.N2);
+        const long long rowz = (long long)z * g.N2;
+        const long long xm = i - x + (x == 0 ? g.N1 - 1 : x - 1), xp = i - x + (x == g.N1 - 1 ? 0 : x + 1);
+        const long long ym = ((rowz + (y == 0 ? g.N2 - 1 : y - 1)) * g.N1) + x;
+        const long long yp = ((rowz + (y == g.N2 - 1 ? 0 : y + 1)) * g.N1) + x;
+        const long long zm = (((long long)(z == 0 ? g.N3 - 1 : z - 1) * g.N2 + y) * g.N1) + x;
+        const long long zp = (((long long)(z == g.N3 - 1 ? 0 : z + 1) * g.N2 + y) * g.N1) + x;
+        const float d = (gg[xp] * grad[xp] - gg[xm] * grad[xm]) * ih2.x +
+                        (gg[yp] * grad[N + yp] - gg[ym] * grad[N + ym]) * ih2.y +
+                        (gg[zp] * grad[2 * N + zp] - gg[zm] * grad[2 * N + zm]) * ih2.z;
+        v[i] -= d;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // energy: fixed-order FP64 reduction of the block partials
 // ---------------------------------------------------------------------------
 __global__ void k_energy_final(const double* __restrict__ epart, int nb0, int nb2, double s0, double s2,
@@ -633,8 +678,21 @@ static int launch_contract_nq(vdw_ctx* c, cudaStream_t s, int write_back) {
     return VDW_OK;
 }
 
+static float3 stencil_ih2(const vdw_ctx* c) {
+    return make_float3((float)(c->g.N1 / (2.0 * c->L[0])), (float)(c->g.N2 / (2.0 * c->L[1])),
+                       (float)(c->g.N3 / (2.0 * c->L[2])));
+}
+static int stencil_blocks(const GridArgs& g) { return (int)std::min<long long>((g.N + 255) / 256, 8192); }
+
+int pipeline_stencil_gradient(vdw_ctx* c, const float* f, float* grad, cudaStream_t s) {
+    k_stencil_gradient<<<stencil_blocks(c->g), 256, 0, s>>>(f, c->g, stencil_ih2(c), grad);
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
 template <int CN1, int CN2, int CN3>
-static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s) {
+static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s,
+                     int fd) {
     const GridArgs& g = c->g;
     const PointParams& P = c->pp;
     const bool want_pot = (v != nullptr) || (w != nullptr);
@@ -674,10 +732,15 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
         k_assemble<CN1, CN3><<<dim3(g.N2, ASM_CTAS), ASM_THREADS, sa, s>>>(
             c->d_spec, n, grad, c->d_t, c->d_k, g, P, c->d_tw, v, w, c->d_gg, mode, c->acc_global ? c->d_acc : nullptr,
             c->tk_smem, c->asm_dbuf, c->d_flags);
-        if (mode == 1)
+        if (mode == 1 && fd) {
+            // finite-difference gradient: the chain term is a stencil, no transforms
+            mark(4);
+            k_stencil_div_sub<<<stencil_blocks(g), 256, 0, s>>>(c->d_gg, grad, g, stencil_ih2(c), v);
+            mark(6);
+        } else if (mode == 1)
             k_w_planes<CN1, CN3><<<dim3(g.N2, 3), PLANE_THREADS, sp, s>>>(c->d_gg, grad, g, c->d_tw, c->d_wspec);
-        mark(4);
-        if (mode == 1) {
+        if (!(mode == 1 && fd)) mark(4);
+        if (mode == 1 && !fd) {
             const size_t sd = smem_pencil_run(g, 3, DIV_COLS);
             k_pencil_div<CN2><<<(g.ncols + DIV_COLS - 1) / DIV_COLS, 256, sd, s>>>(c->d_wspec, g, c->d_tw, DIV_COLS);
             mark(5);
@@ -795,11 +858,12 @@ int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, dou
     return VDW_OK;
 }
 
-int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s) {
+int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s,
+                 int fd) {
     const GridArgs& g = c->g;
-    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) return run_sized<180, 180, 72>(c, n, grad, E, v, w, s);
-    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) return run_sized<256, 256, 96>(c, n, grad, E, v, w, s);
-    return run_sized<0, 0, 0>(c, n, grad, E, v, w, s);
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) return run_sized<180, 180, 72>(c, n, grad, E, v, w, s, fd);
+    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) return run_sized<256, 256, 96>(c, n, grad, E, v, w, s, fd);
+    return run_sized<0, 0, 0>(c, n, grad, E, v, w, s, fd);
 }
 
 }  // namespace vdw

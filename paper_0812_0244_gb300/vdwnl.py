@@ -71,6 +71,7 @@ class Params:
 
 
 EXPORTS = ["vdw_params_default", "vdw_kernel_table", "vdw_create", "vdw_plan", "vdw_energy_potential",
+           "vdw_energy_potential_fd",
            "vdw_energy_potential_host", "vdw_last_invalid_points", "vdw_profile_enable", "vdw_profile_read",
            "vdw_delta_energy_noalloc", "vdw_spectral_gradient", "vdw_learned_param_count", "vdw_learned_load",
            "vdw_learned_energy_potential", "vdw_learned_param_grad", "vdw_learned_fit_grad",
@@ -99,6 +100,7 @@ def lib():
     L.vdw_plan.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
     L.vdw_energy_potential.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.vdw_energy_potential_host.argtypes = [vp, fp, fp, dp, fp, vp]
+    L.vdw_energy_potential_fd.argtypes = [vp, vp, vp, vp, vp, vp]
     L.vdw_last_invalid_points.argtypes = [vp, P(ctypes.c_longlong)]
     L.vdw_profile_enable.argtypes = [vp, ctypes.c_int]
     L.vdw_profile_read.argtypes = [vp, fp]
@@ -226,6 +228,21 @@ class VdwNL:
         _check(lib().vdw_energy_potential(self._h, ptr(n), ptr(grad), ptr(E), ptr(v), ptr(w),
                                           _stream_handle(stream)), "vdw_energy_potential")
         return E, v, w
+
+    def energy_potential_fd(self, n, grad=None, E=None, v=None, stream=None):
+        """vdw_energy_potential_fd: central-difference gradient (given, or
+        computed by the library when grad is None); returns (E, v)."""
+        import torch
+        _cuda_f32(n, self.shape)
+        if grad is not None:
+            _cuda_f32(grad, (3,) + self.shape)
+        if E is None:
+            E = torch.empty(3, dtype=torch.float64, device=n.device)
+        if v is not None:
+            _cuda_f32(v, self.shape)
+        _check(lib().vdw_energy_potential_fd(self._h, _ptr(n), _ptr(grad), _ptr(E), _ptr(v), _stream_handle(stream)),
+               "vdw_energy_potential_fd")
+        return E, v
 
     def compute(self, n, grad, want_v=True, want_w=False, stream=None):
         """Allocate outputs and run; returns (E[3] float64 device tensor, v, w)."""

@@ -153,3 +153,29 @@ def test_nanotube_cell_full_size(torch_cuda, ctx, table):
     assert abs(E[0] - ref["E"]) <= E_TOL, (E, ref["E"])
     assert abs(E[1] - ref["E_soft"]) <= E_TOL
     assert np.max(np.abs(v - ref["v"])) <= V_REL * np.abs(ref["v"]).max()
+
+
+@pytest.mark.parametrize("shape", [(24, 24, 24), (72, 180, 180)], ids=["two_atom_24", "tube_180x180x72"])
+def test_finite_difference_gradient_variant(torch_cuda, table, shape):
+    """vdw_energy_potential_fd against the oracle with the same central-
+    difference gradient; grad = NULL gives the library's own stencil."""
+    torch = torch_cuda
+    from paper_0812_0244_gb300 import vdwnl
+    d = S.two_atom_density(9, shape=shape) if shape[0] == 24 else S.tube_density(4)
+    n32 = d["n"].astype(np.float32)
+    L = d["L"]
+    g = O.stencil_gradient(n32.astype(np.float64), L)
+    ctx = vdwnl.VdwNL(vdwnl.Params()).plan(n32.shape, L)
+    nt = torch.tensor(n32, device="cuda")
+    gt = torch.tensor(g.astype(np.float32), device="cuda")
+    v = torch.empty_like(nt)
+    E, _ = ctx.energy_potential_fd(nt, gt, v=v)
+    ref = O.energy_potential(n32.astype(np.float64), g.astype(np.float32).astype(np.float64), L, table,
+                             gradient="stencil")
+    assert abs(float(E[0]) - ref["E"]) <= E_TOL
+    vv = v.cpu().numpy()
+    assert np.abs(vv - ref["v"]).max() <= V_REL * np.abs(ref["v"]).max()
+    # the library's own stencil gradient: the same pipeline on its own result
+    v2 = torch.empty_like(nt)
+    E2, _ = ctx.energy_potential_fd(nt, None, v=v2)
+    assert abs(float(E2[0]) - ref["E"]) <= 1e-6

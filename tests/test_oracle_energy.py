@@ -160,3 +160,38 @@ def test_factorisation_error_is_small(table):
     E_fac = O.factored_bruteforce_energy(theta, K, dOmega)
     E_unf = O.unfactored_bruteforce_energy(n, g, L, table)
     assert abs(E_fac / E_unf - 1) < 2e-2, (E_fac, E_unf)
+
+
+def test_stencil_potential_matches_fd_of_energy(table):
+    """With grad n from central differences, v = v_loc - (stencil divergence
+    of w) is the exact derivative of E(n, D_fd n): central differences of E
+    at single points agree with it."""
+    n, _, L = small_density(5, shape=(8, 6, 10), L=(8.0, 7.0, 9.0))
+    E0 = lambda m: O.energy(m, O.stencil_gradient(m, L), L, table)
+    r = O.energy_potential(n, O.stencil_gradient(n, L), L, table, gradient="stencil")
+    v = r["v"]
+    dOmega = np.prod(L) / n.size
+    rng = np.random.default_rng(6)
+    for i in rng.choice(n.size, 6, replace=False):
+        pt = np.unravel_index(i, n.shape)
+        h = 1e-4 * n[pt]
+        m1, m2 = n.copy(), n.copy()
+        m1[pt] += h
+        m2[pt] -= h
+        fdv = (E0(m1) - E0(m2)) / (2 * h * dOmega)
+        assert abs(fdv - v[pt]) < 1e-6 * np.abs(v).max(), (pt, fdv, v[pt])
+
+
+def test_stencil_gradient_of_a_sine():
+    """The central difference of sin(k x) on the periodic grid is, in closed
+    form, cos(k x) sin(k h)/h; the other components vanish."""
+    shape = (6, 8, 10)
+    L = np.array([5.0, 6.0, 7.0])
+    z, y, x = np.meshgrid(*(np.arange(N) * Ld / N for N, Ld in zip(shape, L[::-1])), indexing="ij")
+    k = 2 * np.pi / L[0]
+    f = np.sin(k * x)
+    g = O.stencil_gradient(f, L)
+    h = L[0] / shape[2]
+    np.testing.assert_allclose(g[0], k * np.cos(k * x) * np.sin(k * h) / (k * h), atol=1e-12)
+    np.testing.assert_allclose(g[1], 0.0, atol=1e-12)
+    np.testing.assert_allclose(g[2], 0.0, atol=1e-12)
