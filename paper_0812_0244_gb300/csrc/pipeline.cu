@@ -31,7 +31,11 @@
 
 namespace vdw {
 
-constexpr int CONTRACT_THREADS = 288;  // block size bound of the contraction kernel
+// Contraction blocks: at most this many threads, two blocks per SM (the
+// table fetches are latency bound, so resident warps matter more than
+// columns per block: at 180 x 180 x 72, 2 columns x 192 threads x 2 blocks
+// ran in 0.70 ms against 0.87 ms for 3 columns x 288 threads x 1 block).
+constexpr int CONTRACT_THREADS = 192;
 
 // ---------------------------------------------------------------------------
 // P0: pointwise
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_theta_plane(const float* _
 // points' u accumulators in registers and reads their theta values from the
 // block's shared lines (only it reads those two positions).
 template <int NQ, int CN2>
-__global__ void __launch_bounds__(CONTRACT_THREADS, 1) k_pencil_contract(float2* __restrict__ spec, GridArgs g,
+__global__ void __launch_bounds__(CONTRACT_THREADS, 2) k_pencil_contract(float2* __restrict__ spec, GridArgs g,
                                                                        const float4* __restrict__ kcoef,
                                                                        const float2* __restrict__ tw,
                                                                        double* __restrict__ epart, int C,
@@ -617,9 +621,11 @@ static const int DIV_COLS = DIV_COLS_CT;
 int pipeline_plan_check(vdw_ctx* c, size_t* sp, size_t* spen, size_t* sa, size_t* sd) {
     const GridArgs& g = c->g;
     const int nq = c->p.Nq;
-    // columns per pencil block: as many as fit in ~110 KB, at most 8
+    // columns per pencil block: at most 8, within ~110 KB of shared memory
+    // (two blocks per SM), and one (+-y pair) task per thread
+    const int npy = g.N2 / 2 + 1;
     int C = 8;
-    while (C > 1 && smem_pencil(g, nq, C) > 110 * 1024) --C;
+    while (C > 1 && (smem_pencil(g, nq, C) > 110 * 1024 || C * npy > CONTRACT_THREADS)) --C;
     c->pencil_cols = C;
     *sp = smem_plane(g);
     *spen = smem_pencil_run(g, nq, C);
