@@ -145,6 +145,17 @@ int vdw_energy_potential(vdw_handle h, const float* n, const float* grad,
  * Asynchronous on stream. */
 int vdw_energy_potential_fd(vdw_handle h, const float* n, const float* grad, double* E, float* v, void* stream);
 
+/* The whole exchange-correlation functional of Eq. (Exc),
+ * E_xc = E_x^GGA + E_c^LDA + E_c^nl, with Dion et al.'s partners: revPBE
+ * exchange (kappa = 1.245, mu = 0.066725 pi^2/3) and the Perdew-Wang LDA
+ * correlation.  E (device FP64 [4]) receives {E_xc, E_c^nl, E_x, E_c^LDA};
+ * v (device [N] or NULL) the potential of E_xc.  fd = 0: grad n is the
+ * spectral gradient (as vdw_energy_potential), fd = 1: central differences
+ * (as vdw_energy_potential_fd); grad may be NULL for the library to compute
+ * it.  Asynchronous on stream. */
+int vdw_xc_energy_potential(vdw_handle h, const float* n, const float* grad, double* E, float* v, int fd,
+                            void* stream);
+
 /* The same computation on host buffers (n[N], grad[3N] in; E[3], v[N] out):
  * copies the inputs to context-owned device buffers (allocated on first use),
  * runs vdw_energy_potential with the full potential, copies E and v back and

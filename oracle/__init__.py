@@ -15,5 +15,7 @@ dion.c       the Dion kernel phi(d1, d2) by direct double quadrature (compiled
 learned      the learned reduced basis (a network's channel weights and a
              learned pair kernel in place of the splines), its potential,
              parameter gradients and training loss.
+semilocal    the semilocal partner terms of Eq. (Exc): revPBE exchange and
+             LDA correlation, and the total E_xc with its potential.
 """
 from .vdw_oracle import *  # noqa: F401,F403

@@ -49,8 +49,10 @@ static void free_plan(vdw_ctx* c) {
     c->d_gtmp = nullptr;
     cudaFree(c->d_gg);
     cudaFree(c->d_flags);
+    cudaFree(c->d_xc);
     c->d_gg = nullptr;
     c->d_flags = nullptr;
+    c->d_xc = nullptr;
     learned_free(c);
     c->planned = 0;
 }
@@ -180,6 +182,7 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     VDW_CUDA(cudaMalloc(&c->d_invalid, sizeof(unsigned long long)));
     VDW_CUDA(cudaMalloc(&c->d_gg, sizeof(float) * (size_t)g.N));
     VDW_CUDA(cudaMalloc(&c->d_flags, sizeof(int)));
+    VDW_CUDA(cudaMalloc(&c->d_xc, sizeof(double) * (4 + 2 * 1024)));
     VDW_CUDA(cudaMemset(c->d_flags, 0, sizeof(int)));
     VDW_CUDA(cudaMemset(c->d_invalid, 0, sizeof(unsigned long long)));
     if (c->acc_global) VDW_CUDA(cudaMalloc(&c->d_acc, sizeof(float) * 2 * 4 * g.N));
@@ -220,6 +223,22 @@ int vdw_energy_potential_fd(vdw_handle c, const float* n, const float* grad, dou
         grad = c->d_gtmp;
     }
     return pipeline_run(c, n, grad, E, v, nullptr, (cudaStream_t)stream, 1);
+}
+
+int vdw_xc_energy_potential(vdw_handle c, const float* n, const float* grad, double* E, float* v, int fd,
+                            void* stream) {
+    if (!c || !n || !E) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!grad) {
+        if (!c->d_gtmp) VDW_CUDA(cudaMalloc(&c->d_gtmp, sizeof(float) * 3 * (size_t)c->g.N));
+        const int rc = fd ? pipeline_stencil_gradient(c, n, c->d_gtmp, s) : vdw_spectral_gradient(c, n, c->d_gtmp, stream);
+        if (rc) return rc;
+        grad = c->d_gtmp;
+    }
+    int rc = pipeline_run(c, n, grad, c->d_xc, v, nullptr, s, fd ? 1 : 0, 1);
+    if (rc) return rc;
+    return pipeline_xc_final(c, E, s);
 }
 
 int vdw_energy_potential_host(vdw_handle c, const float* n, const float* grad, double* E, float* v, void* stream) {

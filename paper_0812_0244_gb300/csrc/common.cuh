@@ -108,6 +108,7 @@ struct vdw_ctx {
     int asm_dbuf;               // assembly double-buffers its planes (bulk asynchronous copies)
     float* d_gg;                // [N] g of w = g grad n (assembly -> w plane transforms)
     int* d_flags;               // [1] set when a bounded wait in a kernel gave up
+    double* d_xc;               // [4 + 2 XC_BLOCKS] nonlocal E and semilocal partial sums
     float* d_acc;               // [4][2N] their scratch (only when acc_global)
     // buffers of the host-pointer entry point (allocated on first use)
     float* d_in;                // [4N]
@@ -143,7 +144,9 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // pipeline launchers (pipeline.cu)
 int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w,
-                 cudaStream_t s, int fd = 0);
+                 cudaStream_t s, int fd = 0, int xc = 0);
+// E[4] of the functional from the nonlocal energy (d_xc[0]) and the semilocal sums
+int pipeline_xc_final(vdw_ctx* c, double* E, cudaStream_t s);
 // central-difference gradient of a field (into grad [3][N])
 int pipeline_stencil_gradient(vdw_ctx* c, const float* f, float* grad, cudaStream_t s);
 int pipeline_plan_check(vdw_ctx* c, size_t* smem_plane, size_t* smem_pencil, size_t* smem_assemble,

@@ -36,6 +36,7 @@ namespace vdw {
 // columns per block: at 180 x 180 x 72, 2 columns x 192 threads x 2 blocks
 // ran in 0.70 ms against 0.87 ms for 3 columns x 288 threads x 1 block).
 constexpr int CONTRACT_THREADS = 192;
+constexpr int XC_BLOCKS = 1024;  // blocks (and partial-sum slots) of the semilocal kernel
 
 // ---------------------------------------------------------------------------
 // P0: pointwise
@@ -557,6 +558,80 @@ __global__ void __launch_bounds__(256) k_stencil_div_sub(const float* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// semilocal partner terms of Eq. (Exc): revPBE exchange (kappa = 1.245,
+// mu = 0.066725 pi^2/3) and LDA correlation (the PW92 eps_c of q0)
+// ---------------------------------------------------------------------------
+// Adds de/dn to v and the coefficient of grad n in de/d(grad n) to g (so that
+// the divergence stage takes it with the nonlocal w); FP64 block sums of
+// e_x and e_c into epart[block] and epart[nb + block].
+__global__ void __launch_bounds__(256) k_semilocal(const float* __restrict__ n, const float* __restrict__ grad,
+                                                   long long N, float n_min, float* __restrict__ v,
+                                                   float* __restrict__ gg, double* __restrict__ epart) {
+    __shared__ double red[32];
+    const float PI_F = 3.14159265358979f;
+    const float KAPPA = 1.245f, MU = 0.066725f * PI_F * PI_F / 3.f;
+    const float AX = -0.75f * 0.98474502184269641f;  // -(3/4) (3/pi)^(1/3)
+    const float A = 0.031091f, a1 = 0.21370f;
+    const float b1 = 7.5957f, b2 = 3.5876f, b3 = 1.6382f, b4 = 0.49294f;
+    double sx = 0.0, sc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const float ni = n[i];
+        if (!(ni > n_min) || !isfinite(ni)) continue;
+        const float gx = grad[i], gy = grad[N + i], gz = grad[2 * N + i];
+        const float cb = cbrtf(ni);
+        const float kF = cbrtf(3.f * PI_F * PI_F) * cb;
+        const float inv_n = 1.f / ni;
+        const float s2 = (gx * gx + gy * gy + gz * gz) * (0.25f * inv_n * inv_n) / (kF * kF);
+        const float den = 1.f + MU * s2 / KAPPA;
+        const float Fx = 1.f + KAPPA - KAPPA / den;
+        const float dF = MU / (den * den);
+        const float e0 = AX * ni * cb;
+        const float ex = e0 * Fx;
+        const float dex = (4.f / 3.f) * AX * cb * Fx + e0 * dF * (-(8.f / 3.f) * s2 * inv_n);
+        const float gex = e0 * dF * 2.f * (0.25f * inv_n * inv_n) / (kF * kF);
+        const float rs = cbrtf(3.f / (4.f * PI_F * ni));
+        const float srs = sqrtf(rs);
+        const float Q = 2.f * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
+        const float dQ = 2.f * A * (0.5f * b1 / srs + b2 + 1.5f * b3 * srs + 2.f * b4 * rs);
+        const float Lg = log1pf(1.f / Q);
+        const float ec = -2.f * A * (1.f + a1 * rs) * Lg;
+        const float dec = -2.f * A * a1 * Lg + 2.f * A * (1.f + a1 * rs) * dQ / (Q * Q + Q);
+        if (v) v[i] += dex + ec + ni * dec * (-rs * inv_n * (1.f / 3.f));
+        if (gg) gg[i] += gex;
+        sx += (double)ex;
+        sc += (double)(ni * ec);
+    }
+    const double tx = block_sum(sx, red);
+    __syncthreads();
+    const double tcs = block_sum(sc, red);
+    if (threadIdx.x == 0) {
+        epart[blockIdx.x] = tx;
+        epart[gridDim.x + blockIdx.x] = tcs;
+    }
+}
+
+// E[4] = {E_xc, E_c^nl, E_x, E_c^LDA} from the nonlocal E[0] and the partials
+__global__ void k_xc_final(const double* __restrict__ Enl, const double* __restrict__ epart, int nb, double dOmega,
+                           double* __restrict__ E) {
+    __shared__ double red[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += epart[i];
+        b += epart[nb + i];
+    }
+    const double ta = block_sum(a, red);
+    __syncthreads();
+    const double tb = block_sum(b, red);
+    if (threadIdx.x == 0) {
+        const double Ex = dOmega * ta, Ec = dOmega * tb;
+        E[0] = Enl[0] + Ex + Ec;
+        E[1] = Enl[0];
+        E[2] = Ex;
+        E[3] = Ec;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // energy: fixed-order FP64 reduction of the block partials
 // ---------------------------------------------------------------------------
 __global__ void k_energy_final(const double* __restrict__ epart, int nb0, int nb2, double s0, double s2,
@@ -698,7 +773,7 @@ int pipeline_stencil_gradient(vdw_ctx* c, const float* f, float* grad, cudaStrea
 
 template <int CN1, int CN2, int CN3>
 static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s,
-                     int fd) {
+                     int fd, int xc) {
     const GridArgs& g = c->g;
     const PointParams& P = c->pp;
     const bool want_pot = (v != nullptr) || (w != nullptr);
@@ -732,12 +807,17 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
                                          0.5 * Omega / (Nd * Nd), E);
         mark(3);
     }
+    if (xc && !want_pot)
+        k_semilocal<<<XC_BLOCKS, 256, 0, s>>>(n, grad, g.N, P.n_min, nullptr, nullptr, c->d_xc + 4);
     if (want_pot) {
         const size_t sa = smem_assemble(g, !c->acc_global, c->tk_smem, c->asm_dbuf);
         const int mode = (w != nullptr) ? 0 : 1;
         k_assemble<CN1, CN3><<<dim3(g.N2, ASM_CTAS), ASM_THREADS, sa, s>>>(
             c->d_spec, n, grad, c->d_t, c->d_k, g, P, c->d_tw, v, w, c->d_gg, mode, c->acc_global ? c->d_acc : nullptr,
             c->tk_smem, c->asm_dbuf, c->d_flags);
+        if (xc)
+            k_semilocal<<<XC_BLOCKS, 256, 0, s>>>(n, grad, g.N, P.n_min, v, mode == 1 ? c->d_gg : nullptr,
+                                                  c->d_xc + 4);
         if (mode == 1 && fd) {
             // finite-difference gradient: the chain term is a stencil, no transforms
             mark(4);
@@ -865,11 +945,18 @@ int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, dou
 }
 
 int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s,
-                 int fd) {
+                 int fd, int xc) {
     const GridArgs& g = c->g;
-    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) return run_sized<180, 180, 72>(c, n, grad, E, v, w, s, fd);
-    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) return run_sized<256, 256, 96>(c, n, grad, E, v, w, s, fd);
-    return run_sized<0, 0, 0>(c, n, grad, E, v, w, s, fd);
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) return run_sized<180, 180, 72>(c, n, grad, E, v, w, s, fd, xc);
+    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) return run_sized<256, 256, 96>(c, n, grad, E, v, w, s, fd, xc);
+    return run_sized<0, 0, 0>(c, n, grad, E, v, w, s, fd, xc);
+}
+
+int pipeline_xc_final(vdw_ctx* c, double* E, cudaStream_t s) {
+    const double dOmega = c->L[0] * c->L[1] * c->L[2] / (double)c->g.N;
+    k_xc_final<<<1, 256, 0, s>>>(c->d_xc, c->d_xc + 4, XC_BLOCKS, dOmega, E);
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
 }
 
 }  // namespace vdw

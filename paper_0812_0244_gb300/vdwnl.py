@@ -71,7 +71,7 @@ class Params:
 
 
 EXPORTS = ["vdw_params_default", "vdw_kernel_table", "vdw_create", "vdw_plan", "vdw_energy_potential",
-           "vdw_energy_potential_fd",
+           "vdw_energy_potential_fd", "vdw_xc_energy_potential",
            "vdw_energy_potential_host", "vdw_last_invalid_points", "vdw_profile_enable", "vdw_profile_read",
            "vdw_delta_energy_noalloc", "vdw_spectral_gradient", "vdw_learned_param_count", "vdw_learned_load",
            "vdw_learned_energy_potential", "vdw_learned_param_grad", "vdw_learned_fit_grad",
@@ -101,6 +101,7 @@ def lib():
     L.vdw_energy_potential.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.vdw_energy_potential_host.argtypes = [vp, fp, fp, dp, fp, vp]
     L.vdw_energy_potential_fd.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.vdw_xc_energy_potential.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, vp]
     L.vdw_last_invalid_points.argtypes = [vp, P(ctypes.c_longlong)]
     L.vdw_profile_enable.argtypes = [vp, ctypes.c_int]
     L.vdw_profile_read.argtypes = [vp, fp]
@@ -242,6 +243,20 @@ class VdwNL:
             _cuda_f32(v, self.shape)
         _check(lib().vdw_energy_potential_fd(self._h, _ptr(n), _ptr(grad), _ptr(E), _ptr(v), _stream_handle(stream)),
                "vdw_energy_potential_fd")
+        return E, v
+
+    def xc_energy_potential(self, n, grad=None, v=None, fd=False, stream=None):
+        """vdw_xc_energy_potential: E_xc of Eq. (Exc) and its potential;
+        returns (E[4] = {E_xc, E_c^nl, E_x, E_c^LDA}, v)."""
+        import torch
+        _cuda_f32(n, self.shape)
+        if grad is not None:
+            _cuda_f32(grad, (3,) + self.shape)
+        if v is not None:
+            _cuda_f32(v, self.shape)
+        E = torch.empty(4, dtype=torch.float64, device=n.device)
+        _check(lib().vdw_xc_energy_potential(self._h, _ptr(n), _ptr(grad), _ptr(E), _ptr(v), 1 if fd else 0,
+                                             _stream_handle(stream)), "vdw_xc_energy_potential")
         return E, v
 
     def compute(self, n, grad, want_v=True, want_w=False, stream=None):

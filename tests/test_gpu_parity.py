@@ -179,3 +179,27 @@ def test_finite_difference_gradient_variant(torch_cuda, table, shape):
     v2 = torch.empty_like(nt)
     E2, _ = ctx.energy_potential_fd(nt, None, v=v2)
     assert abs(float(E2[0]) - ref["E"]) <= 1e-6
+
+
+@pytest.mark.parametrize("fd", [False, True], ids=["spectral", "stencil"])
+def test_xc_functional_matches_oracle(torch_cuda, table, fd):
+    """E_xc = E_x^revPBE + E_c^LDA + E_c^nl (Eq. Exc) and its potential."""
+    torch = torch_cuda
+    import oracle.semilocal as SL
+    from paper_0812_0244_gb300 import vdwnl
+    d = S.two_atom_density(10, shape=(24, 24, 24))
+    n32 = d["n"].astype(np.float32)
+    L = d["L"]
+    n64 = n32.astype(np.float64)
+    g = (O.stencil_gradient if fd else O.spectral_gradient)(n64, L).astype(np.float32)
+    ctx = vdwnl.VdwNL(vdwnl.Params()).plan(n32.shape, L)
+    v = torch.empty(n32.shape, dtype=torch.float32, device="cuda")
+    E, _ = ctx.xc_energy_potential(torch.tensor(n32, device="cuda"), torch.tensor(g, device="cuda"), v, fd=fd)
+    E = E.cpu().numpy()
+    ref = SL.xc_energy_potential(n64, g.astype(np.float64), L, table, gradient="stencil" if fd else "spectral")
+    assert abs(E[1] - ref["E_nl"]) <= E_TOL
+    assert abs(E[2] - ref["E_x"]) <= 1e-6 * abs(ref["E_x"])
+    assert abs(E[3] - ref["E_c"]) <= 1e-6 * abs(ref["E_c"])
+    assert abs(E[0] - ref["E_xc"]) <= 1e-6 * abs(ref["E_xc"])
+    vv = v.cpu().numpy()
+    assert np.abs(vv - ref["v"]).max() <= V_REL * np.abs(ref["v"]).max()
