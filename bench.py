@@ -57,8 +57,9 @@ def stage_bytes_per_point(Nq, N1):
         "theta_plane": 9 + Nq * 8 * h,             # n, t, k in; theta(G) out
         "pencil_contract": 2 * Nq * 8 * h,         # theta(G) in, u(G) out
         "energy_final": 0.0,
-        # u(G), n, grad, t, k in; v_loc and g out; then g, grad in and w(G) out
-        "assemble": Nq * 8 * h + 16 + 5 + 4 + 4 + 4 + 12 + 3 * 8 * h,
+        # inverse plane transforms: u(G) in, real u out; the sum: real u, n,
+        # grad, t, k in, v_loc and g out; the w transforms: g, grad in, w(G) out
+        "assemble": Nq * 8 * h + Nq * 4 + Nq * 4 + 16 + 5 + 4 + 4 + 4 + 12 + 3 * 8 * h,
         "pencil_div": 3 * 8 * h + 8 * h,           # w(G) in, D.w(G) out
         "div_final": 8 * h + 4 + 4,                # D.w(G), v_loc in; v out
     }
@@ -445,7 +446,7 @@ def main():
             "stages_hbm_frac": stage_frac,
             "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
                     "d2h_bytes_per_step": 4 * N + 24},
-            "gpu_launches": 8 * K,
+            "gpu_launches": 9 * K,
             "cufft_reference": {"ms_per_step": cufft_ms,
                                 "what": "torch.fft (cuFFT) on the step's %d forward + %d inverse real 3D transforms "
                                         "alone, no pointwise work or contraction; reference only"

@@ -32,7 +32,6 @@ static void free_plan(vdw_ctx* c) {
     cudaFree(c->d_k);
     cudaFree(c->d_epart);
     cudaFree(c->d_invalid);
-    cudaFree(c->d_acc);
     cudaFree(c->d_in);
     cudaFree(c->d_v);
     cudaFree(c->d_E);
@@ -42,7 +41,6 @@ static void free_plan(vdw_ctx* c) {
     c->d_k = nullptr;
     c->d_epart = nullptr;
     c->d_invalid = nullptr;
-    c->d_acc = nullptr;
     c->d_in = c->d_v = nullptr;
     c->d_E = nullptr;
     cudaFree(c->d_gtmp);
@@ -185,7 +183,6 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     VDW_CUDA(cudaMalloc(&c->d_xc, sizeof(double) * (4 + 2 * 1024)));
     VDW_CUDA(cudaMemset(c->d_flags, 0, sizeof(int)));
     VDW_CUDA(cudaMemset(c->d_invalid, 0, sizeof(unsigned long long)));
-    if (c->acc_global) VDW_CUDA(cudaMalloc(&c->d_acc, sizeof(float) * 2 * 4 * g.N));
     rc = pipeline_make_twiddles(c);
     if (rc) return rc;
     rc = pipeline_configure(c);
@@ -193,7 +190,7 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     const int npairs = Nq * (Nq + 1) / 2;
     c->bytes = sizeof(float4) * (size_t)(c->p.Nk - 1) * npairs + sizeof(float2) * (n1 + n2 + n3) +
                sizeof(float2) * (spec_n + 3 * (size_t)n2 * g.ncols) + 5 * (size_t)g.N +
-               sizeof(double) * (c->nb_point + c->nb_pencil) + (c->acc_global ? 32 * (size_t)g.N : 0) +
+               sizeof(double) * (c->nb_point + c->nb_pencil) +
                4 * (size_t)g.N + sizeof(int);
     c->planned = 1;
     return VDW_OK;

@@ -95,7 +95,7 @@ struct vdw_ctx {
     vdw::GridArgs g;
     double L[3];
     float2* d_tw;               // twiddles: N1, N2, N3 entries
-    float2* d_spec;             // [Nq][N2][N3][Nh] theta(G) then u(G), in place
+    float2* d_spec;             // [Nq][N2][N3][Nh] theta(G), then u(G), then real u (N3 x N1 per plane), in place
     float2* d_wspec;            // [3][N2][N3][Nh] w(G); component 0 then D.w
     float* d_t;                 // [N] position of q inside its mesh interval
     uint8_t* d_k;               // [N] mesh interval of q (K_INVALID: theta = 0)
@@ -103,13 +103,10 @@ struct vdw_ctx {
     int nb_point, nb_pencil;    // their counts (pointwise, pencil kernels)
     unsigned long long* d_invalid;  // count of negative / non-finite densities
     int pencil_cols;            // columns per pencil block
-    int acc_global;             // assembly accumulators in global memory
-    int tk_smem;                // assembly keeps the plane's (t, k) in shared memory
-    int asm_dbuf;               // assembly double-buffers its planes (bulk asynchronous copies)
+    int bulk_planes;            // inverse plane transforms load their planes by bulk copies
     float* d_gg;                // [N] g of w = g grad n (assembly -> w plane transforms)
     int* d_flags;               // [1] set when a bounded wait in a kernel gave up
     double* d_xc;               // [4 + 2 XC_BLOCKS] nonlocal E and semilocal partial sums
-    float* d_acc;               // [4][2N] their scratch (only when acc_global)
     // buffers of the host-pointer entry point (allocated on first use)
     float* d_in;                // [4N]
     float* d_v;                 // [N]

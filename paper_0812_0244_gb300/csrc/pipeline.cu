@@ -8,8 +8,9 @@
 //                       per G: u_a(G) = sum_b phi_ab(|G|) theta_b(G) with phi_ab
 //                       from the radial table, energy of Eq. (Eoffk) in FP64,
 //                       inverse C2C along y (Eqs. epsilon, epsofk)
-//   P3 k_assemble       inverse plane transform of u_a, Eq. (Vi): v_loc and
-//                       w = dE/d grad n, forward plane transform of w
+//   P3 k_u_planes       inverse plane transform of u_a (in place)
+//      k_u_sum          Eq. (Vi) per point: v_loc and g of w = g grad n
+//      k_w_planes       forward plane transform of w
 //   P4 k_pencil_div     y transform of w, i G' . w(G), inverse y transform
 //   P5 k_div_final      inverse plane transform, v = v_loc - D . w
 //
@@ -228,22 +229,13 @@ __global__ void __launch_bounds__(CONTRACT_THREADS, 2) k_pencil_contract(float2*
 }
 
 // ---------------------------------------------------------------------------
-// P3: inverse plane transforms of u_a and the assembly of Eq. (Vi)
+// P3: inverse plane transforms of u_a, in place
 // ---------------------------------------------------------------------------
-// A cluster of ASM_CTAS blocks shares one y plane: block r transforms the
-// fields a = r, r + ASM_CTAS, ... and accumulates S0 = sum_a u_a p_a and
-// S1 = sum_a u_a p_a' over its fields; after a cluster barrier, block r sums
-// the partials of every block for the rows z = r (mod ASM_CTAS) through
-// distributed shared memory and finishes those points: v_loc, and g with
-// w = g grad n.
-// With dbuf the spectrum plane of the next field arrives by a bulk
-// asynchronous copy (completion counted on an mbarrier) into a second buffer
-// while the current one is transformed and accumulated.
-// mode 0: v_loc to v (if v), w to w_out; mode 1: v_loc to v, g to g_out (the
-// plane transforms of w follow in k_w_planes).
-constexpr int ASM_CTAS = 4;
-constexpr int ASM_THREADS = 384;
-
+// One block per (y plane, field): the plane of u_a(G) arrives by one bulk
+// asynchronous copy (completion counted on an mbarrier) while the twiddles
+// load, goes through the inverse z and x transforms, and its N3 x N1 real
+// values (unscaled: 1/N is folded into the contraction) overwrite the start of
+// the same plane of the spectrum buffer, rows of N1 floats.
 __device__ __forceinline__ void mbar_init1(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
 }
@@ -275,133 +267,101 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
 }
 
 template <int CN1, int CN3>
-__global__ void __cluster_dims__(1, ASM_CTAS, 1) __launch_bounds__(ASM_THREADS, 1)
-    k_assemble(const float2* __restrict__ spec, const float* __restrict__ n, const float* __restrict__ grad,
-               const float* __restrict__ tk, const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
-               const float2* __restrict__ tw, float* __restrict__ v, float* __restrict__ w_out,
-               float* __restrict__ g_out, int mode, float* __restrict__ acc_global, int tk_smem, int dbuf,
-               int* __restrict__ wait_err) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
+__global__ void __launch_bounds__(PLANE_THREADS, 2) k_u_planes(float2* __restrict__ spec, GridArgs g,
+                                                               const float2* __restrict__ tw, int bulk,
+                                                               int* __restrict__ wait_err) {
     extern __shared__ float2 sm[];
-    __shared__ SplineSmem sp;
-    __shared__ uint64_t lbar[2];
-    const int np = g.N1 * g.N3;
-    const int pe = g.N3 * g.Nh;  // complex values of a plane (ncols)
-    const int y = blockIdx.x;
-    const int rank = (int)cluster.block_rank();  // = blockIdx.y
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float2* plane0 = sm;
-    float2* plane1 = dbuf ? plane0 + pe : plane0;
-    float2* tw1 = plane0 + (dbuf ? 2 : 1) * pe;
+    __shared__ uint64_t bar;
+    float2* plane = sm;
+    float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
-    // per-point partial sums of this block: shared memory when the planes leave
-    // room for them, otherwise this block's slice of a global scratch buffer
-    float* after = reinterpret_cast<float*>(tw3 + g.N3);
-    float* S0 = acc_global ? acc_global + ((long long)y * ASM_CTAS + rank) * 2 * np : after;
-    float* S1 = S0 + np;
-    if (!acc_global) after += 2 * np;
-    // the plane's (t, k) in shared memory when there is room (tk_smem), read
-    // once instead of once per field
-    float* t_s = after;
-    uint8_t* k_s = reinterpret_cast<uint8_t*>(t_s + np);
-    const uint32_t pbytes = (uint32_t)(sizeof(float2) * (size_t)pe);
-    if (threadIdx.x == 0 && dbuf) {
-        mbar_init1(&lbar[0]);
-        mbar_init1(&lbar[1]);
+    const int y = blockIdx.x, a = blockIdx.y;
+    float2* src = spec + ((long long)a * g.N2 + y) * g.ncols;
+    // bulk: one copy of the whole plane (16-byte aligned, a multiple of 16
+    // bytes), in flight while the twiddles load
+    if (bulk) {
+        if (threadIdx.x == 0) mbar_init1(&bar);
+        __syncthreads();
+        if (threadIdx.x == 0) bulk_load(plane, src, (uint32_t)(sizeof(float2) * (size_t)g.ncols), &bar);
+    } else {
+        for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && dbuf && rank < P.Nq)
-        bulk_load(plane0, spec + ((long long)rank * g.N2 + y) * g.ncols, pbytes, &lbar[0]);
-    load_spline_smem(&sp, P);
     load_twiddles(tw1, tw, g.N1);
     load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
-    for (int i = threadIdx.x; i < np; i += blockDim.x) { S0[i] = 0.f; S1[i] = 0.f; }
-    if (tk_smem) {
-        for (int z = warp; z < g.N3; z += nw) {
-            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-            for (int x = lane; x < g.N1; x += 32) {
-                t_s[z * g.N1 + x] = tk[row + x];
-                k_s[z * g.N1 + x] = kk[row + x];
-            }
-        }
+    __syncthreads();
+    if (bulk && !mbar_wait_parity(&bar, 0u)) {
+        // gave up: record it, wait once more (bounded) for the copy in flight
+        atomicExch(wait_err, 1);
+        mbar_wait_parity(&bar, 0u);
     }
-    int it = 0;
-    for (int a = rank; a < P.Nq; a += ASM_CTAS, ++it) {
-        float2* plane = (it & 1) ? plane1 : plane0;
-        if (dbuf) {
-            __syncthreads();  // the other buffer is free (and the setup above is done)
-            if (threadIdx.x == 0 && a + ASM_CTAS < P.Nq)
-                bulk_load((it & 1) ? plane0 : plane1, spec + ((long long)(a + ASM_CTAS) * g.N2 + y) * g.ncols,
-                          pbytes, &lbar[(it + 1) & 1]);
-            if (!mbar_wait_parity(&lbar[it & 1], (uint32_t)(it >> 1) & 1u)) {
-                atomicExch(wait_err, 1);
-                mbar_wait_parity(&lbar[it & 1], (uint32_t)(it >> 1) & 1u);
-            }
-        } else {
-            const float2* src = spec + ((long long)a * g.N2 + y) * g.ncols;
-            __syncthreads();
-            for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
-            __syncthreads();
-        }
-        // radices up to 8 here: the longer in-register transforms spill next
-        // to everything else this kernel keeps live
-        plane_inverse<CN1, CN3, 8>(plane, g, tw1, tw3);
-        const float* pf = reinterpret_cast<const float*>(plane);
-        for (int z = warp; z < g.N3; z += nw) {
-            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-            const float* srow = pf + packed_row(z, g.Nh);
-            for (int x = lane; x < g.N1; x += 32) {
-                const int i = z * g.N1 + x;
-                const int k = tk_smem ? k_s[i] : kk[row + x];
-                if (k == K_INVALID) continue;
-                float pa, dpa;
-                cardinal(&sp, a, k, tk_smem ? t_s[i] : tk[row + x], pa, dpa);
-                const float u = srow[2 * x];
-                S0[i] = fmaf(u, pa, S0[i]);
-                S1[i] = fmaf(u, dpa, S1[i]);
-            }
-        }
+    plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
+    const float* pf = reinterpret_cast<const float*>(plane);
+    float* dst = reinterpret_cast<float*>(src);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int z = warp; z < g.N3; z += nw) {
+        const float* srow = pf + packed_row(z, g.Nh);
+        for (int x = lane; x < g.N1; x += 32) dst[z * g.N1 + x] = srow[2 * x];
     }
-    __threadfence_block();
-    cluster.sync();
-    // partial sums of every block of the cluster
-    const float* S0r[ASM_CTAS];
-    for (int r = 0; r < ASM_CTAS; ++r)
-        S0r[r] = acc_global ? acc_global + ((long long)y * ASM_CTAS + r) * 2 * np : cluster.map_shared_rank(S0, r);
+}
+
+// ---------------------------------------------------------------------------
+// P3': the assembly of Eq. (Vi), one thread per point
+// ---------------------------------------------------------------------------
+// S0 = sum_a u_a p_a(q), S1 = sum_a u_a p_a'(q) from the real u_a planes left
+// in the spectrum buffer by k_u_planes; then
+//   v_loc = S0 + n S1 dq/dn + d(Delta eps)/dn,   g = n S1 dq/d|grad n| / |grad n| + ...
+// mode 0: v_loc to v (if v), w = g grad n to w_out; mode 1: v_loc to v, g to
+// g_out (the plane transforms of w follow in k_w_planes).
+constexpr int USUM_THREADS = 256;
+
+template <int NQ>
+__global__ void __launch_bounds__(USUM_THREADS) k_u_sum(const float* __restrict__ uf, const float* __restrict__ n,
+                                                        const float* __restrict__ grad, const float* __restrict__ tk,
+                                                        const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
+                                                        float* __restrict__ v, float* __restrict__ w_out,
+                                                        float* __restrict__ g_out, int mode) {
+    __shared__ SplineSmem sp;
+    load_spline_smem(&sp, P);
+    __syncthreads();
     const long long N = g.N;
-    for (int z = rank + ASM_CTAS * warp; z < g.N3; z += ASM_CTAS * nw) {
-        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-        for (int x = lane; x < g.N1; x += 32) {
-            const int i = z * g.N1 + x;
+    const long long fstride = 2LL * g.N2 * g.ncols;  // floats between the planes of two fields
+    const int N1 = g.N1, N2 = g.N2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / N1;
+        const int x = (int)(i - r * N1);
+        const int z = (int)(r / N2), y = (int)(r - (long long)z * N2);
+        const float* up = uf + 2LL * y * g.ncols + (long long)z * N1 + x;
+        const int k = kk[i];
+        const float ni = n[i];
+        const float gx = grad[i], gy = grad[N + i], gz = grad[2 * N + i];
+        float vl = 0.f, gg = 0.f;
+        if (k != K_INVALID) {
+            float u[NQ];
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) u[a] = up[a * fstride];
+            const float t = tk[i];
             float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-            for (int r = 0; r < ASM_CTAS; ++r) {
-                s0 += S0r[r][i];
-                s1 += S0r[r][np + i];
+            for (int a = 0; a < NQ; ++a) {
+                float pa, dpa;
+                cardinal(&sp, a, k, t, pa, dpa);
+                s0 = fmaf(u[a], pa, s0);
+                s1 = fmaf(u[a], dpa, s1);
             }
-            const long long gi = row + x;
-            const float ni = n[gi];
-            const float gx = grad[gi], gy = grad[N + gi], gz = grad[2 * N + gi];
             const QPoint qp = q_point(ni, gx, gy, gz, P, sp.qm);
-            float vl = 0.f, gg = 0.f;
-            if (qp.k != K_INVALID) {
-                const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
-                const float cn = 1.5f * P.C_s * ni * ni / q4;
-                vl = s0 + ni * qp.dq_dn * s1 + P.C_s * ni / q3 - cn * qp.dq_dn;
-                gg = ni * s1 * qp.dq_dg - cn * qp.dq_dg;
-            }
-            if (v) v[gi] = vl;
-            if (mode == 0 && w_out) {
-                w_out[gi] = gg * gx;
-                w_out[N + gi] = gg * gy;
-                w_out[2 * N + gi] = gg * gz;
-            }
-            if (mode == 1) g_out[gi] = gg;
+            const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
+            const float cn = 1.5f * P.C_s * ni * ni / q4;
+            vl = s0 + ni * qp.dq_dn * s1 + P.C_s * ni / q3 - cn * qp.dq_dn;
+            gg = ni * s1 * qp.dq_dg - cn * qp.dq_dg;
         }
+        if (v) v[i] = vl;
+        if (mode == 0 && w_out) {
+            w_out[i] = gg * gx;
+            w_out[N + i] = gg * gy;
+            w_out[2 * N + i] = gg * gz;
+        }
+        if (mode == 1) g_out[i] = gg;
     }
-    // keep this block's shared memory alive until every block is done reading it
-    cluster.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -677,10 +637,6 @@ static size_t smem_plane(const GridArgs& g) { return sizeof(float2) * ((size_t)g
 static size_t smem_theta(const GridArgs& g) {
     return sizeof(float2) * ((size_t)THETA_FIELDS * g.N3 * g.Nh + g.N1 + g.N3);
 }
-static size_t smem_assemble(const GridArgs& g, bool acc_in_smem, bool tk_in_smem, bool dbuf) {
-    return sizeof(float2) * ((size_t)(dbuf ? 2 : 1) * g.N3 * g.Nh + g.N1 + g.N3) +
-           (acc_in_smem ? sizeof(float) * 2 * (size_t)g.N1 * g.N3 : 0) + (tk_in_smem ? 5 * (size_t)g.N1 * g.N3 : 0);
-}
 static size_t smem_pencil(const GridArgs& g, int nq, int C) { return sizeof(float2) * ((size_t)nq * C * g.N2 + g.N2); }
 static size_t smem_pencil_run(const GridArgs& g, int nq, int C) { return smem_pencil(g, nq, C); }
 
@@ -704,25 +660,12 @@ int pipeline_plan_check(vdw_ctx* c, size_t* sp, size_t* spen, size_t* sa, size_t
     c->pencil_cols = C;
     *sp = smem_plane(g);
     *spen = smem_pencil_run(g, nq, C);
-    // assembly: double-buffered planes if at all possible, then the partial
-    // sums in shared memory, then the (t, k) cache
-    // the first of these that fits (measured at 180 x 180 x 72: the (t, k) cache
-    // in shared memory matters more than double-buffered planes, and double
-    // buffering pays when the partial sums live in global memory)
-    static const bool opts[][3] = {  // double buffer, sums in shared memory, (t, k) cache
-        {false, true, true}, {true, true, false}, {true, false, true}, {true, false, false},
-        {false, true, false}, {false, false, true}, {false, false, false}};
-    for (const auto& o : opts) {
-        if (smem_assemble(g, o[1], o[2], o[0]) <= SMEM_MAX) {
-            c->asm_dbuf = o[0];
-            c->acc_global = !o[1];
-            c->tk_smem = o[2];
-            break;
-        }
-    }
-    *sa = smem_assemble(g, !c->acc_global, c->tk_smem, c->asm_dbuf);
+    // the inverse plane transforms of u take their planes by one bulk copy when
+    // a plane is a whole multiple of 16 bytes (every plane then starts 16-byte aligned)
+    c->bulk_planes = (sizeof(float2) * (size_t)g.ncols) % 16 == 0;
+    *sa = *sp;
     *sd = smem_pencil_run(g, 3, DIV_COLS);
-    if (*sp > SMEM_MAX || smem_theta(g) > SMEM_MAX || *spen > SMEM_MAX || *sa > SMEM_MAX || *sd > SMEM_MAX)
+    if (*sp > SMEM_MAX || smem_theta(g) > SMEM_MAX || *spen > SMEM_MAX || *sd > SMEM_MAX)
         return VDW_ERR_SIZE;
     return VDW_OK;
 }
@@ -771,6 +714,25 @@ int pipeline_stencil_gradient(vdw_ctx* c, const float* f, float* grad, cudaStrea
     return VDW_OK;
 }
 
+static int u_sum_blocks(const GridArgs& g) { return (int)std::min<long long>((g.N + USUM_THREADS - 1) / USUM_THREADS, 1 << 16); }
+
+static int launch_u_sum(vdw_ctx* c, const float* n, const float* grad, float* v, float* w, int mode, cudaStream_t s) {
+    const GridArgs& g = c->g;
+    const float* uf = reinterpret_cast<const float*>(c->d_spec);
+    const int nb = u_sum_blocks(g);
+#define VDW_U_SUM(NQ) \
+    k_u_sum<NQ><<<nb, USUM_THREADS, 0, s>>>(uf, n, grad, c->d_t, c->d_k, g, c->pp, v, w, c->d_gg, mode)
+    switch (c->pp.Nq) {
+        case 20: VDW_U_SUM(20); break;
+        case 8: VDW_U_SUM(8); break;
+        case 12: VDW_U_SUM(12); break;
+        case 16: VDW_U_SUM(16); break;
+        default: set_error("Nq not compiled in"); return VDW_ERR_UNSUPPORTED;
+    }
+#undef VDW_U_SUM
+    return VDW_OK;
+}
+
 template <int CN1, int CN2, int CN3>
 static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s,
                      int fd, int xc) {
@@ -810,11 +772,11 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
     if (xc && !want_pot)
         k_semilocal<<<XC_BLOCKS, 256, 0, s>>>(n, grad, g.N, P.n_min, nullptr, nullptr, c->d_xc + 4);
     if (want_pot) {
-        const size_t sa = smem_assemble(g, !c->acc_global, c->tk_smem, c->asm_dbuf);
         const int mode = (w != nullptr) ? 0 : 1;
-        k_assemble<CN1, CN3><<<dim3(g.N2, ASM_CTAS), ASM_THREADS, sa, s>>>(
-            c->d_spec, n, grad, c->d_t, c->d_k, g, P, c->d_tw, v, w, c->d_gg, mode, c->acc_global ? c->d_acc : nullptr,
-            c->tk_smem, c->asm_dbuf, c->d_flags);
+        k_u_planes<CN1, CN3><<<dim3(g.N2, P.Nq), PLANE_THREADS, sp, s>>>(c->d_spec, g, c->d_tw, c->bulk_planes,
+                                                                         c->d_flags);
+        const int rcs = launch_u_sum(c, n, grad, v, w, mode, s);
+        if (rcs) return rcs;
         if (xc)
             k_semilocal<<<XC_BLOCKS, 256, 0, s>>>(n, grad, g.N, P.n_min, v, mode == 1 ? c->d_gg : nullptr,
                                                   c->d_xc + 4);
@@ -858,11 +820,11 @@ static int set_and_check(K kernel, const char* name, int smem, int threads) {
 template <int CN1, int CN2, int CN3>
 static int configure_sized(vdw_ctx* c) {
     const GridArgs& g = c->g;
-    const int sp = (int)smem_plane(g), sa = (int)smem_assemble(g, !c->acc_global, c->tk_smem, c->asm_dbuf);
+    const int sp = (int)smem_plane(g);
     const int sd = (int)smem_pencil_run(g, 3, DIV_COLS), sc = (int)smem_pencil_run(g, c->p.Nq, c->pencil_cols);
     const int tc = contract_threads(g, c->pencil_cols);
     int rc = set_and_check(k_theta_plane<CN1, CN3>, "k_theta_plane", (int)smem_theta(g), PLANE_THREADS);
-    if (!rc) rc = set_and_check(k_assemble<CN1, CN3>, "k_assemble", sa, ASM_THREADS);
+    if (!rc) rc = set_and_check(k_u_planes<CN1, CN3>, "k_u_planes", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_pencil_div<CN2>, "k_pencil_div", sd, 256);
     if (!rc) rc = set_and_check(k_div_final<CN1, CN3>, "k_div_final", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_w_planes<CN1, CN3>, "k_w_planes", sp, PLANE_THREADS);
@@ -874,27 +836,7 @@ static int configure_sized(vdw_ctx* c) {
         case 16: rc = set_and_check(k_pencil_contract<16, CN2>, "k_pencil_contract", sc, tc); break;
         default: return VDW_ERR_UNSUPPORTED;
     }
-    if (rc) return rc;
-    // the assembly clusters must fit on the device
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g.N2, ASM_CTAS);
-    cfg.blockDim = dim3(ASM_THREADS);
-    cfg.dynamicSmemBytes = sa;
-    cudaLaunchAttribute at;
-    at.id = cudaLaunchAttributeClusterDimension;
-    at.val.clusterDim.x = 1;
-    at.val.clusterDim.y = ASM_CTAS;
-    at.val.clusterDim.z = 1;
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    VDW_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, k_assemble<CN1, CN3>, &cfg));
-    if (nclusters < 1) {
-        set_error("k_assemble: a cluster of " + std::to_string(ASM_CTAS) + " blocks with " + std::to_string(sa) +
-                  " bytes of shared memory each does not fit");
-        return VDW_ERR_UNSUPPORTED;
-    }
-    return VDW_OK;
+    return rc;
 }
 
 int pipeline_configure(vdw_ctx* c) {
