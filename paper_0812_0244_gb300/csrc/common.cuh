@@ -152,6 +152,10 @@ int pipeline_make_twiddles(vdw_ctx* c);
 int pipeline_configure(vdw_ctx* c);
 // the divergence term of a potential (w(G) in d_wspec) and the energy reduction
 int pipeline_divergence(vdw_ctx* c, float* v, cudaStream_t s);
+// in-place plane transforms of the first nfields fields of d_spec: inverse
+// (half spectrum -> N3 x N1 real rows at the start of each plane) or forward
+// (packed real rows -> half spectrum)
+int pipeline_planes_inplace(vdw_ctx* c, int nfields, bool inverse, cudaStream_t s);
 // forward plane transforms of w = g grad n with g in d_gg (into d_wspec)
 int pipeline_w_planes(vdw_ctx* c, const float* grad, cudaStream_t s);
 int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, double* E, cudaStream_t s);

@@ -1,23 +1,22 @@
 // Learned reduced basis: M = 8 channels theta_m = n w_m(x(n, |grad n|)) whose
 // weights come from a 2-64-64-8 SiLU network (bf16 operands on the tensor
 // cores, FP32 accumulation in tensor memory), contracted with a learned
-// piecewise-linear pair kernel K_mn(|G|) on uniform knots, plus the paper's
+// pair kernel K_mn(|G|) (Catmull-Rom pieces between uniform knots), plus the paper's
 // local correction Delta E (Eqs. DEnl, Depsnl).  The transform structure is
 // the plain method's (Eqs. Eoffk, epsilon, epsofk, Vi) with M channels:
 //
-//   L1 k_learned_theta     a cluster of 8 blocks per y plane: the network on
-//                          the plane's points (tiles of 128 points, one per
-//                          warpgroup), theta_m sent to block m's plane through
-//                          distributed shared memory, then block m's forward
-//                          plane transform; Delta E partial sums
+//   L1 k_learned_net       persistent, one block per SM: the network and its
+//                          Jacobian (forward mode) on tiles of 128 points;
+//                          theta_m to the packed real rows of the spectrum
+//                          buffer, Delta E partial sums; then the forward plane
+//                          transforms in place (k_planes_inplace)
 //   L2 k_learned_contract  y pencils of the 8 channels, u_m(G) = sum_n
 //                          K_mn(|G|) theta_n(G), FP64 energy, inverse y; in
 //                          training also dE/dK at the knots
-//   L3 k_learned_assemble  a cluster of 8 blocks per y plane: inverse plane
-//                          transform of u_m in block m; then per point the
-//                          network again and its Jacobian-vector product with
-//                          u (tensor cores), v_loc and w = g grad n (Eq. Vi);
-//                          forward plane transforms of w by blocks 0..2
+//   L3 inverse plane transforms in place (k_planes_inplace), then
+//      k_learned_usum      per point: v_loc and g of w = g grad n (Eq. Vi)
+//                          from u, the stored weights and Jacobian;
+//                          forward plane transforms of w (k_w_planes)
 //   then the plain method's divergence kernels (P4, P5).
 //
 // Training kernels: the parameter gradient of E through the network
@@ -40,7 +39,7 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-constexpr int L_CTAS = 8;         // blocks per cluster = channels
+constexpr int L_SLOTS = 8;        // network partial-sum slots per y plane (epart scratch)
 constexpr int L_THREADS = 256;    // two warpgroups
 constexpr int L_TILE = 128;       // points per warpgroup tile
 constexpr int L_MAXJ = 256;       // knots held in shared memory by the knot-gradient bins
@@ -333,13 +332,6 @@ __device__ bool mlp_forward_jac(MlpShared* S, MlpWG3* W, MlpCtl* ctl, int wg, in
     return true;
 }
 
-// dynamic shared memory of the cluster kernels: plane, twiddles, then the
-// network's shared block (128-byte aligned)
-__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) & ~(size_t)127; }
-__host__ __device__ inline size_t plane_bytes(int N3, int Nh, int N1) {
-    return align128(sizeof(float2) * ((size_t)N3 * Nh + N1 + N3));
-}
-
 // ---------------------------------------------------------------------------
 // L0: model preparation (flat FP32 parameters -> device operands)
 // ---------------------------------------------------------------------------
@@ -388,54 +380,62 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
 }
 
 // ---------------------------------------------------------------------------
-// L1: network, channels, forward plane transforms
+// L1: network and channels
 // ---------------------------------------------------------------------------
-// Tile T (128 consecutive points of the plane, index i = z N1 + x) belongs to
-// block (T / 2) mod 8, warpgroup T mod 2.  With lw the channel weights and
-// the network's Jacobian are also stored for the assembly: lw [24][N] holds
-// w_m, then d o_m / d x1, then d o_m / d x2.
-template <int CN1, int CN3>
-__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
-    k_learned_theta(const float* __restrict__ n, const float* __restrict__ grad, GridArgs g, PointParams P,
-                    LearnedArgs la, const float2* __restrict__ tw, float2* __restrict__ spec,
-                    double* __restrict__ epart, unsigned long long* __restrict__ invalid, float* __restrict__ lw) {
-    cg::cluster_group cluster = cg::this_cluster();
+// Points in packed order: q = ((y (N3/2) + j) N1 + x) 2 + s is the point
+// (x, y, z = 2j + s).  Writing theta_m in this order fills the packed real
+// rows of the plane transforms (real rows 2j and 2j + 1 interleaved in complex
+// row j) with consecutive addresses; returns the flat index (z N2 + y) N1 + x.
+__device__ __forceinline__ long long packed_point(long long q, const GridArgs& g, int& y, int& z, int& x, int& j) {
+    const int s = (int)(q & 1);
+    const long long t = q >> 1;
+    const long long rr = t / g.N1;
+    x = (int)(t - rr * g.N1);
+    const int nh3 = g.N3 >> 1;
+    y = (int)(rr / nh3);
+    j = (int)(rr - (long long)y * nh3);
+    z = 2 * j + s;
+    return ((long long)z * g.N2 + y) * g.N1 + x;
+}
+
+// One persistent block per SM, two warpgroups, each running the network and
+// its two tangents on tiles of 128 points (packed order): layer 1 on CUDA
+// cores gives three bf16 operands in the tcgen05 core-matrix layout; layers 2
+// and 3 are 3 x 4 MMAs each into tensor memory, one commit and one wait per
+// layer.  theta_m = n w_m goes to the packed real rows of plane (m, y) of the
+// spectrum buffer (the forward plane transforms follow in place).  With lw
+// the channel weights and the network's Jacobian are stored for the
+// assembly, lw[c][q] in packed order: w_m, then d o_m / d x1, then
+// d o_m / d x2.  Delta E partial sums per block.
+__global__ void __launch_bounds__(L_THREADS, 1)
+    k_learned_net(const float* __restrict__ n, const float* __restrict__ grad, GridArgs g, PointParams P,
+                  LearnedArgs la, float* __restrict__ specf, double* __restrict__ epart,
+                  unsigned long long* __restrict__ invalid, float* __restrict__ lw) {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ MlpCtl ctl;
     __shared__ double red[32];
     __shared__ float qm[MAX_NQ];
-    float2* plane = reinterpret_cast<float2*>(smraw);
-    float2* tw1 = plane + g.N3 * g.Nh;
-    float2* tw3 = tw1 + g.N1;
-    MlpShared* S = reinterpret_cast<MlpShared*>(smraw + plane_bytes(g.N3, g.Nh, g.N1));
-    MlpWG3* Wb = reinterpret_cast<MlpWG3*>(reinterpret_cast<unsigned char*>(S) + sizeof(MlpShared));
-    const int y = blockIdx.x;
-    const int rank = (int)cluster.block_rank();
+    MlpShared* S = reinterpret_cast<MlpShared*>(smraw);
+    MlpWG3* Wb = reinterpret_cast<MlpWG3*>(smraw + sizeof(MlpShared));
     const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
     MlpWG3* W = Wb + wg;
-    load_twiddles(tw1, tw, g.N1);
-    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
     mlp_load_weights(S, la);
     for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
     mlp_setup(&ctl, 256);
-    float* pf = reinterpret_cast<float*>(plane);
-    float* rem[L_CTAS];
-#pragma unroll
-    for (int m = 0; m < L_CTAS; ++m) rem[m] = cluster.map_shared_rank(pf, m);
-    cluster.sync();  // every block of the cluster is running before remote stores
-    const int np = g.N1 * g.N3;
-    const int ntiles = (np + L_TILE - 1) / L_TILE;
     const long long N = g.N;
+    const long long ntiles = (N + L_TILE - 1) / L_TILE;
+    const long long fstride = 2LL * g.N2 * g.ncols;  // floats between the planes of two channels
     uint32_t phase = 0;
     double eacc = 0.0;
     unsigned int bad = 0;
-    for (int T = 2 * rank + wg; T < ntiles; T += 2 * L_CTAS) {
-        const int i = T * L_TILE + r;
-        const bool in = i < np;
-        const int z = in ? i / g.N1 : 0, x = in ? i - z * g.N1 : 0;
-        const long long gi = (long long)g.N1 * (y + (long long)g.N2 * z) + x;
+    for (long long T = 2 * (long long)blockIdx.x + wg; T < ntiles; T += 2 * (long long)gridDim.x) {
+        const long long q = T * L_TILE + r;
+        const bool in = q < N;
+        int y = 0, z = 0, x = 0, j = 0;
+        long long gi = 0;
         float ni = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
         if (in) {
+            gi = packed_point(q, g, y, z, x, j);
             ni = n[gi];
             gx = grad[gi];
             gy = grad[N + gi];
@@ -457,29 +457,25 @@ __global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 1)
         float o[LRN_M], J1[LRN_M], J2[LRN_M];
         if (!mlp_forward_jac(S, W, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, J1, J2, la.err)) break;
         if (in) {
-            const int off = packed_row(z, g.Nh) + 2 * x;
+            float* dst = specf + 2LL * y * g.ncols + 4 * j * g.Nh + 2 * x + (z & 1);
 #pragma unroll
-            for (int m = 0; m < LRN_M; ++m) rem[m][off] = ok ? ni * (o[m] + pb[m]) : 0.f;
+            for (int m = 0; m < LRN_M; ++m) dst[m * fstride] = ok ? ni * (o[m] + pb[m]) : 0.f;
             if (lw) {
 #pragma unroll
                 for (int m = 0; m < LRN_M; ++m) {
-                    lw[m * N + gi] = ok ? o[m] + pb[m] : 0.f;
-                    lw[(LRN_M + m) * N + gi] = J1[m];
-                    lw[(2 * LRN_M + m) * N + gi] = J2[m];
+                    lw[m * N + q] = ok ? o[m] + pb[m] : 0.f;
+                    lw[(LRN_M + m) * N + q] = J1[m];
+                    lw[(2 * LRN_M + m) * N + q] = J2[m];
                 }
             }
         }
     }
     mlp_teardown(&ctl);
     const double es = block_sum(eacc, red);
-    if (threadIdx.x == 0) epart[y * L_CTAS + rank] = es;
+    if (threadIdx.x == 0) epart[blockIdx.x] = es;
     __syncthreads();
     const double b = block_sum((double)bad, red);
     if (threadIdx.x == 0 && b > 0.0) atomicAdd(invalid, (unsigned long long)b);
-    cluster.sync();  // all channels of the plane have arrived
-    plane_forward<CN1, CN3>(plane, g, tw1, tw3);
-    float2* dst = spec + ((long long)rank * g.N2 + y) * g.ncols;
-    for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -616,100 +612,85 @@ __global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ s
 }
 
 // ---------------------------------------------------------------------------
-// L3: inverse plane transforms of u_m, assembly of Eq. (Vi)
+// L3: assembly of Eq. (Vi), one thread per point (packed order)
 // ---------------------------------------------------------------------------
-// Block m inverse-transforms u_m; after a cluster barrier block r finishes the
-// rows z = r (mod 8) of the plane from the 8 u values of each point (through
-// distributed shared memory), the channel weights and the network's Jacobian
-// stored by L1 (lw), and the spline base.
+// The inverse plane transforms of u_m have left N3 x N1 real rows at the start
+// of each plane of the spectrum buffer.  Per point: the 8 u values, the
+// channel weights and the network's Jacobian stored by L1 (lw), and the
+// spline base give v_loc and g.
 // mode 0: v_loc to v, w = g grad n to w_out; mode 1: v_loc to v, g to g_out
-// (the plane transforms of w follow in k_w_planes); mode 2: only the
-// real-space u_m to U (parameter gradient).
-template <int CN1, int CN3>
-__global__ void __cluster_dims__(1, L_CTAS, 1) __launch_bounds__(L_THREADS, 2)
-    k_learned_assemble(const float2* __restrict__ spec, const float* __restrict__ n, const float* __restrict__ grad,
-                       GridArgs g, PointParams P, LearnedArgs la, const float2* __restrict__ tw,
-                       const float* __restrict__ lw, float* __restrict__ v, float* __restrict__ w_out,
-                       float* __restrict__ g_out, float* __restrict__ U, int mode) {
-    cg::cluster_group cluster = cg::this_cluster();
-    extern __shared__ __align__(128) unsigned char smraw[];
+// (the plane transforms of w follow in k_w_planes).
+__global__ void __launch_bounds__(256) k_learned_usum(const float* __restrict__ uf, const float* __restrict__ n,
+                                                      const float* __restrict__ grad, GridArgs g, PointParams P,
+                                                      LearnedArgs la, const float* __restrict__ lw,
+                                                      float* __restrict__ v, float* __restrict__ w_out,
+                                                      float* __restrict__ g_out, int mode) {
     __shared__ float qm[MAX_NQ];
-    float2* plane = reinterpret_cast<float2*>(smraw);
-    float2* tw1 = plane + g.N3 * g.Nh;
-    float2* tw3 = tw1 + g.N1;
-    const int y = blockIdx.x;
-    const int rank = (int)cluster.block_rank();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const long long N = g.N;
-    load_twiddles(tw1, tw, g.N1);
-    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
     for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
-    const float2* src = spec + ((long long)rank * g.N2 + y) * g.ncols;
-    for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     __syncthreads();
-    plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
-    float* pf = reinterpret_cast<float*>(plane);
-    if (mode == 2) {
-        for (int z = warp; z < g.N3; z += nw) {
-            const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-            const float* srow = pf + packed_row(z, g.Nh);
-            for (int x = lane; x < g.N1; x += 32) U[(long long)rank * N + row + x] = srow[2 * x];
-        }
-        return;
-    }
-    const float* rem[L_CTAS];
+    const long long N = g.N;
+    const long long fstride = 2LL * g.N2 * g.ncols;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int y, z, x, j;
+        const long long gi = packed_point(q, g, y, z, x, j);
+        const float ni = n[gi];
+        const float gx = grad[gi], gy = grad[N + gi], gz = grad[2 * N + gi];
+        const Feat f = features(ni, gx, gy, gz, la, P.n_min);
+        float vl = 0.f, gg = 0.f;
+        if (f.ok) {
+            const float* up = uf + 2LL * y * g.ncols + (long long)z * g.N1 + x;
+            float u[LRN_M];
 #pragma unroll
-    for (int m = 0; m < L_CTAS; ++m) rem[m] = cluster.map_shared_rank(pf, m);
-    cluster.sync();  // every channel's u is in place
-    for (int z = rank + L_CTAS * warp; z < g.N3; z += L_CTAS * nw) {
-        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-        const int off0 = packed_row(z, g.Nh);
-        for (int x = lane; x < g.N1; x += 32) {
-            const long long gi = row + x;
-            const float ni = n[gi];
-            const float gx = grad[gi], gy = grad[N + gi], gz = grad[2 * N + gi];
-            const Feat f = features(ni, gx, gy, gz, la, P.n_min);
-            float vl = 0.f, gg = 0.f;
-            if (f.ok) {
-                float u[LRN_M];
+            for (int m = 0; m < LRN_M; ++m) u[m] = up[m * fstride];
+            const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
+            float dEn = 0.f, dEg = 0.f, bn = 0.f, bg = 0.f;
+            float pb[LRN_M], dpb[LRN_M];
 #pragma unroll
-                for (int m = 0; m < LRN_M; ++m) u[m] = rem[m][off0 + 2 * x];
-                const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
-                float dEn = 0.f, dEg = 0.f, bn = 0.f, bg = 0.f;
-                float pb[LRN_M], dpb[LRN_M];
-#pragma unroll
-                for (int m = 0; m < LRN_M; ++m) pb[m] = dpb[m] = 0.f;
-                if (qp.k != K_INVALID) {
-                    const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
-                    const float cn = 1.5f * P.C_s * ni * ni / q4;
-                    dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
-                    dEg = -cn * qp.dq_dg;
-                    if (la.base && base_weights(q, la, pb, dpb)) {
-                        bn = qp.dq_dn;
-                        bg = qp.dq_dg;
-                    }
+            for (int m = 0; m < LRN_M; ++m) pb[m] = dpb[m] = 0.f;
+            if (qp.k != K_INVALID) {
+                const float qq = qp.q, q3 = qq * qq * qq, q4 = q3 * qq;
+                const float cn = 1.5f * P.C_s * ni * ni / q4;
+                dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
+                dEg = -cn * qp.dq_dg;
+                if (la.base && base_weights(qq, la, pb, dpb)) {
+                    bn = qp.dq_dn;
+                    bg = qp.dq_dg;
                 }
-                float s0 = 0.f, s1 = 0.f, c1 = 0.f, c2 = 0.f;
+            }
+            float s0 = 0.f, s1 = 0.f, c1 = 0.f, c2 = 0.f;
 #pragma unroll
-                for (int m = 0; m < LRN_M; ++m) {
-                    s0 = fmaf(u[m], lw[m * N + gi], s0);
-                    s1 = fmaf(u[m], dpb[m], s1);
-                    c1 = fmaf(u[m], lw[(LRN_M + m) * N + gi], c1);
-                    c2 = fmaf(u[m], lw[(2 * LRN_M + m) * N + gi], c2);
-                }
-                vl = s0 + ni * (c1 * f.dx1_dn + c2 * f.dx2_dn + s1 * bn) + dEn;
-                gg = ni * (c2 * f.gx2 + s1 * bg) + dEg;
+            for (int m = 0; m < LRN_M; ++m) {
+                s0 = fmaf(u[m], lw[m * N + q], s0);
+                s1 = fmaf(u[m], dpb[m], s1);
+                c1 = fmaf(u[m], lw[(LRN_M + m) * N + q], c1);
+                c2 = fmaf(u[m], lw[(2 * LRN_M + m) * N + q], c2);
             }
-            if (v) v[gi] = vl;
-            if (mode == 0 && w_out) {
-                w_out[gi] = gg * gx;
-                w_out[N + gi] = gg * gy;
-                w_out[2 * N + gi] = gg * gz;
-            }
-            if (mode == 1) g_out[gi] = gg;
+            vl = s0 + ni * (c1 * f.dx1_dn + c2 * f.dx2_dn + s1 * bn) + dEn;
+            gg = ni * (c2 * f.gx2 + s1 * bg) + dEg;
         }
+        if (v) v[gi] = vl;
+        if (mode == 0 && w_out) {
+            w_out[gi] = gg * gx;
+            w_out[N + gi] = gg * gy;
+            w_out[2 * N + gi] = gg * gz;
+        }
+        if (mode == 1) g_out[gi] = gg;
     }
-    cluster.sync();  // keep u alive until every block is done reading it
+}
+
+// real-space u_m of the in-place planes -> U[m][N] (flat order), for the
+// parameter gradient
+__global__ void __launch_bounds__(256) k_u_fields(const float* __restrict__ uf, GridArgs g, float* __restrict__ U) {
+    const long long N = g.N;
+    const long long fstride = 2LL * g.N2 * g.ncols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / g.N1;
+        const int x = (int)(i - r * g.N1);
+        const int z = (int)(r / g.N2), y = (int)(r - (long long)z * g.N2);
+        const float* up = uf + 2LL * y * g.ncols + (long long)z * g.N1 + x;
+#pragma unroll
+        for (int m = 0; m < LRN_M; ++m) U[m * N + i] = up[m * fstride];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1035,9 +1016,16 @@ __global__ void k_adam(float* __restrict__ p, const double* __restrict__ g, floa
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t smem_cluster(const GridArgs& g, bool assemble) {
-    // the assembly holds one plane; the network side also its operands
-    return plane_bytes(g.N3, g.Nh, g.N1) + (assemble ? 0 : sizeof(MlpShared) + 2 * sizeof(MlpWG3));
+// the network kernel: its shared block and the two warpgroups' operands.  It
+// allocates all 512 tensor-memory columns of its SM, so the request is at
+// least 116 KB: a second block never fits beside it.
+size_t smem_net() { return std::max(sizeof(MlpShared) + 2 * sizeof(MlpWG3), (size_t)116 * 1024); }
+// network blocks: one per SM, at most the partial-sum slots of the epart scratch
+int net_blocks(vdw_ctx* c) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, std::min(nsm, c->g.N2 * L_SLOTS));
 }
 int contract_cols(const GridArgs& g) {
     int C = 8;
@@ -1066,42 +1054,17 @@ int set_smem(K kernel, size_t bytes, const char* name) {
     return VDW_OK;
 }
 
-template <class K>
-int cluster_fits(K kernel, const GridArgs& g, size_t smem, const char* name) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g.N2, L_CTAS);
-    cfg.blockDim = dim3(L_THREADS);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute at;
-    at.id = cudaLaunchAttributeClusterDimension;
-    at.val.clusterDim.x = 1;
-    at.val.clusterDim.y = L_CTAS;
-    at.val.clusterDim.z = 1;
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    VDW_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg));
-    if (nclusters < 1) {
-        set_error(std::string(name) + ": a cluster of 8 blocks does not fit");
-        return VDW_ERR_UNSUPPORTED;
-    }
-    return VDW_OK;
-}
-
 template <int CN1, int CN2, int CN3>
 int configure(vdw_ctx* c) {
     const GridArgs& g = c->g;
     const int C = contract_cols(g);
-    int rc = set_smem(k_learned_theta<CN1, CN3>, smem_cluster(g, false), "k_learned_theta");
-    if (!rc) rc = set_smem(k_learned_assemble<CN1, CN3>, smem_cluster(g, true), "k_learned_assemble");
+    int rc = set_smem(k_learned_net, smem_net(), "k_learned_net");
     if (!rc) rc = set_smem(k_learned_contract<CN2, false>, smem_contract(g, C, false, c->lrn_J), "k_learned_contract");
     if (!rc) rc = set_smem(k_learned_contract<CN2, true>, smem_contract(g, C, true, c->lrn_J), "k_learned_contract");
     if (!rc) rc = set_smem(k_field_plane<CN1, CN3>, smem_plane1(g), "k_field_plane");
     if (!rc) rc = set_smem(k_plane_inv3<CN1, CN3>, smem_plane1(g), "k_plane_inv3");
     if (!rc) rc = set_smem(k_pencil_grad<CN2>, smem_pgrad_pencil(g), "k_pencil_grad");
     if (!rc) rc = set_smem(k_learned_param_grad, smem_pgrad(), "k_learned_param_grad");
-    if (!rc) rc = cluster_fits(k_learned_theta<CN1, CN3>, g, smem_cluster(g, false), "k_learned_theta");
-    if (!rc) rc = cluster_fits(k_learned_assemble<CN1, CN3>, g, smem_cluster(g, true), "k_learned_assemble");
     return rc;
 }
 
@@ -1127,8 +1090,9 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     const LearnedArgs& la = c->la;
     const int C = contract_cols(g);
     const int nb_c = (g.ncols + C - 1) / C;
-    const int nb0 = g.N2 * L_CTAS;
+    const int nb0 = net_blocks(c);
     double* ep = lrn_epart(c);
+    float* specf = reinterpret_cast<float*>(c->d_spec);
     const double Omega = c->L[0] * c->L[1] * c->L[2];
     // stage marks for vdw_profile_read: 1 network + channel planes, 2 pencils,
     // 3 energy, 4 assembly, 6 divergence (stages 0 and 5 are not separate)
@@ -1144,8 +1108,10 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     }
     VDW_CUDA(cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long), s));
     const bool want_pot = (v != nullptr) || (w != nullptr);
-    k_learned_theta<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, false), s>>>(
-        n, grad, g, P, la, c->d_tw, c->d_spec, ep, c->d_invalid, (want_pot && kind != RUN_GRAD) ? c->d_lw : nullptr);
+    k_learned_net<<<nb0, L_THREADS, smem_net(), s>>>(n, grad, g, P, la, specf, ep, c->d_invalid,
+                                                     (want_pot && kind != RUN_GRAD) ? c->d_lw : nullptr);
+    int rc = pipeline_planes_inplace(c, LRN_M, false, s);
+    if (rc) return rc;
     mark(1);
     if (kind == RUN_GRAD) {
         VDW_CUDA(cudaMemsetAsync(c->d_gK, 0, sizeof(double) * LRN_P * c->lrn_J, s));
@@ -1157,13 +1123,15 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     }
     mark(2);
     if (E) {
-        int rc = pipeline_energy_final(c, ep, nb0, nb_c, E, s);
+        rc = pipeline_energy_final(c, ep, nb0, nb_c, E, s);
         if (rc) return rc;
         mark(3);
     }
+    const int nb_pt = (int)std::min<long long>((g.N + 255) / 256, 1 << 16);
     if (kind == RUN_GRAD) {
-        k_learned_assemble<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, true), s>>>(
-            c->d_spec, n, grad, g, P, la, c->d_tw, nullptr, nullptr, nullptr, nullptr, c->d_U, 2);
+        rc = pipeline_planes_inplace(c, LRN_M, true, s);
+        if (rc) return rc;
+        k_u_fields<<<nb_pt, 256, 0, s>>>(specf, g, c->d_U);
         const double dOmega = Omega / (double)g.N;
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
@@ -1173,15 +1141,16 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
         k_axpy<<<36, 256, 0, s>>>(gout + LRN_OFF_K, c->d_gK, coef, LRN_P * c->lrn_J);
     } else if (want_pot) {
         const int mode = (w != nullptr) ? 0 : 1;
-        k_learned_assemble<CN1, CN3><<<dim3(g.N2, L_CTAS), L_THREADS, smem_cluster(g, true), s>>>(
-            c->d_spec, n, grad, g, P, la, c->d_tw, c->d_lw, v, w, c->d_gg, nullptr, mode);
+        rc = pipeline_planes_inplace(c, LRN_M, true, s);
+        if (rc) return rc;
+        k_learned_usum<<<nb_pt, 256, 0, s>>>(specf, n, grad, g, P, la, c->d_lw, v, w, c->d_gg, mode);
         if (mode == 1) {
-            int rc = pipeline_w_planes(c, grad, s);
+            rc = pipeline_w_planes(c, grad, s);
             if (rc) return rc;
         }
         mark(4);
         if (mode == 1) {
-            int rc = pipeline_divergence(c, v, s);
+            rc = pipeline_divergence(c, v, s);
             if (rc) return rc;
             mark(6);
         }
@@ -1233,7 +1202,7 @@ static LrnLayout lrn_layout(const GridArgs& g, int J) {
         o = (o + bytes + 255) & ~(size_t)255;
         return at;
     };
-    L.epart = take(sizeof(double) * ((size_t)g.N2 * L_CTAS + g.ncols + 1));
+    L.epart = take(sizeof(double) * ((size_t)g.N2 * L_SLOTS + g.ncols + 1));
     L.w1 = take(sizeof(float) * 2 * LRN_H);
     L.b1 = take(sizeof(float) * LRN_H);
     L.b2 = take(sizeof(float) * LRN_H);

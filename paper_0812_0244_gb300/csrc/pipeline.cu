@@ -8,7 +8,7 @@
 //                       per G: u_a(G) = sum_b phi_ab(|G|) theta_b(G) with phi_ab
 //                       from the radial table, energy of Eq. (Eoffk) in FP64,
 //                       inverse C2C along y (Eqs. epsilon, epsofk)
-//   P3 k_u_planes       inverse plane transform of u_a (in place)
+//   P3 k_planes_inplace inverse plane transform of u_a (in place)
 //      k_u_sum          Eq. (Vi) per point: v_loc and g of w = g grad n
 //      k_w_planes       forward plane transform of w
 //   P4 k_pencil_div     y transform of w, i G' . w(G), inverse y transform
@@ -231,11 +231,15 @@ __global__ void __launch_bounds__(CONTRACT_THREADS, 2) k_pencil_contract(float2*
 // ---------------------------------------------------------------------------
 // P3: inverse plane transforms of u_a, in place
 // ---------------------------------------------------------------------------
-// One block per (y plane, field): the plane of u_a(G) arrives by one bulk
-// asynchronous copy (completion counted on an mbarrier) while the twiddles
-// load, goes through the inverse z and x transforms, and its N3 x N1 real
-// values (unscaled: 1/N is folded into the contraction) overwrite the start of
-// the same plane of the spectrum buffer, rows of N1 floats.
+// One block per (y plane, field): the plane arrives by one bulk asynchronous
+// copy (completion counted on an mbarrier) while the twiddles load.
+// Inverse: the plane of u_a(G) goes through the inverse z and x transforms,
+// and its N3 x N1 real values (unscaled: 1/N is folded into the contraction)
+// overwrite the start of the same plane of the spectrum buffer, rows of N1
+// floats.  Forward: the plane holds real rows in the packed layout of the
+// plane transforms (real rows 2j and 2j+1 as the real and imaginary parts of
+// complex row j, rows of 2 Nh complex values) and is replaced by its half
+// spectrum.
 __device__ __forceinline__ void mbar_init1(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
 }
@@ -266,10 +270,10 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
     return false;
 }
 
-template <int CN1, int CN3>
-__global__ void __launch_bounds__(PLANE_THREADS, 2) k_u_planes(float2* __restrict__ spec, GridArgs g,
-                                                               const float2* __restrict__ tw, int bulk,
-                                                               int* __restrict__ wait_err) {
+template <int CN1, int CN3, bool INV>
+__global__ void __launch_bounds__(PLANE_THREADS, 2) k_planes_inplace(float2* __restrict__ spec, GridArgs g,
+                                                                     const float2* __restrict__ tw, int bulk,
+                                                                     int* __restrict__ wait_err) {
     extern __shared__ float2 sm[];
     __shared__ uint64_t bar;
     float2* plane = sm;
@@ -294,13 +298,18 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_u_planes(float2* __restric
         atomicExch(wait_err, 1);
         mbar_wait_parity(&bar, 0u);
     }
-    plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
-    const float* pf = reinterpret_cast<const float*>(plane);
-    float* dst = reinterpret_cast<float*>(src);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int z = warp; z < g.N3; z += nw) {
-        const float* srow = pf + packed_row(z, g.Nh);
-        for (int x = lane; x < g.N1; x += 32) dst[z * g.N1 + x] = srow[2 * x];
+    if constexpr (INV) {
+        plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
+        const float* pf = reinterpret_cast<const float*>(plane);
+        float* dst = reinterpret_cast<float*>(src);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int z = warp; z < g.N3; z += nw) {
+            const float* srow = pf + packed_row(z, g.Nh);
+            for (int x = lane; x < g.N1; x += 32) dst[z * g.N1 + x] = srow[2 * x];
+        }
+    } else {
+        plane_forward<CN1, CN3>(plane, g, tw1, tw3);
+        for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) src[i] = plane[i];
     }
 }
 
@@ -308,7 +317,7 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_u_planes(float2* __restric
 // P3': the assembly of Eq. (Vi), one thread per point
 // ---------------------------------------------------------------------------
 // S0 = sum_a u_a p_a(q), S1 = sum_a u_a p_a'(q) from the real u_a planes left
-// in the spectrum buffer by k_u_planes; then
+// in the spectrum buffer by the inverse k_planes_inplace; then
 //   v_loc = S0 + n S1 dq/dn + d(Delta eps)/dn,   g = n S1 dq/d|grad n| / |grad n| + ...
 // mode 0: v_loc to v (if v), w = g grad n to w_out; mode 1: v_loc to v, g to
 // g_out (the plane transforms of w follow in k_w_planes).
@@ -773,8 +782,8 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
         k_semilocal<<<XC_BLOCKS, 256, 0, s>>>(n, grad, g.N, P.n_min, nullptr, nullptr, c->d_xc + 4);
     if (want_pot) {
         const int mode = (w != nullptr) ? 0 : 1;
-        k_u_planes<CN1, CN3><<<dim3(g.N2, P.Nq), PLANE_THREADS, sp, s>>>(c->d_spec, g, c->d_tw, c->bulk_planes,
-                                                                         c->d_flags);
+        k_planes_inplace<CN1, CN3, true><<<dim3(g.N2, P.Nq), PLANE_THREADS, sp, s>>>(c->d_spec, g, c->d_tw,
+                                                                                     c->bulk_planes, c->d_flags);
         const int rcs = launch_u_sum(c, n, grad, v, w, mode, s);
         if (rcs) return rcs;
         if (xc)
@@ -824,7 +833,8 @@ static int configure_sized(vdw_ctx* c) {
     const int sd = (int)smem_pencil_run(g, 3, DIV_COLS), sc = (int)smem_pencil_run(g, c->p.Nq, c->pencil_cols);
     const int tc = contract_threads(g, c->pencil_cols);
     int rc = set_and_check(k_theta_plane<CN1, CN3>, "k_theta_plane", (int)smem_theta(g), PLANE_THREADS);
-    if (!rc) rc = set_and_check(k_u_planes<CN1, CN3>, "k_u_planes", sp, PLANE_THREADS);
+    if (!rc) rc = set_and_check(k_planes_inplace<CN1, CN3, true>, "k_planes_inplace", sp, PLANE_THREADS);
+    if (!rc) rc = set_and_check(k_planes_inplace<CN1, CN3, false>, "k_planes_inplace", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_pencil_div<CN2>, "k_pencil_div", sd, 256);
     if (!rc) rc = set_and_check(k_div_final<CN1, CN3>, "k_div_final", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_w_planes<CN1, CN3>, "k_w_planes", sp, PLANE_THREADS);
@@ -865,6 +875,26 @@ int pipeline_w_planes(vdw_ctx* c, const float* grad, cudaStream_t s) {
     if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) launch_w_planes<180, 72>(c, grad, s);
     else if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) launch_w_planes<256, 96>(c, grad, s);
     else launch_w_planes<0, 0>(c, grad, s);
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
+template <int CN1, int CN3>
+static void launch_planes_inplace(vdw_ctx* c, int nfields, bool inverse, cudaStream_t s) {
+    const GridArgs& g = c->g;
+    if (inverse)
+        k_planes_inplace<CN1, CN3, true><<<dim3(g.N2, nfields), PLANE_THREADS, smem_plane(g), s>>>(
+            c->d_spec, g, c->d_tw, c->bulk_planes, c->d_flags);
+    else
+        k_planes_inplace<CN1, CN3, false><<<dim3(g.N2, nfields), PLANE_THREADS, smem_plane(g), s>>>(
+            c->d_spec, g, c->d_tw, c->bulk_planes, c->d_flags);
+}
+
+int pipeline_planes_inplace(vdw_ctx* c, int nfields, bool inverse, cudaStream_t s) {
+    const GridArgs& g = c->g;
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) launch_planes_inplace<180, 72>(c, nfields, inverse, s);
+    else if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) launch_planes_inplace<256, 96>(c, nfields, inverse, s);
+    else launch_planes_inplace<0, 0>(c, nfields, inverse, s);
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
 }
