@@ -53,8 +53,8 @@ def measured_peaks():
 def stage_bytes_per_point(Nq, N1):
     h = (N1 // 2 + 1) / N1
     return {
-        "pointwise": 16 + 5,                       # n, grad in; t, k out
-        "theta_plane": 9 + Nq * 8 * h,             # n, t, k in; theta(G) out
+        "pointwise": 16 + 5 + Nq * 4,              # n, grad in; t, k and real theta out
+        "theta_plane": Nq * 4 + Nq * 8 * h,        # real theta in; theta(G) out
         "pencil_contract": 2 * Nq * 8 * h,         # theta(G) in, u(G) out
         "energy_final": 0.0,
         # inverse plane transforms: u(G) in, real u out; the sum: real u, n,

@@ -382,22 +382,6 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
 // ---------------------------------------------------------------------------
 // L1: network and channels
 // ---------------------------------------------------------------------------
-// Points in packed order: q = ((y (N3/2) + j) N1 + x) 2 + s is the point
-// (x, y, z = 2j + s).  Writing theta_m in this order fills the packed real
-// rows of the plane transforms (real rows 2j and 2j + 1 interleaved in complex
-// row j) with consecutive addresses; returns the flat index (z N2 + y) N1 + x.
-__device__ __forceinline__ long long packed_point(long long q, const GridArgs& g, int& y, int& z, int& x, int& j) {
-    const int s = (int)(q & 1);
-    const long long t = q >> 1;
-    const long long rr = t / g.N1;
-    x = (int)(t - rr * g.N1);
-    const int nh3 = g.N3 >> 1;
-    y = (int)(rr / nh3);
-    j = (int)(rr - (long long)y * nh3);
-    z = 2 * j + s;
-    return ((long long)z * g.N2 + y) * g.N1 + x;
-}
-
 // One persistent block per SM, two warpgroups, each running the network and
 // its two tangents on tiles of 128 points (packed order): layer 1 on CUDA
 // cores gives three bf16 operands in the tcgen05 core-matrix layout; layers 2
@@ -457,7 +441,7 @@ __global__ void __launch_bounds__(L_THREADS, 1)
         float o[LRN_M], J1[LRN_M], J2[LRN_M];
         if (!mlp_forward_jac(S, W, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, J1, J2, la.err)) break;
         if (in) {
-            float* dst = specf + 2LL * y * g.ncols + 4 * j * g.Nh + 2 * x + (z & 1);
+            float* dst = specf + 2LL * y * g.ncols + packed_offset(x, j, z & 1, g.Nh);
 #pragma unroll
             for (int m = 0; m < LRN_M; ++m) dst[m * fstride] = ok ? ni * (o[m] + pb[m]) : 0.f;
             if (lw) {

@@ -1,9 +1,11 @@
 // The hot path of the Roman-Perez--Soler evaluation on one GB300.
 //
 //   P0 k_pointwise      n, grad n -> q, mesh interval k, position t (Eq. Sat,
-//                       Eq. fofx); Delta E partial sums (Eqs. DEnl, Depsnl)
-//   P1 k_theta_plane    theta_a = n p_a(q) (text after Eq. Eoffk) on one xz
-//                       plane, R2C along x and C2C along z in shared memory
+//                       Eq. fofx), theta_a = n p_a(q) (text after Eq. Eoffk)
+//                       into packed real planes; Delta E partial sums
+//                       (Eqs. DEnl, Depsnl)
+//   P1 k_planes_inplace forward plane transforms of theta_a in place: R2C
+//                       along x and C2C along z in shared memory
 //   P2 k_pencil_contract  C2C along y of all Nq fields of a few columns, then
 //                       per G: u_a(G) = sum_b phi_ab(|G|) theta_b(G) with phi_ab
 //                       from the radial table, energy of Eq. (Eoffk) in FP64,
@@ -42,25 +44,40 @@ constexpr int XC_BLOCKS = 1024;  // blocks (and partial-sum slots) of the semilo
 // ---------------------------------------------------------------------------
 // P0: pointwise
 // ---------------------------------------------------------------------------
+// q, its mesh interval k and position t per point (flat order out), theta_a
+// = n p_a(q) (text after Eq. Eoffk) into the packed real rows of the
+// spectrum buffer, and the Delta E partial sums.
+template <int NQ>
 __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, const float* __restrict__ grad,
-                                                   long long N, PointParams P, float* __restrict__ t_out,
-                                                   uint8_t* __restrict__ k_out, double* __restrict__ epart,
+                                                   GridArgs g, PointParams P, float* __restrict__ t_out,
+                                                   uint8_t* __restrict__ k_out, float* __restrict__ specf,
+                                                   double* __restrict__ epart,
                                                    unsigned long long* __restrict__ invalid) {
     __shared__ double red[32];
-    __shared__ float qm[MAX_NQ];
-    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
+    __shared__ SplineSmem sp;
+    load_spline_smem(&sp, P);
     __syncthreads();
+    const long long N = g.N;
+    const long long fstride = 2LL * g.N2 * g.ncols;  // floats between the planes of two fields
     double acc = 0.0;
     unsigned int bad = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int y, z, x, j;
+        const long long i = packed_point(q, g, y, z, x, j);
         const float ni = n[i];
         bad += (!(ni >= 0.f) || !isfinite(ni)) ? 1u : 0u;
-        const QPoint qp = q_point(ni, grad[i], grad[N + i], grad[2 * N + i], P, qm);
+        const QPoint qp = q_point(ni, grad[i], grad[N + i], grad[2 * N + i], P, sp.qm);
         t_out[i] = qp.t;
         k_out[i] = (uint8_t)qp.k;
+        float* dst = specf + 2LL * y * g.ncols + packed_offset(x, j, z & 1, g.Nh);
         if (qp.k != K_INVALID) {
             const float q3 = qp.q * qp.q * qp.q;
             acc += (double)(0.5f * P.C_s * ni * ni / q3);
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) dst[a * fstride] = ni * cardinal_value(&sp, a, qp.k, qp.t);
+        } else {
+#pragma unroll
+            for (int a = 0; a < NQ; ++a) dst[a * fstride] = 0.f;
         }
     }
     const double s = block_sum(acc, red);
@@ -70,52 +87,7 @@ __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, 
     if (threadIdx.x == 0 && b > 0.0) atomicAdd(invalid, (unsigned long long)b);
 }
 
-// ---------------------------------------------------------------------------
-// P1: theta_a planes, forward plane transform
-// ---------------------------------------------------------------------------
-// Fields per block (one plane each in shared memory).  Two fields per block
-// share the loads of n, t, k but spill registers in the transforms and were
-// slower at 180 x 180 x 72 (0.47 ms against 0.43 ms).
-constexpr int THETA_FIELDS = 1;
-
-template <int CN1, int CN3>
-__global__ void __launch_bounds__(PLANE_THREADS, 2) k_theta_plane(const float* __restrict__ n, const float* __restrict__ tk,
-                                                        const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
-                                                        const float2* __restrict__ tw, float2* __restrict__ spec) {
-    extern __shared__ float2 sm[];
-    __shared__ SplineSmem sp;
-    const int pe = g.N3 * g.Nh;
-    float2* tw1 = sm + THETA_FIELDS * pe;
-    float2* tw3 = tw1 + g.N1;
-    const int y = blockIdx.x, a0 = blockIdx.y * THETA_FIELDS;
-    load_twiddles(tw1, tw, g.N1);
-    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
-    load_spline_smem(&sp, P);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int z = warp; z < g.N3; z += nw) {
-        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-        const int off = packed_row(z, g.Nh);
-        for (int x = lane; x < g.N1; x += 32) {
-            const int k = kk[row + x];
-            const float t = tk[row + x], ni = n[row + x];
-#pragma unroll
-            for (int f = 0; f < THETA_FIELDS; ++f) {
-                float th = 0.f;
-                if (k != K_INVALID) th = ni * cardinal_value(&sp, a0 + f, k, t);
-                reinterpret_cast<float*>(sm + f * pe)[off + 2 * x] = th;
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int f = 0; f < THETA_FIELDS; ++f) {
-        float2* plane = sm + f * pe;
-        plane_forward<CN1, CN3>(plane, g, tw1, tw3);
-        float2* dst = spec + ((long long)(a0 + f) * g.N2 + y) * g.ncols;
-        for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) dst[i] = plane[i];
-    }
-}
+// P1 (the forward plane transforms of theta_a) is k_planes_inplace below.
 
 // ---------------------------------------------------------------------------
 // P2: pencils along y, contraction with the radial kernel table, energy
@@ -643,9 +615,6 @@ int make_line_plan(int n, LinePlan* lp) {
 }
 
 static size_t smem_plane(const GridArgs& g) { return sizeof(float2) * ((size_t)g.N3 * g.Nh + g.N1 + g.N3); }
-static size_t smem_theta(const GridArgs& g) {
-    return sizeof(float2) * ((size_t)THETA_FIELDS * g.N3 * g.Nh + g.N1 + g.N3);
-}
 static size_t smem_pencil(const GridArgs& g, int nq, int C) { return sizeof(float2) * ((size_t)nq * C * g.N2 + g.N2); }
 static size_t smem_pencil_run(const GridArgs& g, int nq, int C) { return smem_pencil(g, nq, C); }
 
@@ -674,7 +643,7 @@ int pipeline_plan_check(vdw_ctx* c, size_t* sp, size_t* spen, size_t* sa, size_t
     c->bulk_planes = (sizeof(float2) * (size_t)g.ncols) % 16 == 0;
     *sa = *sp;
     *sd = smem_pencil_run(g, 3, DIV_COLS);
-    if (*sp > SMEM_MAX || smem_theta(g) > SMEM_MAX || *spen > SMEM_MAX || *sd > SMEM_MAX)
+    if (*sp > SMEM_MAX || *spen > SMEM_MAX || *sd > SMEM_MAX)
         return VDW_ERR_SIZE;
     return VDW_OK;
 }
@@ -760,12 +729,22 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
         cudaEventRecord(c->ev[0], s);
     }
     VDW_CUDA(cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long), s));
-    k_pointwise<<<c->nb_point, 256, 0, s>>>(n, grad, g.N, P, c->d_t, c->d_k, c->d_epart, c->d_invalid);
+    float* specf = reinterpret_cast<float*>(c->d_spec);
+#define VDW_POINTWISE(NQ)                                                                                  \
+    k_pointwise<NQ><<<c->nb_point, 256, 0, s>>>(n, grad, g, P, c->d_t, c->d_k, specf, c->d_epart, c->d_invalid)
+    switch (P.Nq) {
+        case 20: VDW_POINTWISE(20); break;
+        case 8: VDW_POINTWISE(8); break;
+        case 12: VDW_POINTWISE(12); break;
+        case 16: VDW_POINTWISE(16); break;
+        default: set_error("Nq not compiled in"); return VDW_ERR_UNSUPPORTED;
+    }
+#undef VDW_POINTWISE
     mark(0);
 
     const size_t sp = smem_plane(g);
-    k_theta_plane<CN1, CN3><<<dim3(g.N2, P.Nq / THETA_FIELDS), PLANE_THREADS, smem_theta(g), s>>>(
-        n, c->d_t, c->d_k, g, P, c->d_tw, c->d_spec);
+    k_planes_inplace<CN1, CN3, false><<<dim3(g.N2, P.Nq), PLANE_THREADS, sp, s>>>(c->d_spec, g, c->d_tw,
+                                                                                  c->bulk_planes, c->d_flags);
     mark(1);
 
     int rc = launch_contract_nq<CN2>(c, s, want_pot ? 1 : 0);
@@ -832,8 +811,7 @@ static int configure_sized(vdw_ctx* c) {
     const int sp = (int)smem_plane(g);
     const int sd = (int)smem_pencil_run(g, 3, DIV_COLS), sc = (int)smem_pencil_run(g, c->p.Nq, c->pencil_cols);
     const int tc = contract_threads(g, c->pencil_cols);
-    int rc = set_and_check(k_theta_plane<CN1, CN3>, "k_theta_plane", (int)smem_theta(g), PLANE_THREADS);
-    if (!rc) rc = set_and_check(k_planes_inplace<CN1, CN3, true>, "k_planes_inplace", sp, PLANE_THREADS);
+    int rc = set_and_check(k_planes_inplace<CN1, CN3, true>, "k_planes_inplace", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_planes_inplace<CN1, CN3, false>, "k_planes_inplace", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_pencil_div<CN2>, "k_pencil_div", sd, 256);
     if (!rc) rc = set_and_check(k_div_final<CN1, CN3>, "k_div_final", sp, PLANE_THREADS);

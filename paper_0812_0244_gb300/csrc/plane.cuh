@@ -67,6 +67,25 @@ __device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, c
 // ---------------------------------------------------------------------------
 // plane helpers (one y plane, N3 rows of N1 reals <-> N3 x Nh half spectrum)
 // ---------------------------------------------------------------------------
+// Points in packed order: q = ((y (N3/2) + j) N1 + x) 2 + s is the point
+// (x, y, z = 2j + s).  A field written in this order fills the packed real
+// rows of its y plane (real rows 2j and 2j + 1 interleaved in complex row j)
+// with consecutive addresses.  Sets (y, z, x, j); returns the flat index
+// (z N2 + y) N1 + x.
+__device__ __forceinline__ long long packed_point(long long q, const GridArgs& g, int& y, int& z, int& x, int& j) {
+    const int s = (int)(q & 1);
+    const long long t = q >> 1;
+    const long long rr = t / g.N1;
+    x = (int)(t - rr * g.N1);
+    const int nh3 = g.N3 >> 1;
+    y = (int)(rr / nh3);
+    j = (int)(rr - (long long)y * nh3);
+    z = 2 * j + s;
+    return ((long long)z * g.N2 + y) * g.N1 + x;
+}
+// float offset, within its plane, of real point (x, z = 2j + s) in the packed rows
+__device__ __forceinline__ int packed_offset(int x, int j, int s, int Nh) { return 4 * j * Nh + 2 * x + s; }
+
 // Real rows 2j and 2j+1 share the complex row at offset j (2 Nh), as real and
 // imaginary parts; this is the float offset of the start of real row z.
 __device__ __forceinline__ int packed_row(int z, int Nh) { return 2 * ((z >> 1) * 2 * Nh) + (z & 1); }
