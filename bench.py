@@ -53,13 +53,13 @@ def measured_peaks():
 def stage_bytes_per_point(Nq, N1):
     h = (N1 // 2 + 1) / N1
     return {
-        "pointwise": 16 + 5 + Nq * 4,              # n, grad in; t, k and real theta out
+        "pointwise": 16 + 5 + Nq * 4 + 16,         # n, grad in; t, k, real theta, assembly coefficients out
         "theta_plane": Nq * 4 + Nq * 8 * h,        # real theta in; theta(G) out
         "pencil_contract": 2 * Nq * 8 * h,         # theta(G) in, u(G) out
         "energy_final": 0.0,
-        # inverse plane transforms: u(G) in, real u out; the sum: real u, n,
-        # grad, t, k in, v_loc and g out; the w transforms: g, grad in, w(G) out
-        "assemble": Nq * 8 * h + Nq * 4 + Nq * 4 + 16 + 5 + 4 + 4 + 4 + 12 + 3 * 8 * h,
+        # inverse plane transforms: u(G) in, real u out; the sum: real u, t, k,
+        # coefficients in, v_loc and g out; the w transforms: g, grad in, w(G) out
+        "assemble": Nq * 8 * h + Nq * 4 + Nq * 4 + 5 + 16 + 4 + 4 + 4 + 12 + 3 * 8 * h,
         "pencil_div": 3 * 8 * h + 8 * h,           # w(G) in, D.w(G) out
         "div_final": 8 * h + 4 + 4,                # D.w(G), v_loc in; v out
     }

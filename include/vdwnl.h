@@ -169,9 +169,10 @@ int vdw_last_invalid_points(vdw_handle h, long long* count);
 
 /* Per-stage timing, for measurement.  While enabled, vdw_energy_potential
  * records a CUDA event on its stream before its first kernel and after each
- * stage: 0 pointwise (q, interval, Delta E), 1 theta planes + plane FFT,
+ * stage: 0 pointwise (q, interval, theta, Delta E), 1 forward plane FFT,
  * 2 pencil FFT + contraction + energy, 3 energy reduction, 4 inverse plane
- * FFT + potential assembly, 5 divergence pencils, 6 final planes.
+ * FFT + potential assembly + plane FFT of w, 5 divergence pencils, 6 final
+ * planes.
  * vdw_profile_read synchronises on the last recorded event and writes the
  * durations (ms) of the stages the last call ran into ms[0..6] (-1 for stages
  * it skipped).  Disabled by default; enabling costs 8 event records a call. */

@@ -30,6 +30,7 @@ static void free_plan(vdw_ctx* c) {
     cudaFree(c->d_wspec);
     cudaFree(c->d_t);
     cudaFree(c->d_k);
+    cudaFree(c->d_aux);
     cudaFree(c->d_epart);
     cudaFree(c->d_invalid);
     cudaFree(c->d_in);
@@ -39,6 +40,7 @@ static void free_plan(vdw_ctx* c) {
     c->d_spec = c->d_wspec = nullptr;
     c->d_t = nullptr;
     c->d_k = nullptr;
+    c->d_aux = nullptr;
     c->d_epart = nullptr;
     c->d_invalid = nullptr;
     c->d_in = c->d_v = nullptr;
@@ -176,6 +178,7 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     VDW_CUDA(cudaMalloc(&c->d_wspec, sizeof(float2) * 3 * (size_t)n2 * g.ncols));
     VDW_CUDA(cudaMalloc(&c->d_t, sizeof(float) * g.N));
     VDW_CUDA(cudaMalloc(&c->d_k, g.N));
+    VDW_CUDA(cudaMalloc(&c->d_aux, sizeof(float4) * (size_t)g.N));
     VDW_CUDA(cudaMalloc(&c->d_epart, sizeof(double) * (c->nb_point + c->nb_pencil)));
     VDW_CUDA(cudaMalloc(&c->d_invalid, sizeof(unsigned long long)));
     VDW_CUDA(cudaMalloc(&c->d_gg, sizeof(float) * (size_t)g.N));
@@ -189,7 +192,7 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     if (rc) return rc;
     const int npairs = Nq * (Nq + 1) / 2;
     c->bytes = sizeof(float4) * (size_t)(c->p.Nk - 1) * npairs + sizeof(float2) * (n1 + n2 + n3) +
-               sizeof(float2) * (spec_n + 3 * (size_t)n2 * g.ncols) + 5 * (size_t)g.N +
+               sizeof(float2) * (spec_n + 3 * (size_t)n2 * g.ncols) + 21 * (size_t)g.N +
                sizeof(double) * (c->nb_point + c->nb_pencil) +
                4 * (size_t)g.N + sizeof(int);
     c->planned = 1;

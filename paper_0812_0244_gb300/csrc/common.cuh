@@ -99,6 +99,7 @@ struct vdw_ctx {
     float2* d_wspec;            // [3][N2][N3][Nh] w(G); component 0 then D.w
     float* d_t;                 // [N] position of q inside its mesh interval
     uint8_t* d_k;               // [N] mesh interval of q (K_INVALID: theta = 0)
+    float4* d_aux;              // [N] n dq/dn, n dq/d|grad n| / |grad n|, and the Delta E derivatives
     double* d_epart;            // per-block energy partial sums
     int nb_point, nb_pencil;    // their counts (pointwise, pencil kernels)
     unsigned long long* d_invalid;  // count of negative / non-finite densities
@@ -120,7 +121,7 @@ struct vdw_ctx {
     void* d_lrn;                // one allocation behind the LearnedArgs pointers
     vdw::LearnedArgs la;
     float* d_U;                 // [M][N] real-space u_m for the parameter gradient (on first use)
-    float* d_lw;                // [3M][N] channel weights and network Jacobian for the assembly (on first use)
+    float* d_lw;                // [2M + 2][N] per-point coefficients of the learned assembly (on first use)
     double* d_gK;               // [P][J] knot-gradient accumulator (on first use)
     // per-stage timing (vdw_profile_enable)
     int prof;

@@ -114,17 +114,17 @@ __device__ __forceinline__ bool base_weights(float q, const LearnedArgs& la, flo
     int k = 0;  // knots <= q among the interior ones: interval in [0, M - 2]
 #pragma unroll
     for (int i = 1; i < LRN_M - 1; ++i) k += (qc >= la.bqm[i]) ? 1 : 0;
-    const float x0 = la.bqm[k], x1 = la.bqm[k + 1], h = x1 - x0;
-    const float A = (x1 - qc) / h, B = 1.f - A;
-    const float h6 = h * h / 6.f;
+    const float x0 = la.bqm[k], x1 = la.bqm[k + 1], h = x1 - x0, ih = 1.f / h;
+    const float A = (x1 - qc) * ih, B = 1.f - A;
+    const float h6 = h * h * (1.f / 6.f);
     const float cA = (A * A * A - A) * h6, cB = (B * B * B - B) * h6;
-    const float dA = -(3.f * A * A - 1.f) / 6.f * h, dB = (3.f * B * B - 1.f) / 6.f * h;
+    const float dA = -(3.f * A * A - 1.f) * (1.f / 6.f) * h, dB = (3.f * B * B - 1.f) * (1.f / 6.f) * h;
 #pragma unroll
     for (int m = 0; m < LRN_M; ++m) {
         const float Ma = la.bMq[m * LRN_M + k], Mb = la.bMq[m * LRN_M + k + 1];
         const float ya = (m == k) ? 1.f : 0.f, yb = (m == k + 1) ? 1.f : 0.f;
         p[m] = A * ya + B * yb + cA * Ma + cB * Mb;
-        dp[m] = (yb - ya) / h + dA * Ma + dB * Mb;
+        dp[m] = (yb - ya) * ih + dA * Ma + dB * Mb;
     }
     return inside;
 }
@@ -191,10 +191,10 @@ __device__ void mlp_teardown(MlpCtl* ctl) {
 }
 
 // Issue, for each of nA operands A[i] (K-wide), the K/16 MMAs of A[i] x B^T
-// into column col[i] of this warpgroup's tensor memory; wait for all of them,
-// and agree across the warpgroup on success.
-__device__ __forceinline__ bool wg_mma_n(MlpCtl* ctl, int wg, int r, uint32_t& phase, const uint16_t* const* A,
-                                         const uint32_t* col, int nA, const uint16_t* B, int K, int N, int* err) {
+// into column col[i] of this warpgroup's tensor memory (one elected thread,
+// one commit to the warpgroup's mbarrier).
+__device__ __forceinline__ void wg_mma_issue(MlpCtl* ctl, int wg, int r, const uint16_t* const* A, const uint32_t* col,
+                                             int nA, const uint16_t* B, int K, int N) {
     tc::fence_async_smem();
     tc::fence_before_sync();
     wg_bar(wg);
@@ -209,6 +209,9 @@ __device__ __forceinline__ bool wg_mma_n(MlpCtl* ctl, int wg, int r, uint32_t& p
         }
         tc::mma_commit(&ctl->bar[wg]);
     }
+}
+// Wait for the warpgroup's last commit and agree across the warpgroup on success.
+__device__ __forceinline__ bool wg_mma_wait(MlpCtl* ctl, int wg, uint32_t& phase, int* err) {
     const bool ok = tc::mbar_wait(&ctl->bar[wg], phase);
     phase ^= 1u;
     if (!ok) {
@@ -218,6 +221,11 @@ __device__ __forceinline__ bool wg_mma_n(MlpCtl* ctl, int wg, int r, uint32_t& p
     wg_bar(wg);
     tc::fence_after_sync();
     return ctl->abort[wg] == 0;
+}
+__device__ __forceinline__ bool wg_mma_n(MlpCtl* ctl, int wg, int r, uint32_t& phase, const uint16_t* const* A,
+                                         const uint32_t* col, int nA, const uint16_t* B, int K, int N, int* err) {
+    wg_mma_issue(ctl, wg, r, A, col, nA, B, K, N);
+    return wg_mma_wait(ctl, wg, phase, err);
 }
 
 __device__ __forceinline__ bool wg_mma(MlpCtl* ctl, int wg, int r, uint32_t& phase, const uint16_t* A,
@@ -271,8 +279,11 @@ __device__ bool mlp_forward(MlpShared* S, MlpWG* W, MlpCtl* ctl, int wg, int r, 
 // like the activations.  Tensor memory (256 columns per warpgroup): layer 2
 // in [0, 64), [64, 128), [128, 192); layer 3 in [0, 16), [16, 32), [32, 48).
 // Returns o (8 outputs) and J1, J2 (d o / d x1, d o / d x2).
+// overlap() runs on every thread of the warpgroup while the layer-2 MMAs are
+// in flight (work that does not depend on the network).
+template <class Overlap>
 __device__ bool mlp_forward_jac(MlpShared* S, MlpWG3* W, MlpCtl* ctl, int wg, int r, uint32_t& phase, float x1,
-                                float x2, float* o, float* J1, float* J2, int* err) {
+                                float x2, float* o, float* J1, float* J2, int* err, Overlap overlap) {
 #pragma unroll
     for (int c = 0; c < LRN_H / 8; ++c) {
         float h[8], t1[8], t2[8];
@@ -292,7 +303,9 @@ __device__ bool mlp_forward_jac(MlpShared* S, MlpWG3* W, MlpCtl* ctl, int wg, in
     {
         const uint16_t* As[3] = {W->A[0], W->A[1], W->A[2]};
         const uint32_t cols[3] = {0, 64, 128};
-        if (!wg_mma_n(ctl, wg, r, phase, As, cols, 3, S->w2f, LRN_H, LRN_H, err)) return false;
+        wg_mma_issue(ctl, wg, r, As, cols, 3, S->w2f, LRN_H, LRN_H);
+        overlap();
+        if (!wg_mma_wait(ctl, wg, phase, err)) return false;
     }
 #pragma unroll
     for (int c = 0; c < LRN_H / 16; ++c) {
@@ -388,9 +401,13 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
 // and 3 are 3 x 4 MMAs each into tensor memory, one commit and one wait per
 // layer.  theta_m = n w_m goes to the packed real rows of plane (m, y) of the
 // spectrum buffer (the forward plane transforms follow in place).  With lw
-// the channel weights and the network's Jacobian are stored for the
-// assembly, lw[c][q] in packed order: w_m, then d o_m / d x1, then
-// d o_m / d x2.  Delta E partial sums per block.
+// the per-point coefficients of the assembly of Eq. (Vi) are stored,
+// lw[c][q] in packed order (LW_ROWS rows): v_loc = sum_m u_m lw[m] + lw[2M]
+// and g = sum_m u_m lw[M + m] + lw[2M + 1], i.e.
+//   lw[m]     = w_m + n dw_m/dn          (network Jacobian through x1, x2; base through q)
+//   lw[M + m] = n (dw_m/d|grad n|)/|grad n|
+//   lw[2M], lw[2M + 1] = the Delta E derivatives.
+// Delta E partial sums per block.
 __global__ void __launch_bounds__(L_THREADS, 1)
     k_learned_net(const float* __restrict__ n, const float* __restrict__ grad, GridArgs g, PointParams P,
                   LearnedArgs la, float* __restrict__ specf, double* __restrict__ epart,
@@ -429,17 +446,30 @@ __global__ void __launch_bounds__(L_THREADS, 1)
         const bool ok = in && f.ok;
         float pb[LRN_M], dpb[LRN_M];
 #pragma unroll
-        for (int m = 0; m < LRN_M; ++m) pb[m] = 0.f;
-        if (in) {
-            bad += (!(ni >= 0.f) || !isfinite(ni)) ? 1u : 0u;
-            const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
-            if (qp.k != K_INVALID) {
-                eacc += (double)(0.5f * P.C_s * ni * ni / (qp.q * qp.q * qp.q));
-                if (la.base) base_weights(qp.q, la, pb, dpb);
+        for (int m = 0; m < LRN_M; ++m) pb[m] = dpb[m] = 0.f;
+        float bn = 0.f, bg = 0.f, dEn = 0.f, dEg = 0.f;
+        // q chain, Delta E and the spline base while the layer-2 MMAs run
+        auto qwork = [&]() {
+            if (in) {
+                bad += (!(ni >= 0.f) || !isfinite(ni)) ? 1u : 0u;
+                const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
+                if (qp.k != K_INVALID) {
+                    const float qq = qp.q, q3 = qq * qq * qq, q4 = q3 * qq;
+                    eacc += (double)(0.5f * P.C_s * ni * ni / q3);
+                    const float cn = 1.5f * P.C_s * ni * ni / q4;
+                    dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
+                    dEg = -cn * qp.dq_dg;
+                    // the clamped base has no q derivative
+                    if (la.base && base_weights(qq, la, pb, dpb)) {
+                        bn = qp.dq_dn;
+                        bg = qp.dq_dg;
+                    }
+                }
             }
-        }
+        };
         float o[LRN_M], J1[LRN_M], J2[LRN_M];
-        if (!mlp_forward_jac(S, W, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, J1, J2, la.err)) break;
+        if (!mlp_forward_jac(S, W, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, J1, J2, la.err, qwork))
+            break;
         if (in) {
             float* dst = specf + 2LL * y * g.ncols + packed_offset(x, j, z & 1, g.Nh);
 #pragma unroll
@@ -447,10 +477,13 @@ __global__ void __launch_bounds__(L_THREADS, 1)
             if (lw) {
 #pragma unroll
                 for (int m = 0; m < LRN_M; ++m) {
-                    lw[m * N + q] = ok ? o[m] + pb[m] : 0.f;
-                    lw[(LRN_M + m) * N + q] = J1[m];
-                    lw[(2 * LRN_M + m) * N + q] = J2[m];
+                    const float dwn = J1[m] * f.dx1_dn + J2[m] * f.dx2_dn + dpb[m] * bn;
+                    const float dwg = J2[m] * f.gx2 + dpb[m] * bg;
+                    lw[m * N + q] = ok ? o[m] + pb[m] + ni * dwn : 0.f;
+                    lw[(LRN_M + m) * N + q] = ok ? ni * dwg : 0.f;
                 }
+                lw[2 * LRN_M * N + q] = ok ? dEn : 0.f;
+                lw[(2 * LRN_M + 1) * N + q] = ok ? dEg : 0.f;
             }
         }
     }
@@ -599,64 +632,31 @@ __global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ s
 // L3: assembly of Eq. (Vi), one thread per point (packed order)
 // ---------------------------------------------------------------------------
 // The inverse plane transforms of u_m have left N3 x N1 real rows at the start
-// of each plane of the spectrum buffer.  Per point: the 8 u values, the
-// channel weights and the network's Jacobian stored by L1 (lw), and the
-// spline base give v_loc and g.
+// of each plane of the spectrum buffer.  Per point: v_loc and g from the 8 u
+// values and the coefficients the network pass stored in lw.
 // mode 0: v_loc to v, w = g grad n to w_out; mode 1: v_loc to v, g to g_out
 // (the plane transforms of w follow in k_w_planes).
-__global__ void __launch_bounds__(256) k_learned_usum(const float* __restrict__ uf, const float* __restrict__ n,
-                                                      const float* __restrict__ grad, GridArgs g, PointParams P,
-                                                      LearnedArgs la, const float* __restrict__ lw,
-                                                      float* __restrict__ v, float* __restrict__ w_out,
-                                                      float* __restrict__ g_out, int mode) {
-    __shared__ float qm[MAX_NQ];
-    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
-    __syncthreads();
+__global__ void __launch_bounds__(256) k_learned_usum(const float* __restrict__ uf, const float* __restrict__ grad,
+                                                      GridArgs g, const float* __restrict__ lw, float* __restrict__ v,
+                                                      float* __restrict__ w_out, float* __restrict__ g_out, int mode) {
     const long long N = g.N;
     const long long fstride = 2LL * g.N2 * g.ncols;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
         int y, z, x, j;
         const long long gi = packed_point(q, g, y, z, x, j);
-        const float ni = n[gi];
-        const float gx = grad[gi], gy = grad[N + gi], gz = grad[2 * N + gi];
-        const Feat f = features(ni, gx, gy, gz, la, P.n_min);
-        float vl = 0.f, gg = 0.f;
-        if (f.ok) {
-            const float* up = uf + 2LL * y * g.ncols + (long long)z * g.N1 + x;
-            float u[LRN_M];
+        const float* up = uf + 2LL * y * g.ncols + (long long)z * g.N1 + x;
+        float vl = lw[2 * LRN_M * N + q], gg = lw[(2 * LRN_M + 1) * N + q];
 #pragma unroll
-            for (int m = 0; m < LRN_M; ++m) u[m] = up[m * fstride];
-            const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
-            float dEn = 0.f, dEg = 0.f, bn = 0.f, bg = 0.f;
-            float pb[LRN_M], dpb[LRN_M];
-#pragma unroll
-            for (int m = 0; m < LRN_M; ++m) pb[m] = dpb[m] = 0.f;
-            if (qp.k != K_INVALID) {
-                const float qq = qp.q, q3 = qq * qq * qq, q4 = q3 * qq;
-                const float cn = 1.5f * P.C_s * ni * ni / q4;
-                dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
-                dEg = -cn * qp.dq_dg;
-                if (la.base && base_weights(qq, la, pb, dpb)) {
-                    bn = qp.dq_dn;
-                    bg = qp.dq_dg;
-                }
-            }
-            float s0 = 0.f, s1 = 0.f, c1 = 0.f, c2 = 0.f;
-#pragma unroll
-            for (int m = 0; m < LRN_M; ++m) {
-                s0 = fmaf(u[m], lw[m * N + q], s0);
-                s1 = fmaf(u[m], dpb[m], s1);
-                c1 = fmaf(u[m], lw[(LRN_M + m) * N + q], c1);
-                c2 = fmaf(u[m], lw[(2 * LRN_M + m) * N + q], c2);
-            }
-            vl = s0 + ni * (c1 * f.dx1_dn + c2 * f.dx2_dn + s1 * bn) + dEn;
-            gg = ni * (c2 * f.gx2 + s1 * bg) + dEg;
+        for (int m = 0; m < LRN_M; ++m) {
+            const float u = up[m * fstride];
+            vl = fmaf(u, lw[m * N + q], vl);
+            gg = fmaf(u, lw[(LRN_M + m) * N + q], gg);
         }
         if (v) v[gi] = vl;
         if (mode == 0 && w_out) {
-            w_out[gi] = gg * gx;
-            w_out[N + gi] = gg * gy;
-            w_out[2 * N + gi] = gg * gz;
+            w_out[gi] = gg * grad[gi];
+            w_out[N + gi] = gg * grad[N + gi];
+            w_out[2 * N + gi] = gg * grad[2 * N + gi];
         }
         if (mode == 1) g_out[gi] = gg;
     }
@@ -1127,7 +1127,7 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
         const int mode = (w != nullptr) ? 0 : 1;
         rc = pipeline_planes_inplace(c, LRN_M, true, s);
         if (rc) return rc;
-        k_learned_usum<<<nb_pt, 256, 0, s>>>(specf, n, grad, g, P, la, c->d_lw, v, w, c->d_gg, mode);
+        k_learned_usum<<<nb_pt, 256, 0, s>>>(specf, grad, g, c->d_lw, v, w, c->d_gg, mode);
         if (mode == 1) {
             rc = pipeline_w_planes(c, grad, s);
             if (rc) return rc;
@@ -1215,7 +1215,7 @@ void learned_free(vdw_ctx* c) {
 
 int learned_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s) {
     if (!lrn_ready(c)) return VDW_ERR_STATE;
-    if ((v || w) && !c->d_lw) VDW_CUDA(cudaMalloc(&c->d_lw, sizeof(float) * 3 * LRN_M * (size_t)c->g.N));
+    if ((v || w) && !c->d_lw) VDW_CUDA(cudaMalloc(&c->d_lw, sizeof(float) * (2 * LRN_M + 2) * (size_t)c->g.N));
     return run_any(c, n, grad, E, v, w, RUN_ENERGY, 0.0, nullptr, s);
 }
 

@@ -46,12 +46,14 @@ constexpr int XC_BLOCKS = 1024;  // blocks (and partial-sum slots) of the semilo
 // ---------------------------------------------------------------------------
 // q, its mesh interval k and position t per point (flat order out), theta_a
 // = n p_a(q) (text after Eq. Eoffk) into the packed real rows of the
-// spectrum buffer, and the Delta E partial sums.
+// spectrum buffer, and the Delta E partial sums.  aux (flat order) keeps
+// what the assembly of Eq. (Vi) needs besides the field sums:
+// {n dq/dn, n (dq/d|grad n|)/|grad n|, d(Delta eps)/dn, its grad n coefficient}.
 template <int NQ>
 __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, const float* __restrict__ grad,
                                                    GridArgs g, PointParams P, float* __restrict__ t_out,
-                                                   uint8_t* __restrict__ k_out, float* __restrict__ specf,
-                                                   double* __restrict__ epart,
+                                                   uint8_t* __restrict__ k_out, float4* __restrict__ aux,
+                                                   float* __restrict__ specf, double* __restrict__ epart,
                                                    unsigned long long* __restrict__ invalid) {
     __shared__ double red[32];
     __shared__ SplineSmem sp;
@@ -71,11 +73,14 @@ __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, 
         k_out[i] = (uint8_t)qp.k;
         float* dst = specf + 2LL * y * g.ncols + packed_offset(x, j, z & 1, g.Nh);
         if (qp.k != K_INVALID) {
-            const float q3 = qp.q * qp.q * qp.q;
+            const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
             acc += (double)(0.5f * P.C_s * ni * ni / q3);
+            const float cn = 1.5f * P.C_s * ni * ni / q4;
+            aux[i] = make_float4(ni * qp.dq_dn, ni * qp.dq_dg, P.C_s * ni / q3 - cn * qp.dq_dn, -cn * qp.dq_dg);
 #pragma unroll
             for (int a = 0; a < NQ; ++a) dst[a * fstride] = ni * cardinal_value(&sp, a, qp.k, qp.t);
         } else {
+            aux[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int a = 0; a < NQ; ++a) dst[a * fstride] = 0.f;
         }
@@ -289,16 +294,20 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_planes_inplace(float2* __r
 // P3': the assembly of Eq. (Vi), one thread per point
 // ---------------------------------------------------------------------------
 // S0 = sum_a u_a p_a(q), S1 = sum_a u_a p_a'(q) from the real u_a planes left
-// in the spectrum buffer by the inverse k_planes_inplace; then
-//   v_loc = S0 + n S1 dq/dn + d(Delta eps)/dn,   g = n S1 dq/d|grad n| / |grad n| + ...
+// in the spectrum buffer by the inverse k_planes_inplace.  On interval k with
+// A = 1 - t, B = t, p_a = A d_ak + B d_a,k+1 + [(A^3 - A) M_ak + (B^3 - B)
+// M_a,k+1] h^2/6 is linear in the second derivatives M, so both sums need
+// only u_k, u_k+1 and the two dot products m0 = sum_a u_a M_ak, m1 = sum_a
+// u_a M_a,k+1.  Then, with aux from the pointwise pass,
+//   v_loc = S0 + S1 n dq/dn + d(Delta eps)/dn,   g = S1 n dq/d|grad n| / |grad n| + ...
 // mode 0: v_loc to v (if v), w = g grad n to w_out; mode 1: v_loc to v, g to
 // g_out (the plane transforms of w follow in k_w_planes).
 constexpr int USUM_THREADS = 256;
 
 template <int NQ>
-__global__ void __launch_bounds__(USUM_THREADS) k_u_sum(const float* __restrict__ uf, const float* __restrict__ n,
-                                                        const float* __restrict__ grad, const float* __restrict__ tk,
-                                                        const uint8_t* __restrict__ kk, GridArgs g, PointParams P,
+__global__ void __launch_bounds__(USUM_THREADS) k_u_sum(const float* __restrict__ uf, const float* __restrict__ grad,
+                                                        const float* __restrict__ tk, const uint8_t* __restrict__ kk,
+                                                        const float4* __restrict__ aux, GridArgs g, PointParams P,
                                                         float* __restrict__ v, float* __restrict__ w_out,
                                                         float* __restrict__ g_out, int mode) {
     __shared__ SplineSmem sp;
@@ -313,33 +322,32 @@ __global__ void __launch_bounds__(USUM_THREADS) k_u_sum(const float* __restrict_
         const int z = (int)(r / N2), y = (int)(r - (long long)z * N2);
         const float* up = uf + 2LL * y * g.ncols + (long long)z * N1 + x;
         const int k = kk[i];
-        const float ni = n[i];
-        const float gx = grad[i], gy = grad[N + i], gz = grad[2 * N + i];
         float vl = 0.f, gg = 0.f;
         if (k != K_INVALID) {
             float u[NQ];
 #pragma unroll
             for (int a = 0; a < NQ; ++a) u[a] = up[a * fstride];
             const float t = tk[i];
-            float s0 = 0.f, s1 = 0.f;
+            const float4 ax = aux[i];
+            float uk = 0.f, uk1 = 0.f, m0 = 0.f, m1 = 0.f;
 #pragma unroll
             for (int a = 0; a < NQ; ++a) {
-                float pa, dpa;
-                cardinal(&sp, a, k, t, pa, dpa);
-                s0 = fmaf(u[a], pa, s0);
-                s1 = fmaf(u[a], dpa, s1);
+                m0 = fmaf(u[a], sp.Mq[a * MAX_NQ + k], m0);
+                m1 = fmaf(u[a], sp.Mq[a * MAX_NQ + k + 1], m1);
+                uk = (a == k) ? u[a] : uk;
+                uk1 = (a == k + 1) ? u[a] : uk1;
             }
-            const QPoint qp = q_point(ni, gx, gy, gz, P, sp.qm);
-            const float q = qp.q, q3 = q * q * q, q4 = q3 * q;
-            const float cn = 1.5f * P.C_s * ni * ni / q4;
-            vl = s0 + ni * qp.dq_dn * s1 + P.C_s * ni / q3 - cn * qp.dq_dn;
-            gg = ni * s1 * qp.dq_dg - cn * qp.dq_dg;
+            const float A = 1.f - t, B = t;
+            const float s0 = A * uk + B * uk1 + ((A * A * A - A) * m0 + (B * B * B - B) * m1) * sp.h26[k];
+            const float s1 = (uk1 - uk) * sp.ih[k] + ((3.f * B * B - 1.f) * m1 - (3.f * A * A - 1.f) * m0) * sp.h6[k];
+            vl = s0 + ax.x * s1 + ax.z;
+            gg = ax.y * s1 + ax.w;
         }
         if (v) v[i] = vl;
         if (mode == 0 && w_out) {
-            w_out[i] = gg * gx;
-            w_out[N + i] = gg * gy;
-            w_out[2 * N + i] = gg * gz;
+            w_out[i] = gg * grad[i];
+            w_out[N + i] = gg * grad[N + i];
+            w_out[2 * N + i] = gg * grad[2 * N + i];
         }
         if (mode == 1) g_out[i] = gg;
     }
@@ -699,7 +707,7 @@ static int launch_u_sum(vdw_ctx* c, const float* n, const float* grad, float* v,
     const float* uf = reinterpret_cast<const float*>(c->d_spec);
     const int nb = u_sum_blocks(g);
 #define VDW_U_SUM(NQ) \
-    k_u_sum<NQ><<<nb, USUM_THREADS, 0, s>>>(uf, n, grad, c->d_t, c->d_k, g, c->pp, v, w, c->d_gg, mode)
+    k_u_sum<NQ><<<nb, USUM_THREADS, 0, s>>>(uf, grad, c->d_t, c->d_k, c->d_aux, g, c->pp, v, w, c->d_gg, mode)
     switch (c->pp.Nq) {
         case 20: VDW_U_SUM(20); break;
         case 8: VDW_U_SUM(8); break;
@@ -731,7 +739,8 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
     VDW_CUDA(cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long), s));
     float* specf = reinterpret_cast<float*>(c->d_spec);
 #define VDW_POINTWISE(NQ)                                                                                  \
-    k_pointwise<NQ><<<c->nb_point, 256, 0, s>>>(n, grad, g, P, c->d_t, c->d_k, specf, c->d_epart, c->d_invalid)
+    k_pointwise<NQ><<<c->nb_point, 256, 0, s>>>(n, grad, g, P, c->d_t, c->d_k, c->d_aux, specf, c->d_epart, \
+                                                c->d_invalid)
     switch (P.Nq) {
         case 20: VDW_POINTWISE(20); break;
         case 8: VDW_POINTWISE(8); break;

@@ -29,21 +29,26 @@ __device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz,
     const float A = 0.031091f, a1 = 0.21370f;
     const float b1 = 7.5957f, b2 = 3.5876f, b3 = 1.6382f, b4 = 0.49294f;
     const float Z = -0.8491f;
-    const float kF = cbrtf(3.0f * PI_F * PI_F * n);
-    const float rs = cbrtf(3.0f / (4.0f * PI_F * n));
+    // one cube root: k_F = (3 pi^2 n)^(1/3), r_s = (3 / (4 pi n))^(1/3)
+    const float cb = cbrtf(n);
+    const float icb = 1.0f / cb;
+    const float kF = 3.0936677262801355f * cb;   // (3 pi^2)^(1/3) n^(1/3)
+    const float rs = 0.6203504908994001f * icb;  // (3 / (4 pi))^(1/3) n^(-1/3)
+    const float ikF = 0.323240919347991f * icb;  // 1 / k_F
     const float g2 = gx * gx + gy * gy + gz * gz;
     const float inv_n = 1.0f / n;
-    const float s2 = g2 * (0.25f * inv_n * inv_n) / (kF * kF);
-    const float srs = sqrtf(rs);
+    const float s2 = g2 * (0.25f * inv_n * inv_n) * (ikF * ikF);
+    const float rsq = rsqrtf(rs);
+    const float srs = rs * rsq;  // sqrt(r_s)
     const float Q = 2.f * A * (b1 * srs + b2 * rs + b3 * rs * srs + b4 * rs * rs);
-    const float dQ = 2.f * A * (0.5f * b1 / srs + b2 + 1.5f * b3 * srs + 2.f * b4 * rs);
+    const float dQ = 2.f * A * (0.5f * b1 * rsq + b2 + 1.5f * b3 * srs + 2.f * b4 * rs);
     const float Lg = log1pf(1.0f / Q);
     const float ec = -2.f * A * (1.f + a1 * rs) * Lg;
     const float dec = -2.f * A * a1 * Lg + 2.f * A * (1.f + a1 * rs) * dQ / (Q * Q + Q);
     const float q0 = kF * (1.f - Z / 9.f * s2) - 4.f * PI_F / 3.f * ec;
     const float dq0_dn = kF * inv_n * (1.f / 3.f) - Z / 9.f * (kF * s2 * inv_n * (1.f / 3.f) - kF * 8.f * s2 * inv_n * (1.f / 3.f))
                          + 4.f * PI_F / 3.f * dec * rs * inv_n * (1.f / 3.f);
-    const float dq0_dg = -Z / (18.f * kF) * inv_n * inv_n;
+    const float dq0_dg = -Z / 18.f * ikF * inv_n * inv_n;
     // saturation: h = q_c (1 - exp(-S)), S = sum_{m=1}^{m_c} y^m/m, y = q0/q_c.
     // For y > 4 exp(-S) is far below the FP32 (and FP64) range: h = q_c, h' = 0.
     const float y = q0 / P.q_c;
@@ -55,11 +60,12 @@ __device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz,
         for (int m = 1; m <= P.m_c; ++m) {
             dS += yp;
             yp *= y;
-            S += yp / (float)m;
+            S = fmaf(yp, __frcp_rn((float)m), S);
         }
         // 1 - exp(-S) through expm1: no cancellation for small q0
-        h = -P.q_c * expm1f(-S);
-        hp = expf(-S) * dS;
+        const float em1 = expm1f(-S);
+        h = -P.q_c * em1;
+        hp = (1.f + em1) * dS;
     }
     // below the mesh q is clamped to q_1 and no longer varies with n, grad n
     if (h < qm[0]) hp = 0.f;
