@@ -414,35 +414,86 @@ constexpr int ct_max_m(int n, int maxr = 16, int s = 0) {
                                     : (n / ct_radix_at(n, s, maxr) > ct_max_m(n, maxr, s + 1) ? n / ct_radix_at(n, s, maxr)
                                                                                                 : ct_max_m(n, maxr, s + 1));
 }
+// (two lines of at most 16 butterflies go one per half-warp, see ct_pass)
 constexpr int ct_lines_per_warp(int n, int maxr = 16) {
-    const int l = 32 / ct_max_m(n, maxr);
+    const int m = ct_max_m(n, maxr);
+    if (m <= 16) return 2;
+    const int l = 32 / m;
     return l < 1 ? 1 : (l > 4 ? 4 : l);
 }
 
+// Twiddle table of a compile-time length N, laid out by pass: pass s with
+// Ns > 1 keeps W_N^(r k TS) (r = 1 .. R-1, k = 0 .. Ns-1, TS = N/(Ns R)) at
+// ct_tw_off(N, s) + (r - 1) Ns + k, so that the lanes of a pass, which take
+// consecutive k, read consecutive entries (no bank conflicts).  At most N
+// entries in all.
+constexpr int ct_tw_off(int n, int s, int maxr = 16) {
+    return s == 0 ? 0
+                  : ct_tw_off(n, s - 1, maxr) +
+                        (ct_ns_at(n, s - 1, maxr) > 1 ? (ct_radix_at(n, s - 1, maxr) - 1) * ct_ns_at(n, s - 1, maxr) : 0);
+}
+// Fills the table from the plain one (src[e] = W_N^e), all threads of the block.
+template <int N, int MAXR = 16, int S = 0>
+__device__ __forceinline__ void ct_load_twiddles(float2* dst, const float2* src) {
+    if constexpr (S < ct_npasses(N, MAXR)) {
+        constexpr int R = ct_radix_at(N, S, MAXR), Ns = ct_ns_at(N, S, MAXR);
+        if constexpr (Ns > 1) {
+            constexpr int TS = N / (Ns * R), off = ct_tw_off(N, S, MAXR);
+            for (int i = threadIdx.x; i < (R - 1) * Ns; i += blockDim.x) {
+                const int r = 1 + i / Ns, k = i - (r - 1) * Ns;
+                dst[off + i] = src[r * k * TS];
+            }
+        }
+        ct_load_twiddles<N, MAXR, S + 1>(dst, src);
+    }
+}
+
 // One pass over L lines (line l at p + l*ls, element stride es) by one warp.
+// Two lines of at most 16 butterflies go one per half-warp: a 64-bit shared
+// access is served per half-warp, so the two lines never compete for banks
+// whatever their distance, and consecutive butterflies of one line hit
+// distinct banks.  The first pass (Ns = 1) has no twiddles; the others read
+// the pass-ordered table of ct_load_twiddles.
 template <int N, int S, int L, bool INV, int MAXR>
 __device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const float2* tw, int lane) {
     constexpr int R = ct_radix_at(N, S, MAXR);
     constexpr int Ns = ct_ns_at(N, S, MAXR);
     constexpr int M = N / R;
-    constexpr int TS = N / (Ns * R);
     constexpr int TOT = L * M;
-    constexpr int B = (TOT + 31) / 32;
+    constexpr bool HALF = (L == 2) && (M <= 16);
+    constexpr int B = HALF ? 1 : (TOT + 31) / 32;
     float2 v[B][R];
+    int lj[B][2];
+    bool act[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        const int t0 = lane + 32 * b;
-        const int t = (TOT % 32 == 0 || t0 < TOT) ? t0 : 0;  // in-range index for tail lanes
-        if (TOT % 32 == 0 || t0 < TOT) {
-            const int l = t / M, j = t - l * M;
+        if constexpr (HALF) {
+            lj[b][0] = lane >> 4;
+            lj[b][1] = lane & 15;
+            act[b] = (M == 16) || lj[b][1] < M;
+        } else {
+            const int t0 = lane + 32 * b;
+            act[b] = (TOT % 32 == 0) || t0 < TOT;
+            const int t = act[b] ? t0 : 0;  // in-range index for tail lanes
+            lj[b][0] = t / M;
+            lj[b][1] = t - lj[b][0] * M;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if (act[b]) {
+            const int l = lj[b][0], j = lj[b][1];
             const int k = j % Ns;
             const float2* q = p + l * ls;
 #pragma unroll
             for (int r = 0; r < R; ++r) v[b][r] = q[(j + r * M) * es];
+            if constexpr (Ns > 1) {
+                constexpr int off = ct_tw_off(N, S, MAXR);
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const float2 w = tw[r * k * TS];
-                v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+                for (int r = 1; r < R; ++r) {
+                    const float2 w = tw[off + (r - 1) * Ns + k];
+                    v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+                }
             }
             dft<R, INV>(v[b]);
         }
@@ -450,10 +501,8 @@ __device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const float2*
     __syncwarp();
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        const int t0 = lane + 32 * b;
-        const int t = (TOT % 32 == 0 || t0 < TOT) ? t0 : 0;  // in-range index for tail lanes
-        if (TOT % 32 == 0 || t0 < TOT) {
-            const int l = t / M, j = t - l * M;
+        if (act[b]) {
+            const int l = lj[b][0], j = lj[b][1];
             const int k = j % Ns;
             float2* q = p + l * ls;
             const int base = (j - k) * R + k;

@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ s
     float2* lines = sm;  // [NQ][C][N2]
     float2* tw2 = lines + NQ * C * N2;
     float* bins = reinterpret_cast<float*>(tw2 + N2);  // [P][J] (GRADK)
-    load_twiddles(tw2, tw + g.N1, N2);
+    load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     if (GRADK)
         for (int i = threadIdx.x; i < LRN_P * la.J; i += blockDim.x) bins[i] = 0.f;
     const int c0 = blockIdx.x * C;
@@ -902,8 +902,8 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_field_plane(const float* _
     float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
     const int y = blockIdx.x;
-    load_twiddles(tw1, tw, g.N1);
-    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    load_line_twiddles<CN1>(tw1, tw, g.N1);
+    load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
     float* pf = reinterpret_cast<float*>(plane);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int z = warp; z < g.N3; z += nw) {
@@ -924,7 +924,7 @@ __global__ void __launch_bounds__(256, 2) k_pencil_grad(const float2* __restrict
     const int N2 = CN2 > 0 ? CN2 : g.N2;
     float2* lines = sm;  // [4][C][N2]: the field, then its three derivatives
     float2* tw2 = lines + 4 * C * N2;
-    load_twiddles(tw2, tw + g.N1, N2);
+    load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
     for (int i = threadIdx.x; i < N2 * C; i += blockDim.x) {
         const int cc = i % C, yy = i / C;
@@ -966,8 +966,8 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_inv3(const float2* _
     float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
     const int y = blockIdx.x, c = blockIdx.y;
-    load_twiddles(tw1, tw, g.N1);
-    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    load_line_twiddles<CN1>(tw1, tw, g.N1);
+    load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
     const float2* src = wspec + ((long long)c * g.N2 + y) * g.ncols;
     for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     __syncthreads();

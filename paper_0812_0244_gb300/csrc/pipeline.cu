@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(CONTRACT_THREADS, 2) k_pencil_contract(float2*
     const int N2 = CN2 > 0 ? CN2 : g.N2;
     float2* lines = sm;  // [NQ][C][N2]
     float2* tw2 = lines + NQ * C * N2;
-    load_twiddles(tw2, tw + g.N1, N2);
+    load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
     const int tot = NQ * N2 * C;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
@@ -267,8 +267,8 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_planes_inplace(float2* __r
     } else {
         for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     }
-    load_twiddles(tw1, tw, g.N1);
-    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    load_line_twiddles<CN1>(tw1, tw, g.N1);
+    load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
     __syncthreads();
     if (bulk && !mbar_wait_parity(&bar, 0u)) {
         // gave up: record it, wait once more (bounded) for the copy in flight
@@ -366,8 +366,8 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_w_planes(const float* __re
     float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
     const int y = blockIdx.x, c = blockIdx.y;
-    load_twiddles(tw1, tw, g.N1);
-    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    load_line_twiddles<CN1>(tw1, tw, g.N1);
+    load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
     float* pf = reinterpret_cast<float*>(plane);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const float* gc = grad + c * g.N;
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
     const int N2 = CN2 > 0 ? CN2 : g.N2;
     float2* lines = sm;  // [3][C][N2]
     float2* tw2 = lines + 3 * C * N2;
-    load_twiddles(tw2, tw + g.N1, N2);
+    load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
     const int tot = 3 * N2 * C;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_div_final(const float2* __
     float2* tw1 = plane + g.N3 * g.Nh;
     float2* tw3 = tw1 + g.N1;
     const int y = blockIdx.x;
-    load_twiddles(tw1, tw, g.N1);
-    load_twiddles(tw3, tw + g.N1 + g.N2, g.N3);
+    load_line_twiddles<CN1>(tw1, tw, g.N1);
+    load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
     const float2* src = wspec + (long long)y * g.ncols;
     for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     __syncthreads();

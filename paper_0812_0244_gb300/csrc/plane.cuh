@@ -32,6 +32,13 @@ __device__ inline double block_sum(double v, double* red) {
 __device__ __forceinline__ void load_twiddles(float2* dst, const float2* src, int n) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
+// Shared-memory twiddles of a line length: the pass-ordered table of the
+// compile-time transforms when CN > 0 (CN == n), the plain table otherwise.
+template <int CN>
+__device__ __forceinline__ void load_line_twiddles(float2* dst, const float2* src, int n) {
+    if constexpr (CN > 0) ct_load_twiddles<CN>(dst, src);
+    else load_twiddles(dst, src, n);
+}
 
 // ---------------------------------------------------------------------------
 // line-transform dispatch: compile-time length when CN > 0
