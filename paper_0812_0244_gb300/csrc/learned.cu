@@ -514,9 +514,10 @@ __global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ s
     if (GRADK)
         for (int i = threadIdx.x; i < LRN_P * la.J; i += blockDim.x) bins[i] = 0.f;
     const int c0 = blockIdx.x * C;
+    const SmallDiv sC = small_div(C);  // i / C in the staging loops
     const int tot = NQ * N2 * C;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int cc = i % C, rr = i / C, yy = rr % N2, a = rr / N2;
+        const int rr = sdiv(i, sC), cc = i - rr * C, yy = rr % N2, a = rr / N2;
         const int col = c0 + cc;
         float2 val = make_float2(0.f, 0.f);
         if (col < g.ncols) val = spec[((long long)a * N2 + yy) * g.ncols + col];
@@ -622,7 +623,7 @@ __global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ s
     pencils_fft<CN2, true>(lines, NQ * C, N2, g.p2, tw2);
     __syncthreads();
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int cc = i % C, rr = i / C, yy = rr % N2, a = rr / N2;
+        const int rr = sdiv(i, sC), cc = i - rr * C, yy = rr % N2, a = rr / N2;
         const int col = c0 + cc;
         if (col < g.ncols) spec[((long long)a * N2 + yy) * g.ncols + col] = lines[(a * C + cc) * N2 + yy];
     }
@@ -926,8 +927,9 @@ __global__ void __launch_bounds__(256, 2) k_pencil_grad(const float2* __restrict
     float2* tw2 = lines + 4 * C * N2;
     load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
+    const SmallDiv sC = small_div(C);  // i / C in the staging loops
     for (int i = threadIdx.x; i < N2 * C; i += blockDim.x) {
-        const int cc = i % C, yy = i / C;
+        const int yy = sdiv(i, sC), cc = i - yy * C;
         const int col = c0 + cc;
         lines[cc * N2 + yy] = col < g.ncols ? spec[(long long)yy * g.ncols + col] : make_float2(0.f, 0.f);
     }
@@ -951,7 +953,7 @@ __global__ void __launch_bounds__(256, 2) k_pencil_grad(const float2* __restrict
     pencils_fft<CN2, true>(lines + C * N2, 3 * C, N2, g.p2, tw2);
     __syncthreads();
     for (int i = threadIdx.x; i < 3 * N2 * C; i += blockDim.x) {
-        const int cc = i % C, rr = i / C, yy = rr % N2, c = rr / N2;
+        const int rr = sdiv(i, sC), cc = i - rr * C, yy = rr % N2, c = rr / N2;
         const int col = c0 + cc;
         if (col < g.ncols) wspec[((long long)c * N2 + yy) * g.ncols + col] = lines[((1 + c) * C + cc) * N2 + yy];
     }

@@ -114,9 +114,10 @@ __global__ void __launch_bounds__(CONTRACT_THREADS, 2) k_pencil_contract(float2*
     float2* tw2 = lines + NQ * C * N2;
     load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
+    const SmallDiv sC = small_div(C);  // i / C in the staging loops
     const int tot = NQ * N2 * C;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int cc = i % C, r = i / C, yy = r % N2, a = r / N2;
+        const int r = sdiv(i, sC), cc = i - r * C, yy = r % N2, a = r / N2;
         const int col = c0 + cc;
         float2 val = make_float2(0.f, 0.f);
         if (col < g.ncols) val = spec[((long long)a * N2 + yy) * g.ncols + col];
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(CONTRACT_THREADS, 2) k_pencil_contract(float2*
     pencils_fft<CN2, true>(lines, NQ * C, N2, g.p2, tw2);
     __syncthreads();
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int cc = i % C, r = i / C, yy = r % N2, a = r / N2;
+        const int r = sdiv(i, sC), cc = i - r * C, yy = r % N2, a = r / N2;
         const int col = c0 + cc;
         if (col < g.ncols) spec[((long long)a * N2 + yy) * g.ncols + col] = lines[(a * C + cc) * N2 + yy];
     }
@@ -396,9 +397,10 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
     float2* tw2 = lines + 3 * C * N2;
     load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
+    const SmallDiv sC = small_div(C);  // i / C in the staging loops
     const int tot = 3 * N2 * C;
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int cc = i % C, r = i / C, yy = r % N2, c = r / N2;
+        const int r = sdiv(i, sC), cc = i - r * C, yy = r % N2, c = r / N2;
         const int col = c0 + cc;
         float2 val = make_float2(0.f, 0.f);
         if (col < g.ncols) val = wspec[((long long)c * N2 + yy) * g.ncols + col];
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
     pencils_fft<CN2, true>(lines, C, N2, g.p2, tw2);
     __syncthreads();
     for (int i = threadIdx.x; i < N2 * C; i += blockDim.x) {
-        const int cc = i % C, yy = i / C;
+        const int yy = sdiv(i, sC), cc = i - yy * C;
         const int col = c0 + cc;
         if (col < g.ncols) wspec[(long long)yy * g.ncols + col] = lines[cc * N2 + yy];
     }

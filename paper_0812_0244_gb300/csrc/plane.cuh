@@ -40,6 +40,21 @@ __device__ __forceinline__ void load_line_twiddles(float2* dst, const float2* sr
     else load_twiddles(dst, src, n);
 }
 
+// i / d for a small divisor (1 <= d < 256) and 0 <= i < 2^24 by one
+// multiply-high with m = ceil(2^32 / d): the error term i (m d - 2^32) / 2^32 /
+// d stays below 1/d, so the quotient is exact in that range.
+struct SmallDiv {
+    unsigned m;
+    int d;
+};
+__device__ __forceinline__ SmallDiv small_div(int d) {
+    SmallDiv s;
+    s.d = d;
+    s.m = d == 1 ? 0u : 0xFFFFFFFFu / (unsigned)d + 1u;
+    return s;
+}
+__device__ __forceinline__ int sdiv(int i, SmallDiv s) { return s.d == 1 ? i : (int)__umulhi((unsigned)i, s.m); }
+
 // ---------------------------------------------------------------------------
 // line-transform dispatch: compile-time length when CN > 0
 // ---------------------------------------------------------------------------
