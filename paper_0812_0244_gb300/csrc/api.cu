@@ -1,6 +1,8 @@
 // C ABI of the vdwnl library (declared in include/vdwnl.h).
 #include "common.cuh"
 
+#include <algorithm>
+
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -148,6 +150,13 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     g.N3 = n3;
     g.Nh = n1 / 2 + 1;
     g.N = (long long)n1 * n2 * n3;
+    {
+        const unsigned long long dmax = (unsigned long long)std::max(n1, std::max(n2, n3));
+        g.fast = (n1 > 1 && n2 > 1 && n3 / 2 > 1 && (unsigned long long)g.N * dmax < (1ull << 32)) ? 1 : 0;
+        g.m1 = g.fast ? 0xFFFFFFFFu / (unsigned)n1 + 1u : 0u;
+        g.m2 = g.fast ? 0xFFFFFFFFu / (unsigned)n2 + 1u : 0u;
+        g.mh3 = g.fast ? 0xFFFFFFFFu / (unsigned)(n3 / 2) + 1u : 0u;
+    }
     g.ncols = n3 * g.Nh;
     for (int d = 0; d < 3; ++d) c->L[d] = L[d];
     g.gx = (float)(2.0 * PI_D / L[0]);

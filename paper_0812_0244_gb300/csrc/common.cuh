@@ -43,6 +43,11 @@ struct GridArgs {
     int Nk;                // points of the radial table
     float invN;            // 1 / N
     LinePlan p1, p2, p3;   // line transforms along x, y, z
+    // Flat-index divisions by N1, N2 and N3/2 as multiply-high by
+    // m = ceil(2^32 / d), exact for i d < 2^32; fast = 0 (plain division)
+    // when N max(N1, N2, N3) reaches 2^32 or a divisor is 1.
+    unsigned m1, m2, mh3;
+    int fast;
 };
 
 // Learned reduced basis: sizes fixed at compile time.

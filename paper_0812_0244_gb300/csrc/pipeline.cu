@@ -316,11 +316,10 @@ __global__ void __launch_bounds__(USUM_THREADS) k_u_sum(const float* __restrict_
     __syncthreads();
     const long long N = g.N;
     const long long fstride = 2LL * g.N2 * g.ncols;  // floats between the planes of two fields
-    const int N1 = g.N1, N2 = g.N2;
+    const int N1 = g.N1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const long long r = i / N1;
-        const int x = (int)(i - r * N1);
-        const int z = (int)(r / N2), y = (int)(r - (long long)z * N2);
+        int x, y, z;
+        flat_point(i, g, x, y, z);
         const float* up = uf + 2LL * y * g.ncols + (long long)z * N1 + x;
         const int k = kk[i];
         float vl = 0.f, gg = 0.f;
@@ -471,9 +470,8 @@ __global__ void __launch_bounds__(256) k_stencil_gradient(const float* __restric
                                                           float* __restrict__ grad) {
     const long long N = g.N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.N1);
-        const long long r = i / g.N1;
-        const int y = (int)(r % g.N2), z = (int)(r / g.N2);
+        int x, y, z;
+        flat_point(i, g, x, y, z);
         const long long rowz = (long long)z * g.N2;
         const long long xm = i - x + (x == 0 ? g.N1 - 1 : x - 1), xp = i - x + (x == g.N1 - 1 ? 0 : x + 1);
         const long long ym = ((rowz + (y == 0 ? g.N2 - 1 : y - 1)) * g.N1) + x;
@@ -492,9 +490,8 @@ __global__ void __launch_bounds__(256) k_stencil_div_sub(const float* __restrict
                                                          GridArgs g, float3 ih2, float* __restrict__ v) {
     const long long N = g.N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % g.N1);
-        const long long r = i / g.N1;
-        const int y = (int)(r % g.N2), z = (int)(r / g.N2);
+        int x, y, z;
+        flat_point(i, g, x, y, z);
         const long long rowz = (long long)z * g.N2;
         const long long xm = i - x + (x == 0 ? g.N1 - 1 : x - 1), xp = i - x + (x == g.N1 - 1 ? 0 : x + 1);
         const long long ym = ((rowz + (y == 0 ? g.N2 - 1 : y - 1)) * g.N1) + x;

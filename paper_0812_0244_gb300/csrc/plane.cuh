@@ -96,14 +96,36 @@ __device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, c
 // (z N2 + y) N1 + x.
 __device__ __forceinline__ long long packed_point(long long q, const GridArgs& g, int& y, int& z, int& x, int& j) {
     const int s = (int)(q & 1);
-    const long long t = q >> 1;
-    const long long rr = t / g.N1;
-    x = (int)(t - rr * g.N1);
     const int nh3 = g.N3 >> 1;
-    y = (int)(rr / nh3);
-    j = (int)(rr - (long long)y * nh3);
+    if (g.fast) {
+        const unsigned t = (unsigned)(q >> 1);
+        const unsigned rr = __umulhi(t, g.m1);
+        x = (int)(t - rr * (unsigned)g.N1);
+        y = (int)__umulhi(rr, g.mh3);
+        j = (int)(rr - (unsigned)y * (unsigned)nh3);
+    } else {
+        const long long t = q >> 1;
+        const long long rr = t / g.N1;
+        x = (int)(t - rr * g.N1);
+        y = (int)(rr / nh3);
+        j = (int)(rr - (long long)y * nh3);
+    }
     z = 2 * j + s;
     return ((long long)z * g.N2 + y) * g.N1 + x;
+}
+// (x, y, z) of flat index i = (z N2 + y) N1 + x
+__device__ __forceinline__ void flat_point(long long i, const GridArgs& g, int& x, int& y, int& z) {
+    if (g.fast) {
+        const unsigned r = __umulhi((unsigned)i, g.m1);
+        x = (int)((unsigned)i - r * (unsigned)g.N1);
+        z = (int)__umulhi(r, g.m2);
+        y = (int)(r - (unsigned)z * (unsigned)g.N2);
+    } else {
+        const long long r = i / g.N1;
+        x = (int)(i - r * g.N1);
+        z = (int)(r / g.N2);
+        y = (int)(r - (long long)z * g.N2);
+    }
 }
 // float offset, within its plane, of real point (x, z = 2j + s) in the packed rows
 __device__ __forceinline__ int packed_offset(int x, int j, int s, int Nh) { return 4 * j * Nh + 2 * x + s; }
