@@ -40,7 +40,9 @@ namespace {
 namespace cg = cooperative_groups;
 
 constexpr int L_SLOTS = 8;        // network partial-sum slots per y plane (epart scratch)
-constexpr int L_THREADS = 256;    // two warpgroups
+constexpr int L_THREADS = 256;    // two warpgroups (channel kernel)
+constexpr int L_NET_WG = 3;       // warpgroups of the network kernel
+constexpr int L_NET_THREADS = 128 * L_NET_WG;
 constexpr int L_TILE = 128;       // points per warpgroup tile
 constexpr int L_MAXJ = 256;       // knots held in shared memory by the knot-gradient bins
 
@@ -146,11 +148,13 @@ struct __align__(128) MlpWG {
 struct __align__(128) MlpWG3 {
     uint16_t A[3][L_TILE * LRN_H];
 };
+constexpr int L_MAXWG = 4;  // warpgroups per block at most
 struct MlpCtl {
-    uint64_t bar[2];
+    uint64_t bar[L_MAXWG];
     uint32_t tmem;
     uint32_t wgcols;  // tensor-memory columns per warpgroup
-    int abort[2];     // per warpgroup: a wait gave up
+    uint32_t cols;    // columns allocated (a power of two >= warpgroups x wgcols)
+    int abort[L_MAXWG];  // per warpgroup: a wait gave up
 };
 
 __device__ void mlp_load_weights(MlpShared* S, const LearnedArgs& la) {
@@ -168,16 +172,21 @@ __device__ void mlp_load_weights(MlpShared* S, const LearnedArgs& la) {
     for (int i = threadIdx.x; i < LRN_M; i += blockDim.x) S->b3[i] = la.b3[i];
 }
 
-// Block setup: barriers, tensor memory (2 wgcols columns: wgcols per
-// warpgroup; a power of two of at least 32).
+// Block setup: barriers, tensor memory (wgcols columns per warpgroup, a
+// power of two of at least 32; the allocation is rounded up to a power of two).
 __device__ void mlp_setup(MlpCtl* ctl, uint32_t wgcols) {
+    const int nwg = blockDim.x >> 7;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)nwg * wgcols) cols <<= 1;
     if (threadIdx.x == 0) {
-        tc::mbar_init(&ctl->bar[0], 1);
-        tc::mbar_init(&ctl->bar[1], 1);
-        ctl->abort[0] = ctl->abort[1] = 0;
+        for (int i = 0; i < nwg; ++i) {
+            tc::mbar_init(&ctl->bar[i], 1);
+            ctl->abort[i] = 0;
+        }
         ctl->wgcols = wgcols;
+        ctl->cols = cols;
     }
-    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&ctl->tmem, 2 * wgcols);
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&ctl->tmem, cols);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -187,7 +196,7 @@ __device__ void mlp_setup(MlpCtl* ctl, uint32_t wgcols) {
 __device__ void mlp_teardown(MlpCtl* ctl) {
     tc::fence_before_sync();
     __syncthreads();
-    if ((threadIdx.x >> 5) == 0) tc::tmem_free(ctl->tmem, 2 * ctl->wgcols);
+    if ((threadIdx.x >> 5) == 0) tc::tmem_free(ctl->tmem, ctl->cols);
 }
 
 // Issue, for each of nA operands A[i] (K-wide), the K/16 MMAs of A[i] x B^T
@@ -274,13 +283,15 @@ __device__ bool mlp_forward(MlpShared* S, MlpWG* W, MlpCtl* ctl, int wg, int r, 
 
 // Forward network with its Jacobian by forward mode (two tangents, one per
 // feature), on the warpgroup's tile: layer 1 and its tangents on the CUDA
-// cores, then layers 2 and 3 on the tensor cores for the activation and both
-// tangents at once (one wait per layer).  Tangents enter the products as bf16
-// like the activations.  Tensor memory (256 columns per warpgroup): layer 2
-// in [0, 64), [64, 128), [128, 192); layer 3 in [0, 16), [16, 32), [32, 48).
+// cores, then layers 2 and 3 on the tensor cores.  Tangents enter the
+// products as bf16 like the activations.  Tensor memory: 128 columns per
+// warpgroup.  Layer 2 runs in two batches: the activation into [0, 64) and
+// the first tangent into [64, 128); after their epilogue the second tangent
+// reuses [64, 128) while the layer-2 pre-activation stays in [0, 64) for its
+// SiLU derivative.  Layer 3 then writes [0, 16), [16, 32), [32, 48).
 // Returns o (8 outputs) and J1, J2 (d o / d x1, d o / d x2).
-// overlap() runs on every thread of the warpgroup while the layer-2 MMAs are
-// in flight (work that does not depend on the network).
+// overlap() runs on every thread of the warpgroup while the first layer-2
+// batch is in flight (work that does not depend on the network).
 template <class Overlap>
 __device__ bool mlp_forward_jac(MlpShared* S, MlpWG3* W, MlpCtl* ctl, int wg, int r, uint32_t& phase, float x1,
                                 float x2, float* o, float* J1, float* J2, int* err, Overlap overlap) {
@@ -301,29 +312,42 @@ __device__ bool mlp_forward_jac(MlpShared* S, MlpWG3* W, MlpCtl* ctl, int wg, in
         store8_bf16(W->A[2] + tc::kmaj(r, 8 * c, LRN_H), t2);
     }
     {
-        const uint16_t* As[3] = {W->A[0], W->A[1], W->A[2]};
-        const uint32_t cols[3] = {0, 64, 128};
-        wg_mma_issue(ctl, wg, r, As, cols, 3, S->w2f, LRN_H, LRN_H);
+        const uint16_t* As[2] = {W->A[0], W->A[1]};
+        const uint32_t cols[2] = {0, 64};
+        wg_mma_issue(ctl, wg, r, As, cols, 2, S->w2f, LRN_H, LRN_H);
         overlap();
         if (!wg_mma_wait(ctl, wg, phase, err)) return false;
     }
 #pragma unroll
     for (int c = 0; c < LRN_H / 16; ++c) {
-        float z[16], d1[16], d2[16];
+        float z[16], d1[16];
         tc::tmem_ld16(lane_addr(ctl, wg, 16 * c), z);
         tc::tmem_ld16(lane_addr(ctl, wg, 64 + 16 * c), d1);
-        tc::tmem_ld16(lane_addr(ctl, wg, 128 + 16 * c), d2);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             float sp;
             silu_both(z[q] + S->b2[16 * c + q], z[q], sp);
             d1[q] *= sp;
-            d2[q] *= sp;
         }
         store8_bf16(W->A[0] + tc::kmaj(r, 16 * c, LRN_H), z);
         store8_bf16(W->A[0] + tc::kmaj(r, 16 * c + 8, LRN_H), z + 8);
         store8_bf16(W->A[1] + tc::kmaj(r, 16 * c, LRN_H), d1);
         store8_bf16(W->A[1] + tc::kmaj(r, 16 * c + 8, LRN_H), d1 + 8);
+    }
+    {
+        // the first tangent's columns are read (tcgen05.wait::ld in tmem_ld16)
+        const uint16_t* As[1] = {W->A[2]};
+        const uint32_t cols[1] = {64};
+        wg_mma_issue(ctl, wg, r, As, cols, 1, S->w2f, LRN_H, LRN_H);
+        if (!wg_mma_wait(ctl, wg, phase, err)) return false;
+    }
+#pragma unroll
+    for (int c = 0; c < LRN_H / 16; ++c) {
+        float z[16], d2[16];
+        tc::tmem_ld16(lane_addr(ctl, wg, 16 * c), z);
+        tc::tmem_ld16(lane_addr(ctl, wg, 64 + 16 * c), d2);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) d2[q] *= silu_prime(z[q] + S->b2[16 * c + q]);
         store8_bf16(W->A[2] + tc::kmaj(r, 16 * c, LRN_H), d2);
         store8_bf16(W->A[2] + tc::kmaj(r, 16 * c + 8, LRN_H), d2 + 8);
     }
@@ -395,11 +419,11 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
 // ---------------------------------------------------------------------------
 // L1: network and channels
 // ---------------------------------------------------------------------------
-// One persistent block per SM, two warpgroups, each running the network and
+// One persistent block per SM, three warpgroups, each running the network and
 // its two tangents on tiles of 128 points (packed order): layer 1 on CUDA
-// cores gives three bf16 operands in the tcgen05 core-matrix layout; layers 2
-// and 3 are 3 x 4 MMAs each into tensor memory, one commit and one wait per
-// layer.  theta_m = n w_m goes to the packed real rows of plane (m, y) of the
+// cores gives three bf16 operands in the tcgen05 core-matrix layout; layer 2
+// is 2 x 4 and then 1 x 4 MMAs into the warpgroup's 128 tensor-memory
+// columns, layer 3 is 3 x 4 MMAs (mlp_forward_jac).  theta_m = n w_m goes to the packed real rows of plane (m, y) of the
 // spectrum buffer (the forward plane transforms follow in place).  With lw
 // the per-point coefficients of the assembly of Eq. (Vi) are stored,
 // lw[c][q] in packed order (LW_ROWS rows): v_loc = sum_m u_m lw[m] + lw[2M]
@@ -408,7 +432,7 @@ __global__ void k_learned_prepare(const float* __restrict__ flat, LearnedArgs la
 //   lw[M + m] = n (dw_m/d|grad n|)/|grad n|
 //   lw[2M], lw[2M + 1] = the Delta E derivatives.
 // Delta E partial sums per block.
-__global__ void __launch_bounds__(L_THREADS, 1)
+__global__ void __launch_bounds__(L_NET_THREADS, 1)
     k_learned_net(const float* __restrict__ n, const float* __restrict__ grad, GridArgs g, PointParams P,
                   LearnedArgs la, float* __restrict__ specf, double* __restrict__ epart,
                   unsigned long long* __restrict__ invalid, float* __restrict__ lw) {
@@ -422,14 +446,14 @@ __global__ void __launch_bounds__(L_THREADS, 1)
     MlpWG3* W = Wb + wg;
     mlp_load_weights(S, la);
     for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
-    mlp_setup(&ctl, 256);
+    mlp_setup(&ctl, 128);
     const long long N = g.N;
     const long long ntiles = (N + L_TILE - 1) / L_TILE;
     const long long fstride = 2LL * g.N2 * g.ncols;  // floats between the planes of two channels
     uint32_t phase = 0;
     double eacc = 0.0;
     unsigned int bad = 0;
-    for (long long T = 2 * (long long)blockIdx.x + wg; T < ntiles; T += 2 * (long long)gridDim.x) {
+    for (long long T = L_NET_WG * (long long)blockIdx.x + wg; T < ntiles; T += L_NET_WG * (long long)gridDim.x) {
         const long long q = T * L_TILE + r;
         const bool in = q < N;
         int y = 0, z = 0, x = 0, j = 0;
@@ -669,9 +693,8 @@ __global__ void __launch_bounds__(256) k_u_fields(const float* __restrict__ uf, 
     const long long N = g.N;
     const long long fstride = 2LL * g.N2 * g.ncols;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        const long long r = i / g.N1;
-        const int x = (int)(i - r * g.N1);
-        const int z = (int)(r / g.N2), y = (int)(r - (long long)z * g.N2);
+        int x, y, z;
+        flat_point(i, g, x, y, z);
         const float* up = uf + 2LL * y * g.ncols + (long long)z * g.N1 + x;
 #pragma unroll
         for (int m = 0; m < LRN_M; ++m) U[m * N + i] = up[m * fstride];
@@ -1002,10 +1025,10 @@ __global__ void k_adam(float* __restrict__ p, const double* __restrict__ g, floa
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// the network kernel: its shared block and the two warpgroups' operands.  It
-// allocates all 512 tensor-memory columns of its SM, so the request is at
+// the network kernel: its shared block and the three warpgroups' operands.
+// It allocates all 512 tensor-memory columns of its SM, so the request is at
 // least 116 KB: a second block never fits beside it.
-size_t smem_net() { return std::max(sizeof(MlpShared) + 2 * sizeof(MlpWG3), (size_t)116 * 1024); }
+size_t smem_net() { return std::max(sizeof(MlpShared) + L_NET_WG * sizeof(MlpWG3), (size_t)116 * 1024); }
 // network blocks: one per SM, at most the partial-sum slots of the epart scratch
 int net_blocks(vdw_ctx* c) {
     int dev = 0, nsm = 0;
@@ -1094,7 +1117,7 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     }
     VDW_CUDA(cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long), s));
     const bool want_pot = (v != nullptr) || (w != nullptr);
-    k_learned_net<<<nb0, L_THREADS, smem_net(), s>>>(n, grad, g, P, la, specf, ep, c->d_invalid,
+    k_learned_net<<<nb0, L_NET_THREADS, smem_net(), s>>>(n, grad, g, P, la, specf, ep, c->d_invalid,
                                                      (want_pot && kind != RUN_GRAD) ? c->d_lw : nullptr);
     int rc = pipeline_planes_inplace(c, LRN_M, false, s);
     if (rc) return rc;
