@@ -194,7 +194,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     K = max(1, min(args.steps, 4))
-    W = min(args.warmup, 1)
+    W = min(args.warmup, 3)
     total_pts, total_s = 0, 0.0
     for i in range(W + K):
         rate, sec, pts = oracle_sample_rate()

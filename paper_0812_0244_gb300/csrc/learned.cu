@@ -928,12 +928,12 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_field_plane(const float* _
     const int y = blockIdx.x;
     load_line_twiddles<CN1>(tw1, tw, g.N1);
     load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
-    float* pf = reinterpret_cast<float*>(plane);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int z = warp; z < g.N3; z += nw) {
-        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-        float* dst = pf + packed_row(z, g.Nh);
-        for (int x = lane; x < g.N1; x += 32) dst[2 * x] = f[row + x];
+    const long long zs = (long long)g.N1 * g.N2;  // flat distance between rows z and z + 1
+    for (int jr = warp; jr < (g.N3 >> 1); jr += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * 2 * jr);
+        float2* crow = plane + jr * 2 * g.Nh;
+        for (int x = lane; x < g.N1; x += 32) crow[x] = make_float2(f[row + x], f[row + zs + x]);
     }
     __syncthreads();
     plane_forward<CN1, CN3>(plane, g, tw1, tw3);
@@ -997,12 +997,17 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_inv3(const float2* _
     for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     __syncthreads();
     plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
-    const float* pf = reinterpret_cast<const float*>(plane);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int z = warp; z < g.N3; z += nw) {
-        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-        const float* srow = pf + packed_row(z, g.Nh);
-        for (int x = lane; x < g.N1; x += 32) out[c * g.N + row + x] = srow[2 * x];
+    const long long zs = (long long)g.N1 * g.N2;
+    float* oc = out + c * g.N;
+    for (int jr = warp; jr < (g.N3 >> 1); jr += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * 2 * jr);
+        const float2* crow = plane + jr * 2 * g.Nh;
+        for (int x = lane; x < g.N1; x += 32) {
+            const float2 d = crow[x];
+            oc[row + x] = d.x;
+            oc[row + zs + x] = d.y;
+        }
     }
 }
 

@@ -278,12 +278,17 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_planes_inplace(float2* __r
     }
     if constexpr (INV) {
         plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
-        const float* pf = reinterpret_cast<const float*>(plane);
         float* dst = reinterpret_cast<float*>(src);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int z = warp; z < g.N3; z += nw) {
-            const float* srow = pf + packed_row(z, g.Nh);
-            for (int x = lane; x < g.N1; x += 32) dst[z * g.N1 + x] = srow[2 * x];
+        // complex row jr holds real rows 2 jr (real parts) and 2 jr + 1 (imaginary parts)
+        for (int jr = warp; jr < (g.N3 >> 1); jr += nw) {
+            const float2* crow = plane + jr * 2 * g.Nh;
+            float* d0 = dst + 2 * jr * g.N1;
+            for (int x = lane; x < g.N1; x += 32) {
+                const float2 u = crow[x];
+                d0[x] = u.x;
+                d0[g.N1 + x] = u.y;
+            }
         }
     } else {
         plane_forward<CN1, CN3>(plane, g, tw1, tw3);
@@ -368,13 +373,14 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_w_planes(const float* __re
     const int y = blockIdx.x, c = blockIdx.y;
     load_line_twiddles<CN1>(tw1, tw, g.N1);
     load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
-    float* pf = reinterpret_cast<float*>(plane);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const float* gc = grad + c * g.N;
-    for (int z = warp; z < g.N3; z += nw) {
-        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-        float* dst = pf + packed_row(z, g.Nh);
-        for (int x = lane; x < g.N1; x += 32) dst[2 * x] = gfield[row + x] * gc[row + x];
+    const long long zs = (long long)g.N1 * g.N2;  // flat distance between rows z and z + 1
+    for (int jr = warp; jr < (g.N3 >> 1); jr += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * 2 * jr);
+        float2* crow = plane + jr * 2 * g.Nh;
+        for (int x = lane; x < g.N1; x += 32)
+            crow[x] = make_float2(gfield[row + x] * gc[row + x], gfield[row + zs + x] * gc[row + zs + x]);
     }
     __syncthreads();
     plane_forward<CN1, CN3>(plane, g, tw1, tw3);
@@ -453,12 +459,16 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_div_final(const float2* __
     for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     __syncthreads();
     plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
-    const float* pf = reinterpret_cast<const float*>(plane);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int z = warp; z < g.N3; z += nw) {
-        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
-        const float* srow = pf + packed_row(z, g.Nh);
-        for (int x = lane; x < g.N1; x += 32) v[row + x] -= srow[2 * x];
+    const long long zs = (long long)g.N1 * g.N2;
+    for (int jr = warp; jr < (g.N3 >> 1); jr += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * 2 * jr);
+        const float2* crow = plane + jr * 2 * g.Nh;
+        for (int x = lane; x < g.N1; x += 32) {
+            const float2 d = crow[x];
+            v[row + x] -= d.x;
+            v[row + zs + x] -= d.y;
+        }
     }
 }
 

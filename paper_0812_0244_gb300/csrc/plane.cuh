@@ -127,12 +127,10 @@ __device__ __forceinline__ void flat_point(long long i, const GridArgs& g, int& 
         y = (int)(r - (long long)z * g.N2);
     }
 }
-// float offset, within its plane, of real point (x, z = 2j + s) in the packed rows
+// Packed real rows: real rows 2j and 2j+1 of a plane are the real and
+// imaginary parts of complex row j, which starts at complex offset 2 Nh j.
+// This is the float offset, within its plane, of real point (x, z = 2j + s).
 __device__ __forceinline__ int packed_offset(int x, int j, int s, int Nh) { return 4 * j * Nh + 2 * x + s; }
-
-// Real rows 2j and 2j+1 share the complex row at offset j (2 Nh), as real and
-// imaginary parts; this is the float offset of the start of real row z.
-__device__ __forceinline__ int packed_row(int z, int Nh) { return 2 * ((z >> 1) * 2 * Nh) + (z & 1); }
 
 // Rows of a plane (complex row j holds real rows 2j and 2j+1) through the
 // x transform, several rows per warp at compile-time lengths; each row is
