@@ -459,16 +459,14 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_div_final(const float2* __
     for (int i = threadIdx.x; i < g.ncols; i += blockDim.x) plane[i] = src[i];
     __syncthreads();
     plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
+    const float* pf = reinterpret_cast<const float*>(plane);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const long long zs = (long long)g.N1 * g.N2;
-    for (int jr = warp; jr < (g.N3 >> 1); jr += nw) {
-        const long long row = (long long)g.N1 * (y + (long long)g.N2 * 2 * jr);
-        const float2* crow = plane + jr * 2 * g.Nh;
-        for (int x = lane; x < g.N1; x += 32) {
-            const float2 d = crow[x];
-            v[row + x] -= d.x;
-            v[row + zs + x] -= d.y;
-        }
+    // real row z: component z & 1 of complex row z / 2 (one row per warp: the
+    // read-modify-write of v keeps more rows in flight this way than by pairs)
+    for (int z = warp; z < g.N3; z += nw) {
+        const long long row = (long long)g.N1 * (y + (long long)g.N2 * z);
+        const float* srow = pf + 2 * ((z >> 1) * 2 * g.Nh) + (z & 1);
+        for (int x = lane; x < g.N1; x += 32) v[row + x] -= srow[2 * x];
     }
 }
 
