@@ -49,7 +49,7 @@ def measured_peaks():
 
 
 # algorithmic bytes per grid point of each stage (FP32 fields, complex64
-# half spectrum with Nh/N1 of the points); see the design doc
+# half spectrum with Nh/N1 of the points)
 def stage_bytes_per_point(Nq, N1):
     h = (N1 // 2 + 1) / N1
     return {
