@@ -446,6 +446,8 @@ def main():
             "stages_hbm_frac": stage_frac,
             "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
                     "d2h_bytes_per_step": 4 * N + 24},
+            # pointwise, forward planes, contraction, energy reduction, inverse
+            # planes, field sum, w planes, divergence pencils, final planes
             "gpu_launches": 9 * K,
             "cufft_reference": {"ms_per_step": cufft_ms,
                                 "what": "torch.fft (cuFFT) on the step's %d forward + %d inverse real 3D transforms "

@@ -159,7 +159,11 @@ int vdw_xc_energy_potential(vdw_handle h, const float* n, const float* grad, dou
 /* The same computation on host buffers (n[N], grad[3N] in; E[3], v[N] out):
  * copies the inputs to context-owned device buffers (allocated on first use),
  * runs vdw_energy_potential with the full potential, copies E and v back and
- * synchronises stream before returning. */
+ * synchronises stream before returning.  The inputs go up in up to four z
+ * slabs on a context-owned copy stream, and the pointwise pass processes each
+ * slab as soon as it has arrived; the results are bitwise those of
+ * vdw_energy_potential.  Host buffers should be page-locked for the copies to
+ * overlap. */
 int vdw_energy_potential_host(vdw_handle h, const float* n, const float* grad,
                               double* E, float* v, void* stream);
 

@@ -56,6 +56,13 @@ static void free_plan(vdw_ctx* c) {
     c->d_flags = nullptr;
     c->d_xc = nullptr;
     learned_free(c);
+    if (c->s_copy) cudaStreamDestroy(c->s_copy);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    for (int i = 0; i < 4; ++i)
+        if (c->ev_slab[i]) cudaEventDestroy(c->ev_slab[i]);
+    c->s_copy = nullptr;
+    c->ev_in = nullptr;
+    for (int i = 0; i < 4; ++i) c->ev_slab[i] = nullptr;
     c->planned = 0;
 }
 
@@ -180,7 +187,16 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     }
     const int Nq = c->p.Nq;
     const size_t spec_n = (size_t)Nq * n2 * g.ncols;
-    c->nb_point = (int)std::min<long long>((g.N + 255) / 256, 4096);
+    {
+        // pointwise slabs: 4, 3, 2 or 1 equal slabs of the N3/2 complex rows
+        const int nh3 = n3 / 2;
+        c->p0_chunks = (nh3 % 4 == 0) ? 4 : (nh3 % 3 == 0) ? 3 : (nh3 % 2 == 0) ? 2 : 1;
+        c->p0_nj = nh3 / c->p0_chunks;
+        c->p0_mnj = c->p0_nj > 1 ? 0xFFFFFFFFu / (unsigned)c->p0_nj + 1u : 0u;
+        const long long nb = std::min<long long>((g.N + 255) / 256, 4096);
+        c->nb_p0 = (int)((nb + c->p0_chunks - 1) / c->p0_chunks);
+        c->nb_point = c->nb_p0 * c->p0_chunks;
+    }
     c->nb_pencil = (g.ncols + c->pencil_cols - 1) / c->pencil_cols;
     VDW_CUDA(cudaMalloc(&c->d_tw, sizeof(float2) * (n1 + n2 + n3)));
     VDW_CUDA(cudaMalloc(&c->d_spec, sizeof(float2) * spec_n));
@@ -193,6 +209,9 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     VDW_CUDA(cudaMalloc(&c->d_gg, sizeof(float) * (size_t)g.N));
     VDW_CUDA(cudaMalloc(&c->d_flags, sizeof(int)));
     VDW_CUDA(cudaMalloc(&c->d_xc, sizeof(double) * (4 + 2 * 1024)));
+    VDW_CUDA(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
+    VDW_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    for (int i = 0; i < 4; ++i) VDW_CUDA(cudaEventCreateWithFlags(&c->ev_slab[i], cudaEventDisableTiming));
     VDW_CUDA(cudaMemset(c->d_flags, 0, sizeof(int)));
     VDW_CUDA(cudaMemset(c->d_invalid, 0, sizeof(unsigned long long)));
     rc = pipeline_make_twiddles(c);
@@ -261,9 +280,20 @@ int vdw_energy_potential_host(vdw_handle c, const float* n, const float* grad, d
         VDW_CUDA(cudaMalloc(&c->d_E, sizeof(double) * 3));
         c->bytes += sizeof(float) * 5 * N + sizeof(double) * 3;
     }
-    VDW_CUDA(cudaMemcpyAsync(c->d_in, n, sizeof(float) * N, cudaMemcpyHostToDevice, s));
-    VDW_CUDA(cudaMemcpyAsync(c->d_in + N, grad, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s));
-    int rc = pipeline_run(c, c->d_in, c->d_in + N, c->d_E, v ? c->d_v : nullptr, nullptr, s);
+    // the inputs go up slab by slab on the copy stream; the pointwise pass
+    // takes each slab as soon as it has arrived
+    VDW_CUDA(cudaEventRecord(c->ev_in, s));
+    VDW_CUDA(cudaStreamWaitEvent(c->s_copy, c->ev_in, 0));
+    const long long slab = 2LL * c->p0_nj * c->g.N2 * c->g.N1;  // points of a slab (contiguous in z)
+    for (int sl = 0; sl < c->p0_chunks; ++sl) {
+        const long long off = sl * slab;
+        VDW_CUDA(cudaMemcpyAsync(c->d_in + off, n + off, sizeof(float) * slab, cudaMemcpyHostToDevice, c->s_copy));
+        for (int d = 0; d < 3; ++d)
+            VDW_CUDA(cudaMemcpyAsync(c->d_in + N + d * N + off, grad + d * N + off, sizeof(float) * slab,
+                                     cudaMemcpyHostToDevice, c->s_copy));
+        VDW_CUDA(cudaEventRecord(c->ev_slab[sl], c->s_copy));
+    }
+    int rc = pipeline_run(c, c->d_in, c->d_in + N, c->d_E, v ? c->d_v : nullptr, nullptr, s, 0, 0, c->ev_slab);
     if (rc) return rc;
     if (E) VDW_CUDA(cudaMemcpyAsync(E, c->d_E, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
     if (v) VDW_CUDA(cudaMemcpyAsync(v, c->d_v, sizeof(float) * N, cudaMemcpyDeviceToHost, s));

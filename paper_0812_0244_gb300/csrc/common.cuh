@@ -107,6 +107,14 @@ struct vdw_ctx {
     float4* d_aux;              // [N] n dq/dn, n dq/d|grad n| / |grad n|, and the Delta E derivatives
     double* d_epart;            // per-block energy partial sums
     int nb_point, nb_pencil;    // their counts (pointwise, pencil kernels)
+    // the pointwise pass runs in p0_chunks slabs of p0_nj complex rows (2 p0_nj
+    // z values) with nb_p0 blocks each, so that the host entry point can copy
+    // slab c + 1 while slab c is processed (nb_point = p0_chunks * nb_p0)
+    int p0_chunks, p0_nj, nb_p0;
+    unsigned p0_mnj;            // ceil(2^32 / p0_nj) (multiply-high division)
+    cudaStream_t s_copy;        // copy stream of the host entry point
+    cudaEvent_t ev_in;          // orders the copy stream after the caller's stream
+    cudaEvent_t ev_slab[4];     // slab c of the inputs is on the device
     unsigned long long* d_invalid;  // count of negative / non-finite densities
     int pencil_cols;            // columns per pencil block
     int bulk_planes;            // inverse plane transforms load their planes by bulk copies
@@ -146,8 +154,10 @@ int cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 // pipeline launchers (pipeline.cu)
+// slab_ready (optional): per slab of the pointwise pass, an event to wait on
+// before processing it (the host entry point's copies)
 int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w,
-                 cudaStream_t s, int fd = 0, int xc = 0);
+                 cudaStream_t s, int fd = 0, int xc = 0, const cudaEvent_t* slab_ready = nullptr);
 // E[4] of the functional from the nonlocal energy (d_xc[0]) and the semilocal sums
 int pipeline_xc_final(vdw_ctx* c, double* E, cudaStream_t s);
 // central-difference gradient of a field (into grad [3][N])

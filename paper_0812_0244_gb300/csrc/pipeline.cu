@@ -49,23 +49,50 @@ constexpr int XC_BLOCKS = 1024;  // blocks (and partial-sum slots) of the semilo
 // spectrum buffer, and the Delta E partial sums.  aux (flat order) keeps
 // what the assembly of Eq. (Vi) needs besides the field sums:
 // {n dq/dn, n (dq/d|grad n|)/|grad n|, d(Delta eps)/dn, its grad n coefficient}.
+// The grid is cut into slabs of nj complex rows (z = 2 j0 .. 2 (j0 + nj) - 1
+// for slab j0 / nj), each walked in packed order within the slab: q = ((y nj
+// + (j - j0)) N1 + x) 2 + s, by nbs blocks of which block b writes its
+// Delta E partial sum to epart[slab nbs + b].  A launch with slab >= 0 does
+// that slab alone (grid nbs); with slab < 0 the grid holds nbs blocks for
+// every slab, block b doing block b mod nbs of slab b / nbs, so that both
+// forms give the same partial sums.  mnj = ceil(2^32 / nj) when g.fast.
 template <int NQ>
 __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, const float* __restrict__ grad,
-                                                   GridArgs g, PointParams P, float* __restrict__ t_out,
-                                                   uint8_t* __restrict__ k_out, float4* __restrict__ aux,
-                                                   float* __restrict__ specf, double* __restrict__ epart,
+                                                   GridArgs g, PointParams P, int slab, int nj, unsigned mnj,
+                                                   int nbs, float* __restrict__ t_out, uint8_t* __restrict__ k_out,
+                                                   float4* __restrict__ aux, float* __restrict__ specf,
+                                                   double* __restrict__ epart,
                                                    unsigned long long* __restrict__ invalid) {
     __shared__ double red[32];
     __shared__ SplineSmem sp;
     load_spline_smem(&sp, P);
     __syncthreads();
+    const int sl = slab >= 0 ? slab : (int)blockIdx.x / nbs;
+    const int lb = slab >= 0 ? (int)blockIdx.x : (int)blockIdx.x - sl * nbs;
+    const int j0 = sl * nj;
     const long long N = g.N;
+    const long long Nc = 2LL * g.N2 * nj * g.N1;    // points of the slab
     const long long fstride = 2LL * g.N2 * g.ncols;  // floats between the planes of two fields
     double acc = 0.0;
     unsigned int bad = 0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
-        int y, z, x, j;
-        const long long i = packed_point(q, g, y, z, x, j);
+    for (long long q = lb * (long long)blockDim.x + threadIdx.x; q < Nc; q += (long long)nbs * blockDim.x) {
+        int y, x, jj;
+        const int s = (int)(q & 1);
+        if (g.fast) {
+            const unsigned t = (unsigned)(q >> 1);
+            const unsigned rr = __umulhi(t, g.m1);
+            x = (int)(t - rr * (unsigned)g.N1);
+            y = nj == 1 ? (int)rr : (int)__umulhi(rr, mnj);
+            jj = (int)(rr - (unsigned)y * (unsigned)nj);
+        } else {
+            const long long t = q >> 1;
+            const long long rr = t / g.N1;
+            x = (int)(t - rr * g.N1);
+            y = (int)(rr / nj);
+            jj = (int)(rr - (long long)y * nj);
+        }
+        const int j = j0 + jj, z = 2 * j + s;
+        const long long i = ((long long)z * g.N2 + y) * g.N1 + x;
         const float ni = n[i];
         bad += (!(ni >= 0.f) || !isfinite(ni)) ? 1u : 0u;
         const QPoint qp = q_point(ni, grad[i], grad[N + i], grad[2 * N + i], P, sp.qm);
@@ -86,7 +113,7 @@ __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, 
         }
     }
     const double s = block_sum(acc, red);
-    if (threadIdx.x == 0) epart[blockIdx.x] = s;
+    if (threadIdx.x == 0) epart[sl * nbs + lb] = s;
     __syncthreads();
     const double b = block_sum((double)bad, red);
     if (threadIdx.x == 0 && b > 0.0) atomicAdd(invalid, (unsigned long long)b);
@@ -728,7 +755,7 @@ static int launch_u_sum(vdw_ctx* c, const float* n, const float* grad, float* v,
 
 template <int CN1, int CN2, int CN3>
 static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s,
-                     int fd, int xc) {
+                     int fd, int xc, const cudaEvent_t* slab_ready) {
     const GridArgs& g = c->g;
     const PointParams& P = c->pp;
     const bool want_pot = (v != nullptr) || (w != nullptr);
@@ -745,17 +772,24 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
     }
     VDW_CUDA(cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long), s));
     float* specf = reinterpret_cast<float*>(c->d_spec);
+    // one launch over all slabs, or (host entry point) one per slab as its inputs arrive
+    const int nlaunch = slab_ready ? c->p0_chunks : 1;
+    for (int sl = 0; sl < nlaunch; ++sl) {
+        if (slab_ready) VDW_CUDA(cudaStreamWaitEvent(s, slab_ready[sl], 0));
+        const int slab = slab_ready ? sl : -1;
+        const int nblk = slab_ready ? c->nb_p0 : c->nb_point;
 #define VDW_POINTWISE(NQ)                                                                                  \
-    k_pointwise<NQ><<<c->nb_point, 256, 0, s>>>(n, grad, g, P, c->d_t, c->d_k, c->d_aux, specf, c->d_epart, \
-                                                c->d_invalid)
-    switch (P.Nq) {
-        case 20: VDW_POINTWISE(20); break;
-        case 8: VDW_POINTWISE(8); break;
-        case 12: VDW_POINTWISE(12); break;
-        case 16: VDW_POINTWISE(16); break;
-        default: set_error("Nq not compiled in"); return VDW_ERR_UNSUPPORTED;
-    }
+    k_pointwise<NQ><<<nblk, 256, 0, s>>>(n, grad, g, P, slab, c->p0_nj, c->p0_mnj, c->nb_p0, c->d_t, c->d_k, \
+                                         c->d_aux, specf, c->d_epart, c->d_invalid)
+        switch (P.Nq) {
+            case 20: VDW_POINTWISE(20); break;
+            case 8: VDW_POINTWISE(8); break;
+            case 12: VDW_POINTWISE(12); break;
+            case 16: VDW_POINTWISE(16); break;
+            default: set_error("Nq not compiled in"); return VDW_ERR_UNSUPPORTED;
+        }
 #undef VDW_POINTWISE
+    }
     mark(0);
 
     const size_t sp = smem_plane(g);
@@ -911,11 +945,13 @@ int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, dou
 }
 
 int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s,
-                 int fd, int xc) {
+                 int fd, int xc, const cudaEvent_t* slab_ready) {
     const GridArgs& g = c->g;
-    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72) return run_sized<180, 180, 72>(c, n, grad, E, v, w, s, fd, xc);
-    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96) return run_sized<256, 256, 96>(c, n, grad, E, v, w, s, fd, xc);
-    return run_sized<0, 0, 0>(c, n, grad, E, v, w, s, fd, xc);
+    if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72)
+        return run_sized<180, 180, 72>(c, n, grad, E, v, w, s, fd, xc, slab_ready);
+    if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96)
+        return run_sized<256, 256, 96>(c, n, grad, E, v, w, s, fd, xc, slab_ready);
+    return run_sized<0, 0, 0>(c, n, grad, E, v, w, s, fd, xc, slab_ready);
 }
 
 int pipeline_xc_final(vdw_ctx* c, double* E, cudaStream_t s) {
