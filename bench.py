@@ -396,6 +396,24 @@ def main():
     except Exception:
         fd_ms = None
 
+    # the whole functional: revPBE exchange and LDA correlation beside the
+    # nonlocal term (Eq. Exc), same density and gradient
+    xc_ms = None
+    try:
+        Kx = min(K, 100)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * Kx)]
+        for _ in range(3):
+            ctx.xc_energy_potential(n, g, v)
+        for i in range(Kx):
+            flush.zero_()
+            ev[2 * i].record(stream)
+            ctx.xc_energy_potential(n, g, v)
+            ev[2 * i + 1].record(stream)
+        torch.cuda.synchronize()
+        xc_ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(Kx)) / Kx
+    except Exception:
+        xc_ms = None
+
     # learned reduced basis (M = 8 channels) on the same density: the trained
     # model if one is stored in the package, else its initialisation
     learned = None
@@ -455,6 +473,9 @@ def main():
                                         % (params.Nq + 3, params.Nq + 1)},
             "clocks": clocks,
             "learned_m8": learned,
+            "xc_functional": {"ms_per_step": xc_ms, "value": (N / (xc_ms * 1e-3)) if xc_ms else None,
+                              "unit": UNIT, "what": "vdw_xc_energy_potential: E_x^revPBE + E_c^LDA + E_c^nl "
+                                                    "and the potential of E_xc, spectral gradient"},
             "fd_gradient_variant": {"ms_per_step": fd_ms, "value": (N / (fd_ms * 1e-3)) if fd_ms else None,
                                     "unit": UNIT, "what": "vdw_energy_potential_fd: central-difference gradient, "
                                                           "chain term by stencil"},
