@@ -414,6 +414,36 @@ def main():
     except Exception:
         xc_ms = None
 
+    # the autograd Function on the 256 x 256 x 96 tube: forward (energy only)
+    # and backward (theta recomputed; dE/dn and dE/d grad n), n and grad n leaves
+    ag_ms = None
+    try:
+        from paper_0812_0244_gb300.autograd import vdw_energy
+        shape2 = (96, 256, 256)
+        n64, L2, _ = S.tube_density_torch(3, shape=shape2, device="cuda")
+        ctx2 = vdwnl.VdwNL(vdwnl.Params()).plan(shape2, L2)
+        n2 = n64.to(torch.float32).contiguous()
+        g2 = ctx2.spectral_gradient(n2)
+        del n64
+        n2.requires_grad_(True)
+        g2.requires_grad_(True)
+        Ka = min(K, 40)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * Ka)]
+        for i in range(3 + Ka):
+            flush.zero_()
+            if i >= 3:
+                ev[2 * (i - 3)].record(stream)
+            vdw_energy(n2, g2, ctx2).backward()
+            if i >= 3:
+                ev[2 * (i - 3) + 1].record(stream)
+            n2.grad = None
+            g2.grad = None
+        torch.cuda.synchronize()
+        ag_ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(Ka)) / Ka
+        del ctx2, n2, g2
+    except Exception:
+        ag_ms = None
+
     # learned reduced basis (M = 8 channels) on the same density: the trained
     # model if one is stored in the package, else its initialisation
     learned = None
@@ -473,6 +503,10 @@ def main():
                                         % (params.Nq + 3, params.Nq + 1)},
             "clocks": clocks,
             "learned_m8": learned,
+            "autograd_256x256x96": {"ms_per_step": ag_ms,
+                                    "value": (256 * 256 * 96 / (ag_ms * 1e-3)) if ag_ms else None, "unit": UNIT,
+                                    "what": "torch.autograd.Function forward (E) + backward (theta recomputed, "
+                                            "dE/dn and dE/d grad n) on the 256x256x96 tube"},
             "xc_functional": {"ms_per_step": xc_ms, "value": (N / (xc_ms * 1e-3)) if xc_ms else None,
                               "unit": UNIT, "what": "vdw_xc_energy_potential: E_x^revPBE + E_c^LDA + E_c^nl "
                                                     "and the potential of E_xc, spectral gradient"},
