@@ -506,8 +506,26 @@ __device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const float2*
             const int k = j % Ns;
             float2* q = p + l * ls;
             const int base = (j - k) * R + k;
+            if constexpr (HALF && Ns == 1 && R == 16) {
+                // the outputs of butterfly j go to 16 j + r: with the same r in
+                // every lane the 16 lanes of a half-warp would hit one bank.
+                // Rotate each lane's outputs by j (four conditional rotations
+                // by 1, 2, 4, 8) so that step r' stores output (r' + j) mod 16.
 #pragma unroll
-            for (int r = 0; r < R; ++r) q[(base + r * Ns) * es] = v[b][r];
+                for (int bit = 0; bit < 4; ++bit) {
+                    const bool rot = (j >> bit) & 1;
+                    float2 t[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) t[r] = v[b][(r + (1 << bit)) & (R - 1)];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) v[b][r] = rot ? t[r] : v[b][r];
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) q[(base + ((r + j) & (R - 1))) * es] = v[b][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) q[(base + r * Ns) * es] = v[b][r];
+            }
         }
     }
     __syncwarp();
