@@ -49,20 +49,42 @@ def measured_peaks():
 
 
 # algorithmic bytes per grid point of each stage (FP32 fields, complex64
-# half spectrum with Nh/N1 of the points)
+# half spectrum with h = Nh/N1 of the points); the stage names are those of
+# VdwNL.STAGES
 def stage_bytes_per_point(Nq, N1):
     h = (N1 // 2 + 1) / N1
     return {
         "pointwise": 16 + 5 + Nq * 4 + 16,         # n, grad in; t, k, real theta, assembly coefficients out
-        "theta_plane": Nq * 4 + Nq * 8 * h,        # real theta in; theta(G) out
-        "pencil_contract": 2 * Nq * 8 * h,         # theta(G) in, u(G) out
+        "planes_fwd": Nq * 4 + Nq * 8 * h,         # real theta in; theta(G) (x, z transformed) out
+        "pencils_fwd": 2 * Nq * 8 * h,             # theta(G) in; y-transformed points in |G| order out
+        "contract": 2 * Nq * 8 * h + 4 * h,        # theta(G) and |G| in, u(G) out
         "energy_final": 0.0,
-        # inverse plane transforms: u(G) in, real u out; the sum: real u, t, k,
-        # coefficients in, v_loc and g out; the w transforms: g, grad in, w(G) out
-        "assemble": Nq * 8 * h + Nq * 4 + Nq * 4 + 5 + 16 + 4 + 4 + 4 + 12 + 3 * 8 * h,
+        "pencils_inv": 2 * Nq * 8 * h,             # u(G) in |G| order in; y-transformed back out
+        "planes_inv": Nq * 8 * h + Nq * 4,         # u(G) in; real u out
+        "usum": Nq * 4 + 5 + 16 + 4 + 4,           # real u, t, k, coefficients in; v_loc and g out
+        "w_planes": 4 + 12 + 3 * 8 * h,            # g, grad in; w(G) out
         "pencil_div": 3 * 8 * h + 8 * h,           # w(G) in, D.w(G) out
         "div_final": 8 * h + 4 + 4,                # D.w(G), v_loc in; v out
     }
+
+
+def contract_flops_per_point(Nq, N1):
+    """FP32 flops of the contraction per grid point: per half-spectrum point
+    Nq(Nq+1)/2 cubic evaluations (3 FMA), the symmetric matrix-vector product
+    (4 FMA per off-diagonal pair, 2 per diagonal one), the energy (2 FMA per
+    field) and the 1/N scaling (2 products per field); 2 flops per FMA."""
+    NP = Nq * (Nq + 1) // 2
+    fma = 3 * NP + 4 * (NP - Nq) + 2 * Nq + 2 * Nq
+    return (2 * fma + 2 * Nq) * (N1 // 2 + 1) / N1
+
+
+# FP32 peak of the GPU from its unit counts: 152 SMs x 128 FP32 lanes x 2
+# flops per FMA x the SM clock (2070 MHz at most)
+FP32_LANES = 152 * 128
+
+
+def fp32_peak_tflops(sm_mhz):
+    return FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
 
 
 def source_sha1():
@@ -163,59 +185,93 @@ class ClockSampler:
                 "window": "timed region" if inside else "whole run (no sample fell inside the timed region)"}
 
 
-def oracle_sample_rate(timeout=600):
-    """Time the FP64 oracle (as it stands) on one axial period of the tube
-    (180 x 180 x 18 points, the same grid spacing and density recipe) in a
-    single-threaded child process; returns (points/s, seconds, points)."""
-    code = r"""
+ORACLE_SAMPLE = r"""
 import os, sys, time, json
 sys.path.insert(0, %r)
 import numpy as np
 import oracle as O
 from paper_0812_0244_gb300 import synthetic as S
 T = O.kernel_table(O.Params())
-d = S.tube_density(0, shape=(18, 180, 180), cell_ang=(25.0, 25.0, 2.46))
+d = S.tube_density(int(sys.argv[1]), shape=(18, 180, 180), cell_ang=(25.0, 25.0, 2.46))
 n = d["n"].astype(np.float32).astype(np.float64)
-g = d["grad"].astype(np.float32).astype(np.float64)
-t0 = time.perf_counter()
+g = O.spectral_gradient(n, d["L"]).astype(np.float32).astype(np.float64)
+t0 = time.time()
 r = O.energy_potential(n, g, d["L"], T)
-dt = time.perf_counter() - t0
-print(json.dumps({"points": int(n.size), "seconds": dt, "E": r["E"]}))
-""" % ROOT
+t1 = time.time()
+print(json.dumps({"points": int(n.size), "t0": t0, "t1": t1, "E": r["E"]}))
+"""
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(procs=1, timeout=900):
+    """Time the FP64 oracle (as it stands, one thread per process) on one
+    axial period of the tube (180 x 180 x 18 points, the workload's grid
+    spacing and density recipe, grad n = D n), in `procs` child processes at
+    once, one sample each.  Returns (aggregate points/s, seconds of the
+    overlapped window, points per sample)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["points"] / d["seconds"], d["seconds"], d["points"]
+    code = ORACLE_SAMPLE % ROOT
+    ps = [subprocess.Popen([sys.executable, "-c", code, str(i)], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True, env=env) for i in range(procs)]
+    outs = []
+    for p in ps:
+        o, e = p.communicate(timeout=timeout)
+        if p.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + e[-2000:])
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    t0 = min(d["t0"] for d in outs)
+    t1 = max(d["t1"] for d in outs)
+    pts = outs[0]["points"]
+    return procs * pts / (t1 - t0), t1 - t0, pts
+
+
+def cpu_baselines():
+    """The oracle on one core, then on every core of the process's affinity
+    set (independent samples, one process per core)."""
+    r1, s1, pts = oracle_rate(1)
+    ncores = host_cores()
+    rn, sn, _ = oracle_rate(ncores)
+    return {"value": rn, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": "FP64 numpy/C oracle, E and v of one axial period of the tube (180x180x18 of the 180x180x72 "
+                      "grid, %d points, grad n = D n) per process, %d single-threaded processes at once (%.1f s)"
+                      % (pts, ncores, sn),
+            "single_core": {"value": r1, "cores": 1, "seconds": s1}}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    K = max(1, min(args.steps, 4))
-    W = min(args.warmup, 3)
+    K = max(1, min(args.steps, 3))
+    W = min(args.warmup, 1)
+    ncores = host_cores()
     total_pts, total_s = 0, 0.0
     for i in range(W + K):
-        rate, sec, pts = oracle_sample_rate()
+        rate, sec, pts = oracle_rate(ncores)
         if i >= W:
-            total_pts += pts
+            total_pts += ncores * pts
             total_s += sec
     value = total_pts / total_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": K, "warmup": W, "ms_per_step": 1e3 * total_s / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "one axial period, 180x180x18 points"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "FP64 numpy/C oracle, E and v on one axial period of the tube "
-                                       "(180x180x18 of the 180x180x72 grid), single thread, %d steps" % K},
+            "config": {"workload": WORKLOAD, "sample": "one axial period (180x180x18 points) per host core"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                             "sample": "FP64 numpy/C oracle, E and v of one axial period of the tube (180x180x18 "
+                                       "of the 180x180x72 grid) in each of %d single-threaded processes, %d steps"
+                                       % (ncores, K)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def learned_leg(ctx, n, g, E, v, flush, stream, K, E_plain, natoms, ms_plain, N):
+def learned_leg(ctx, n, g, E, v, flush, stream, K, E_plain, v_plain, natoms, ms_plain, N):
     """Time the learned 8-channel path (E and v) like the plain one and compare
-    its energy with the plain Nq = 20 energy of the same density."""
+    its energy and potential with the plain Nq = 20 results of the same density."""
     import torch
     from paper_0812_0244_gb300 import learned as LR
     from paper_0812_0244_gb300 import vdwnl
@@ -245,6 +301,10 @@ def learned_leg(ctx, n, g, E, v, flush, stream, K, E_plain, natoms, ms_plain, N)
     torch.cuda.synchronize()
     ms_l = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K
     El = float(E[0])
+    dv = (v.double() - v_plain.double())
+    w = n.double()
+    vrms = float(torch.sqrt((w * dv * dv).sum() / w.sum()) / torch.sqrt((w * v_plain.double() ** 2).sum() / w.sum()))
+    vmax = float(dv.abs().max() / v_plain.double().abs().max())
     ctx.profile(True)
     ctx.learned_energy_potential(n, g, E, v)
     stages = {k: round(t, 4) for k, t in ctx.profile_read().items()}
@@ -252,7 +312,21 @@ def learned_leg(ctx, n, g, E, v, flush, stream, K, E_plain, natoms, ms_plain, N)
     return {"model": kind, "ms_per_step": ms_l, "value": N / (ms_l * 1e-3), "unit": UNIT,
             "speedup_vs_plain_nq20": ms_plain / ms_l, "stages_ms": stages,
             "energy_error_mev_per_atom_vs_plain_nq20": (El - E_plain) / natoms * 27211.386245988,
+            "potential_vs_plain_nq20": {"density_weighted_rms_rel": vrms, "max_abs_rel": vmax},
             "tc_error": ctx.learned_status()}
+
+
+def timed(fn, K, flush, stream):
+    """Mean CUDA-event time (ms) of fn() over K calls, L2 flushed before each."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+    for i in range(K):
+        flush.zero_()
+        ev[2 * i].record(stream)
+        fn()
+        ev[2 * i + 1].record(stream)
+    torch.cuda.synchronize()
+    return sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(K)) / K
 
 
 def main():
@@ -262,6 +336,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-only", action="store_true",
+                    help="time the plain call alone (no stage profile, other legs or host-buffer figure)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -270,6 +346,11 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+
+    # CPU baseline first (child processes, before this process touches the GPU)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.plain_only:
+        cpu = cpu_baselines()
 
     import torch
     import torch.distributed as dist
@@ -285,23 +366,15 @@ def main():
         if world > 1:
             dist.barrier()
 
-    # CPU baseline first (child process, before this process does GPU work)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, sec, pts = oracle_sample_rate()
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "FP64 numpy/C oracle, E and v on one axial period of the tube (180x180x18 of the "
-                         "180x180x72 grid, %d points, %.1f s), single thread" % (pts, sec)}
-
     d = S.tube_density(rank)
     n_h = d["n"].astype(np.float32)
-    g_h = d["grad"].astype(np.float32)
     N = n_h.size
     params = vdwnl.Params()
     ctx = vdwnl.VdwNL(params)
     ctx.plan(n_h.shape, d["L"])
     n = torch.tensor(n_h, device=dev)
-    g = torch.tensor(g_h, device=dev)
+    g = ctx.spectral_gradient(n)  # grad n = D n, the library's spectral derivative
+    torch.cuda.synchronize()
     E = torch.empty(3, dtype=torch.float64, device=dev)
     v = torch.empty_like(n)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
@@ -326,14 +399,36 @@ def main():
         torch.cuda.synchronize()
         clk.mark("stop")
         barrier()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(step_ms) / K
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * N / (ms * 1e-3)
     Eh = E.cpu().numpy()
+    peak, peak_kind = measured_peaks()
+    clocks = clk.summary() if rank == 0 else None
+    base = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded double-wall tube density; grad n = D n by the library's "
+                                "spectral derivative)",
+        "config": {"workload": WORKLOAD, "grid": [180, 180, 72], "Nq": params.Nq, "cell_angstrom": [25, 25, 9.84],
+                   "sites": int(d["natoms"]), "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed (256 MiB write) before every timed step", "energy_fp64": float(Eh[0])},
+        # pointwise, forward planes, forward y pencils, contraction, energy
+        # reduction, inverse y pencils, inverse planes, field sum, w planes,
+        # divergence pencils, final planes
+        "gpu_launches": 11 * K,
+        "clocks": clocks,
+    }
+    if args.plain_only:
+        if rank == 0:
+            print(json.dumps(base), flush=True)
+        ctx.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     # per-stage durations (separate, untimed iterations with stage events)
     ctx.profile(True)
@@ -347,9 +442,11 @@ def main():
     ctx.profile(False)
     sb = stage_bytes_per_point(params.Nq, n_h.shape[2])
     top = max((k2 for k2 in acc if k2 != "energy_final"), key=lambda k2: acc[k2])
-    peak, peak_kind = measured_peaks()
     achieved = sb[top] * N / (acc[top] * 1e-3) / 1e9
     traffic = captured_traffic(top)
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    alu_peak = fp32_peak_tflops(sm_mhz)
+    alu_achieved = contract_flops_per_point(params.Nq, n_h.shape[2]) * N / (acc["contract"] * 1e-3) / 1e12
 
     # reference only: cuFFT (through torch.fft) on the transforms of one step:
     # Nq forward and Nq inverse real 3D transforms, plus 3 forward and 1
@@ -358,23 +455,16 @@ def main():
     try:
         fields = torch.randn((params.Nq,) + n_h.shape, device=dev, dtype=torch.float32)
         wf = torch.randn((3,) + n_h.shape, device=dev, dtype=torch.float32)
-        for _ in range(3):
-            torch.fft.irfftn(torch.fft.rfftn(fields, dim=(1, 2, 3)), s=n_h.shape, dim=(1, 2, 3))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tot = 0.0
-        reps = 10
-        for _ in range(reps):
-            flush.zero_()
-            e0.record(stream)
+
+        def cufft_step():
             th = torch.fft.rfftn(fields, dim=(1, 2, 3))
             torch.fft.irfftn(th, s=n_h.shape, dim=(1, 2, 3))
             wh = torch.fft.rfftn(wf, dim=(1, 2, 3))
             torch.fft.irfftn(wh[0], s=n_h.shape, dim=(0, 1, 2))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            tot += e0.elapsed_time(e1)
-        cufft_ms = tot / reps
-        del fields, wf, th, wh
+        for _ in range(3):
+            cufft_step()
+        cufft_ms = timed(cufft_step, 10, flush, stream)
+        del fields, wf
     except Exception:
         cufft_ms = None
 
@@ -382,17 +472,10 @@ def main():
     # operator; the chain term is a stencil instead of three transforms)
     fd_ms = None
     try:
-        Kf = min(K, 100)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * Kf)]
+        # grad = None: the library's central-difference gradient, inside the call
         for _ in range(3):
-            ctx.energy_potential_fd(n, g, E, v)
-        for i in range(Kf):
-            flush.zero_()
-            ev[2 * i].record(stream)
-            ctx.energy_potential_fd(n, g, E, v)
-            ev[2 * i + 1].record(stream)
-        torch.cuda.synchronize()
-        fd_ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(Kf)) / Kf
+            ctx.energy_potential_fd(n, None, E, v)
+        fd_ms = timed(lambda: ctx.energy_potential_fd(n, None, E, v), min(K, 100), flush, stream)
     except Exception:
         fd_ms = None
 
@@ -400,17 +483,9 @@ def main():
     # nonlocal term (Eq. Exc), same density and gradient
     xc_ms = None
     try:
-        Kx = min(K, 100)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * Kx)]
         for _ in range(3):
             ctx.xc_energy_potential(n, g, v)
-        for i in range(Kx):
-            flush.zero_()
-            ev[2 * i].record(stream)
-            ctx.xc_energy_potential(n, g, v)
-            ev[2 * i + 1].record(stream)
-        torch.cuda.synchronize()
-        xc_ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(Kx)) / Kx
+        xc_ms = timed(lambda: ctx.xc_energy_potential(n, g, v), min(K, 100), flush, stream)
     except Exception:
         xc_ms = None
 
@@ -427,34 +502,35 @@ def main():
         del n64
         n2.requires_grad_(True)
         g2.requires_grad_(True)
-        Ka = min(K, 40)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * Ka)]
-        for i in range(3 + Ka):
-            flush.zero_()
-            if i >= 3:
-                ev[2 * (i - 3)].record(stream)
+
+        def ag_step():
             vdw_energy(n2, g2, ctx2).backward()
-            if i >= 3:
-                ev[2 * (i - 3) + 1].record(stream)
             n2.grad = None
             g2.grad = None
-        torch.cuda.synchronize()
-        ag_ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(Ka)) / Ka
+        for _ in range(3):
+            ag_step()
+        ag_ms = timed(ag_step, min(K, 40), flush, stream)
         del ctx2, n2, g2
     except Exception:
         ag_ms = None
+
+    # plain potential of the same density, for the learned comparison
+    ctx.energy_potential(n, g, E, v)
+    v_plain = v.clone()
+    E_plain = float(E[0])
 
     # learned reduced basis (M = 8 channels) on the same density: the trained
     # model if one is stored in the package, else its initialisation
     learned = None
     try:
-        learned = learned_leg(ctx, n, g, E, v, flush, stream, min(K, 100), float(Eh[0]), int(d["natoms"]), ms, N)
+        learned = learned_leg(ctx, n, g, E, v, flush, stream, min(K, 100), E_plain, v_plain, int(d["natoms"]), ms,
+                              N)
     except Exception as ex:  # reported, never silently replaced
         learned = {"error": str(ex)[:200]}
 
     # end to end through the host-pointer entry point (pinned buffers)
     n_p = torch.from_numpy(n_h).pin_memory()
-    g_p = torch.from_numpy(g_h).pin_memory()
+    g_p = g.cpu().pin_memory()
     v_p = torch.empty(n_h.shape, dtype=torch.float32).pin_memory()
     E_p = np.zeros(3)
     Ke = max(1, min(K, 50))
@@ -473,20 +549,18 @@ def main():
         e2e_s = float(t.item())
 
     if rank == 0:
-        clocks = clk.summary()
         stage_frac = {k2: round(sb[k2] * N / (t2 * 1e-3) / 1e9 / peak, 4) for k2, t2 in acc.items() if sb[k2] > 0}
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
-            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [180, 180, 72], "Nq": params.Nq, "cell_angstrom": [25, 25, 9.84],
-                       "sites": int(d["natoms"]), "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "flushed (256 MiB write) before every timed step",
-                       "energy_fp64": float(Eh[0])},
+        line = dict(base)
+        line.update({
             "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                          "peak_kind": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind if peak_kind == "measured"
                          else "fallback 6.8 TB/s", "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "bytes_per_point": sb[top], "launch_ms": acc[top]},
+                         "traffic": traffic, "bytes_per_point": sb[top], "launch_ms": acc[top],
+                         "alu": {"kernel": "contract", "flops_per_point": contract_flops_per_point(params.Nq,
+                                                                                                  n_h.shape[2]),
+                                 "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                                 "frac": alu_achieved / alu_peak,
+                                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_mhz}},
             "step_roofline": {"bytes_per_point": b_alg(params.Nq),
                               "achieved_gbs": b_alg(params.Nq) * N / (ms * 1e-3) / 1e9,
                               "frac": b_alg(params.Nq) * N / (ms * 1e-3) / 1e9 / peak},
@@ -494,14 +568,10 @@ def main():
             "stages_hbm_frac": stage_frac,
             "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 16 * N,
                     "d2h_bytes_per_step": 4 * N + 24},
-            # pointwise, forward planes, contraction, energy reduction, inverse
-            # planes, field sum, w planes, divergence pencils, final planes
-            "gpu_launches": 9 * K,
             "cufft_reference": {"ms_per_step": cufft_ms,
                                 "what": "torch.fft (cuFFT) on the step's %d forward + %d inverse real 3D transforms "
                                         "alone, no pointwise work or contraction; reference only"
                                         % (params.Nq + 3, params.Nq + 1)},
-            "clocks": clocks,
             "learned_m8": learned,
             "autograd_256x256x96": {"ms_per_step": ag_ms,
                                     "value": (256 * 256 * 96 / (ag_ms * 1e-3)) if ag_ms else None, "unit": UNIT,
@@ -511,9 +581,9 @@ def main():
                               "unit": UNIT, "what": "vdw_xc_energy_potential: E_x^revPBE + E_c^LDA + E_c^nl "
                                                     "and the potential of E_xc, spectral gradient"},
             "fd_gradient_variant": {"ms_per_step": fd_ms, "value": (N / (fd_ms * 1e-3)) if fd_ms else None,
-                                    "unit": UNIT, "what": "vdw_energy_potential_fd: central-difference gradient, "
-                                                          "chain term by stencil"},
-        }
+                                    "unit": UNIT, "what": "vdw_energy_potential_fd: central-difference gradient "
+                                                          "(computed in the call), chain term by stencil"},
+        })
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -40,6 +40,9 @@ extern "C" {
 #define VDW_ERR_OOM (-4)     /* device allocation failed                         */
 #define VDW_ERR_STATE (-5)   /* call made before vdw_plan                        */
 #define VDW_ERR_UNSUPPORTED (-6) /* Nq not compiled in                           */
+#define VDW_ERR_TIMEOUT (-7) /* a kernel of an earlier call gave up a bounded
+                                wait (see vdw_wait_status); that call's
+                                results may be wrong                        */
 
 /* ---- method parameters --------------------------------------------------
  * Nq, q_c, m_c   interpolation mesh size (paper: "N_alpha ~ 20"), saturation
@@ -134,6 +137,28 @@ int vdw_plan(vdw_handle h, int n1, int n2, int n3, const double L[3]);
 int vdw_energy_potential(vdw_handle h, const float* n, const float* grad,
                          double* E, float* v, float* w, void* stream);
 
+/* ---- several densities per call ------------------------------------------
+ * The per-SCF-step cost of the method is its Nq forward and Nq inverse FFTs
+ * (text after Eq. Eoffk); a training set or an energy-map scan evaluates many
+ * densities of one grid.  vdw_plan_batch sizes the context's per-density
+ * workspaces for Bmax densities (about (Nq + 3) (N1/2+1) N2 N3 complex FP32
+ * values, twice over, plus 25 N bytes, per density); the kernel table, the
+ * twiddles and the |G| order stay shared.  It synchronises the device, and
+ * replaces the workspaces of earlier calls; vdw_plan resets Bmax to 1.
+ * Returns VDW_ERR_OOM if they do not fit (the context must then be planned
+ * again).  Synchronous. */
+int vdw_plan_batch(vdw_handle h, int Bmax);
+
+/* E_c^nl and v_nl of B <= Bmax densities of the planned grid in one call,
+ * each stage one kernel launch over all of them (device pointers,
+ * caller-owned, contiguous per density):
+ *   n [B][N], grad [B][3][N] (required), E [B][3] FP64 ({E_c^nl, E_soft,
+ *   Delta E} per density), v [B][N] or NULL (energy only).
+ * Density b's results are bitwise those of vdw_energy_potential on n[b],
+ * grad[b].  Asynchronous on stream. */
+int vdw_energy_potential_batched(vdw_handle h, int B, const float* n, const float* grad, double* E, float* v,
+                                 void* stream);
+
 /* The same energy with the finite-difference gradient of the paper's own
  * implementation: grad n by second-order central differences on the periodic
  * grid, (f(r + h_c e_c) - f(r - h_c e_c)) / (2 h_c).  grad (device [3][N])
@@ -172,20 +197,24 @@ int vdw_energy_potential_host(vdw_handle h, const float* n, const float* grad,
 int vdw_last_invalid_points(vdw_handle h, long long* count);
 
 /* Per-stage timing, for measurement.  While enabled, vdw_energy_potential
- * records a CUDA event on its stream before its first kernel and after each
- * stage: 0 pointwise (q, interval, theta, Delta E), 1 forward plane FFT,
- * 2 pencil FFT + contraction + energy, 3 energy reduction, 4 inverse plane
- * FFT + potential assembly + plane FFT of w, 5 divergence pencils, 6 final
- * planes.
+ * (and the learned and finite-difference variants) record a CUDA event on
+ * the stream before the first kernel and after each stage:
+ *   0 pointwise (q, interval, theta, Delta E)   1 forward plane FFTs (x, z)
+ *   2 forward y FFTs into |G| order             3 contraction (Eqs. Eoffk, epsofk)
+ *   4 energy reduction                          5 inverse y FFTs
+ *   6 inverse plane FFTs                        7 potential assembly (Eq. Vi)
+ *   8 plane FFTs of w                           9 divergence pencils
+ *  10 final planes (or the stencil divergence of the finite-difference form)
  * vdw_profile_read synchronises on the last recorded event and writes the
- * durations (ms) of the stages the last call ran into ms[0..6] (-1 for stages
- * it skipped).  Disabled by default; enabling costs 8 event records a call. */
-#define VDW_NSTAGES 7
+ * durations (ms) of the stages the last call ran into ms[0..10] (-1 for
+ * stages it skipped).  Disabled by default; enabling costs up to 12 event
+ * records a call. */
+#define VDW_NSTAGES 11
 int vdw_profile_enable(vdw_handle h, int enable);
 int vdw_profile_read(vdw_handle h, float* ms);
 
 /* ---- Delta E without device allocation ---------------------------------
- * The paper has no counterpart to this entry point; it exists for callers
+ * The paper has no counterpart to this entry point.  It exists for callers
  * that must not allocate device memory when they evaluate the energy: a
  * program whose device memory all belongs to its own pool allocator, a
  * plugin host that forbids allocations inside a step, or code that cannot
@@ -193,8 +222,8 @@ int vdw_profile_read(vdw_handle h, float* ms);
  * once beforehand (vdw_create allocates its tables; vdw_plan is not needed);
  * this call then allocates nothing.
  *
- * Computes Delta E = dOmega sum_i C_s n_i^2 / (2 q_i^3), the local correction
- * of Eqs. (DEnl, Depsnl) -- the value vdw_energy_potential returns in E[2] --
+ * Computes Delta E = dOmega sum_i C_s n_i^2 / (2 q_i^3), the local
+ * softening correction (the value vdw_energy_potential returns in E[2]),
  * for n[npoints] and grad[3][npoints] (device, FP32) and writes it to *dE
  * (device, FP64).  Its per-block partial sums live in a fixed 32 KiB array
  * of the library (4096 FP64 slots, one per 4096 points), which every GPU that
@@ -302,9 +331,17 @@ int vdw_adam_step(float* p, const double* g, float* m, float* v, long long count
                   double beta2, double eps, int step, void* stream);
 
 /* *gave_up = 1 if, since vdw_plan, a bounded wait inside a kernel (an
- * asynchronous copy or a tensor-core completion) ran out and the kernel
- * carried on without it, so results may be wrong; else 0.  Every such wait
- * polls a bounded number of times instead of spinning forever.  Synchronous. */
+ * asynchronous copy or a tensor-core completion) ran out, else 0.  Every such
+ * wait polls a bounded number of times instead of spinning forever; a kernel
+ * whose wait gives up waits once more (bounded) for the operation in flight,
+ * then stops without using its data (a plane transform leaves its plane
+ * as it was, a network warpgroup skips its remaining tiles), so that call's
+ * results are wrong.  The flag lives in page-locked host memory: the next call
+ * of vdw_energy_potential, vdw_energy_potential_fd, vdw_xc_energy_potential,
+ * vdw_energy_potential_host, vdw_learned_energy_potential or
+ * vdw_learned_param_grad on the context returns VDW_ERR_TIMEOUT without
+ * running (and clears the flag), and this call keeps reporting 1 until the
+ * next vdw_plan.  Synchronous. */
 int vdw_wait_status(vdw_handle h, int* gave_up);
 
 /* Bytes of device memory the context holds. */

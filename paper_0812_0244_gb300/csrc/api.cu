@@ -19,6 +19,16 @@ int cuda_fail(cudaError_t e, const char* what) {
     return (e == cudaErrorMemoryAllocation) ? VDW_ERR_OOM : VDW_ERR_CUDA;
 }
 
+int check_wait(vdw_ctx* c) {
+    volatile int* f = c->h_flags;
+    if (!f || (f[0] == 0 && f[1] == 0)) return VDW_OK;
+    c->wait_seen = 1;
+    f[0] = 0;
+    f[1] = 0;
+    g_last_error = "a bounded wait inside a kernel of an earlier call gave up; that call's results may be wrong";
+    return VDW_ERR_TIMEOUT;
+}
+
 static bool smooth235(int n) {
     if (n < 1) return false;
     for (int r : {2, 3, 5})
@@ -28,6 +38,9 @@ static bool smooth235(int n) {
 
 static void free_plan(vdw_ctx* c) {
     cudaFree(c->d_tw);
+    cudaFree(c->d_Q);
+    c->d_Q = nullptr;
+    c->batch_max = 0;
     cudaFree(c->d_spec);
     cudaFree(c->d_wspec);
     cudaFree(c->d_t);
@@ -50,12 +63,14 @@ static void free_plan(vdw_ctx* c) {
     cudaFree(c->d_gtmp);
     c->d_gtmp = nullptr;
     cudaFree(c->d_gg);
-    cudaFree(c->d_flags);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
+    c->h_flags = nullptr;
     cudaFree(c->d_xc);
     c->d_gg = nullptr;
     c->d_flags = nullptr;
     c->d_xc = nullptr;
     learned_free(c);
+    sorted_free(c);
     if (c->s_copy) cudaStreamDestroy(c->s_copy);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     for (int i = 0; i < 4; ++i)
@@ -64,6 +79,53 @@ static void free_plan(vdw_ctx* c) {
     c->ev_in = nullptr;
     for (int i = 0; i < 4; ++i) c->ev_slab[i] = nullptr;
     c->planned = 0;
+}
+
+// The per-density workspaces for Bmax densities at once (spectra, records,
+// w spectra, the pointwise results and the energy partial sums), with the
+// batch strides the kernels use.  Frees the previous ones.
+int alloc_density_work(vdw_ctx* c, int Bmax) {
+    GridArgs& g = c->g;
+    const size_t Nq = (size_t)c->p.Nq, N = (size_t)g.N;
+    const size_t spec_n = Nq * g.N2 * g.ncols, wspec_n = 3 * (size_t)g.N2 * g.ncols;
+    const size_t q_n = Nq * (size_t)c->Npad / 2;  // float4 values (Nq/4 quads of Npad 32-byte records)
+    const size_t ep_n = (size_t)c->nb_point + c->nb_sorted;
+    const size_t old = c->batch_max > 0
+                           ? (size_t)c->batch_max * (8 * (spec_n + wspec_n) + 16 * q_n + 25 * N + 8 * ep_n)
+                           : 0;
+    cudaFree(c->d_spec);
+    cudaFree(c->d_wspec);
+    cudaFree(c->d_Q);
+    cudaFree(c->d_t);
+    cudaFree(c->d_k);
+    cudaFree(c->d_aux);
+    cudaFree(c->d_gg);
+    cudaFree(c->d_epart);
+    c->d_spec = c->d_wspec = nullptr;
+    c->d_Q = nullptr;
+    c->d_t = c->d_gg = nullptr;
+    c->d_k = nullptr;
+    c->d_aux = nullptr;
+    c->d_epart = nullptr;
+    c->bytes -= old;
+    c->batch_max = 0;
+    const size_t B = (size_t)Bmax;
+    VDW_CUDA(cudaMalloc(&c->d_spec, sizeof(float2) * spec_n * B));
+    VDW_CUDA(cudaMalloc(&c->d_wspec, sizeof(float2) * wspec_n * B));
+    VDW_CUDA(cudaMalloc(&c->d_Q, sizeof(float4) * q_n * B));
+    VDW_CUDA(cudaMemset(c->d_Q, 0, sizeof(float4) * q_n * B));  // padding records stay zero
+    VDW_CUDA(cudaMalloc(&c->d_t, sizeof(float) * N * B));
+    VDW_CUDA(cudaMalloc(&c->d_k, N * B));
+    VDW_CUDA(cudaMalloc(&c->d_aux, sizeof(float4) * N * B));
+    VDW_CUDA(cudaMalloc(&c->d_gg, sizeof(float) * N * B));
+    VDW_CUDA(cudaMalloc(&c->d_epart, sizeof(double) * ep_n * B));
+    g.bs_spec = (long long)spec_n;
+    g.bs_wspec = (long long)wspec_n;
+    g.bs_Q = (long long)q_n;
+    g.bs_epart = (int)ep_n;
+    c->batch_max = Bmax;
+    c->bytes += B * (8 * (spec_n + wspec_n) + 16 * q_n + 25 * N + 8 * ep_n);
+    return VDW_OK;
 }
 
 }  // namespace vdw
@@ -151,6 +213,7 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     }
     cudaSetDevice(c->device);
     free_plan(c);
+    c->bytes = 0;  // recounted below (tables included)
     GridArgs& g = c->g;
     g.N1 = n1;
     g.N2 = n2;
@@ -197,32 +260,28 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
         c->nb_p0 = (int)((nb + c->p0_chunks - 1) / c->p0_chunks);
         c->nb_point = c->nb_p0 * c->p0_chunks;
     }
-    c->nb_pencil = (g.ncols + c->pencil_cols - 1) / c->pencil_cols;
-    VDW_CUDA(cudaMalloc(&c->d_tw, sizeof(float2) * (n1 + n2 + n3)));
-    VDW_CUDA(cudaMalloc(&c->d_spec, sizeof(float2) * spec_n));
-    VDW_CUDA(cudaMalloc(&c->d_wspec, sizeof(float2) * 3 * (size_t)n2 * g.ncols));
-    VDW_CUDA(cudaMalloc(&c->d_t, sizeof(float) * g.N));
-    VDW_CUDA(cudaMalloc(&c->d_k, g.N));
-    VDW_CUDA(cudaMalloc(&c->d_aux, sizeof(float4) * (size_t)g.N));
-    VDW_CUDA(cudaMalloc(&c->d_epart, sizeof(double) * (c->nb_point + c->nb_pencil)));
+    VDW_CUDA(cudaMalloc(&c->d_tw, sizeof(float4) * (n1 + n2 + n3)));
+    rc = sorted_plan(c);
+    if (rc) return rc;
+    rc = alloc_density_work(c, 1);
+    if (rc) return rc;
     VDW_CUDA(cudaMalloc(&c->d_invalid, sizeof(unsigned long long)));
-    VDW_CUDA(cudaMalloc(&c->d_gg, sizeof(float) * (size_t)g.N));
-    VDW_CUDA(cudaMalloc(&c->d_flags, sizeof(int)));
+    VDW_CUDA(cudaHostAlloc(&c->h_flags, 2 * sizeof(int), cudaHostAllocMapped));
+    c->h_flags[0] = c->h_flags[1] = 0;
+    VDW_CUDA(cudaHostGetDevicePointer((void**)&c->d_flags, c->h_flags, 0));
+    c->wait_seen = 0;
     VDW_CUDA(cudaMalloc(&c->d_xc, sizeof(double) * (4 + 2 * 1024)));
     VDW_CUDA(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
     VDW_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     for (int i = 0; i < 4; ++i) VDW_CUDA(cudaEventCreateWithFlags(&c->ev_slab[i], cudaEventDisableTiming));
-    VDW_CUDA(cudaMemset(c->d_flags, 0, sizeof(int)));
     VDW_CUDA(cudaMemset(c->d_invalid, 0, sizeof(unsigned long long)));
     rc = pipeline_make_twiddles(c);
     if (rc) return rc;
     rc = pipeline_configure(c);
     if (rc) return rc;
     const int npairs = Nq * (Nq + 1) / 2;
-    c->bytes = sizeof(float4) * (size_t)(c->p.Nk - 1) * npairs + sizeof(float2) * (n1 + n2 + n3) +
-               sizeof(float2) * (spec_n + 3 * (size_t)n2 * g.ncols) + 21 * (size_t)g.N +
-               sizeof(double) * (c->nb_point + c->nb_pencil) +
-               4 * (size_t)g.N + sizeof(int);
+    (void)spec_n;
+    c->bytes += sizeof(float4) * (size_t)(c->p.Nk - 1) * npairs + sizeof(float4) * (n1 + n2 + n3);
     c->planned = 1;
     return VDW_OK;
 }
@@ -231,6 +290,7 @@ int vdw_energy_potential(vdw_handle c, const float* n, const float* grad, double
                          void* stream) {
     if (!c || !n) return VDW_ERR_ARG;
     if (!c->planned) return VDW_ERR_STATE;
+    if (const int rw = check_wait(c)) return rw;
     if (!grad) {
         // grad n = D n with the library's spectral derivative
         if (!c->d_gtmp) VDW_CUDA(cudaMalloc(&c->d_gtmp, sizeof(float) * 3 * (size_t)c->g.N));
@@ -241,9 +301,35 @@ int vdw_energy_potential(vdw_handle c, const float* n, const float* grad, double
     return pipeline_run(c, n, grad, E, v, w, (cudaStream_t)stream);
 }
 
+int vdw_plan_batch(vdw_handle c, int Bmax) {
+    if (!c || Bmax < 1) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    cudaSetDevice(c->device);
+    VDW_CUDA(cudaDeviceSynchronize());  // no call of the context may still use the old workspaces
+    const int rc = alloc_density_work(c, Bmax);
+    if (rc) {
+        c->planned = 0;  // the workspaces are gone; the caller has to plan again
+        return rc;
+    }
+    return VDW_OK;
+}
+
+int vdw_energy_potential_batched(vdw_handle c, int B, const float* n, const float* grad, double* E, float* v,
+                                 void* stream) {
+    if (!c || !n || !grad || !E || B < 1) return VDW_ERR_ARG;
+    if (!c->planned) return VDW_ERR_STATE;
+    if (B > c->batch_max) {
+        set_error("batch larger than the workspaces of vdw_plan_batch");
+        return VDW_ERR_SIZE;
+    }
+    if (const int rw = check_wait(c)) return rw;
+    return pipeline_run(c, n, grad, E, v, nullptr, (cudaStream_t)stream, 0, 0, nullptr, B);
+}
+
 int vdw_energy_potential_fd(vdw_handle c, const float* n, const float* grad, double* E, float* v, void* stream) {
     if (!c || !n) return VDW_ERR_ARG;
     if (!c->planned) return VDW_ERR_STATE;
+    if (const int rw = check_wait(c)) return rw;
     if (!grad) {
         if (!c->d_gtmp) VDW_CUDA(cudaMalloc(&c->d_gtmp, sizeof(float) * 3 * (size_t)c->g.N));
         const int rc = pipeline_stencil_gradient(c, n, c->d_gtmp, (cudaStream_t)stream);
@@ -258,6 +344,7 @@ int vdw_xc_energy_potential(vdw_handle c, const float* n, const float* grad, dou
     if (!c || !n || !E) return VDW_ERR_ARG;
     if (!c->planned) return VDW_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
+    if (const int rw = check_wait(c)) return rw;
     if (!grad) {
         if (!c->d_gtmp) VDW_CUDA(cudaMalloc(&c->d_gtmp, sizeof(float) * 3 * (size_t)c->g.N));
         const int rc = fd ? pipeline_stencil_gradient(c, n, c->d_gtmp, s) : vdw_spectral_gradient(c, n, c->d_gtmp, stream);
@@ -272,6 +359,7 @@ int vdw_xc_energy_potential(vdw_handle c, const float* n, const float* grad, dou
 int vdw_energy_potential_host(vdw_handle c, const float* n, const float* grad, double* E, float* v, void* stream) {
     if (!c || !n || !grad) return VDW_ERR_ARG;
     if (!c->planned) return VDW_ERR_STATE;
+    if (const int rw = check_wait(c)) return rw;
     cudaStream_t s = (cudaStream_t)stream;
     const long long N = c->g.N;
     if (!c->d_in) {
@@ -341,10 +429,9 @@ int vdw_profile_read(vdw_handle c, float* ms) {
 int vdw_wait_status(vdw_handle c, int* gave_up) {
     if (!c || !gave_up) return VDW_ERR_ARG;
     if (!c->planned) return VDW_ERR_STATE;
-    int f = 0, l = 0;
-    VDW_CUDA(cudaMemcpy(&f, c->d_flags, sizeof(int), cudaMemcpyDeviceToHost));
-    if (c->lrn_loaded) VDW_CUDA(cudaMemcpy(&l, c->la.err, sizeof(int), cudaMemcpyDeviceToHost));
-    *gave_up = (f || l) ? 1 : 0;
+    VDW_CUDA(cudaDeviceSynchronize());
+    volatile int* f = c->h_flags;
+    *gave_up = (f[0] || f[1] || c->wait_seen) ? 1 : 0;
     return VDW_OK;
 }
 
@@ -374,6 +461,7 @@ const char* vdw_error_string(int code) {
         case VDW_ERR_OOM: return "device out of memory";
         case VDW_ERR_STATE: return "context not planned";
         case VDW_ERR_UNSUPPORTED: return "unsupported parameter";
+        case VDW_ERR_TIMEOUT: return "a bounded wait in a kernel gave up";
         default: return "unknown error";
     }
 }

@@ -10,6 +10,23 @@
 
 namespace vdw {
 
+// Stages of one call, for vdw_profile_read (include/vdwnl.h lists them).
+enum Stage {
+    ST_POINTWISE = 0,
+    ST_PLANES_FWD,
+    ST_PENCILS_FWD,
+    ST_CONTRACT,
+    ST_ENERGY,
+    ST_PENCILS_INV,
+    ST_PLANES_INV,
+    ST_USUM,
+    ST_W_PLANES,
+    ST_PENCIL_DIV,
+    ST_DIV_FINAL,
+    ST_COUNT
+};
+static_assert(ST_COUNT == VDW_NSTAGES, "stage list");
+
 constexpr int MAX_NQ = 32;     // largest interpolation mesh the kernels take
 constexpr int MAX_DIM = 256;   // largest grid dimension (FFT line length)
 constexpr uint8_t K_INVALID = 255;  // interval code of a point with theta = 0
@@ -48,6 +65,13 @@ struct GridArgs {
     // when N max(N1, N2, N3) reaches 2^32 or a divisor is 1.
     unsigned m1, m2, mh3;
     int fast;
+    // batches (vdw_energy_potential_batched): density b of a batch uses the
+    // workspaces at these element offsets times b; the kernels take b from
+    // their last grid dimension (0 for a single density)
+    long long bs_spec;   // float2 values between two densities' spectrum buffers
+    long long bs_wspec;  // float2 values between two w-spectrum buffers
+    long long bs_Q;      // float4 values between two record buffers (contract.cu)
+    int bs_epart;        // energy partial sums per density
 };
 
 // Learned reduced basis: sizes fixed at compile time.
@@ -99,14 +123,21 @@ struct vdw_ctx {
     int planned;
     vdw::GridArgs g;
     double L[3];
-    float2* d_tw;               // twiddles: N1, N2, N3 entries
+    float4* d_tw;               // twiddles (hi/lo pairs): N1, N2, N3 entries
     float2* d_spec;             // [Nq][N2][N3][Nh] theta(G), then u(G), then real u (N3 x N1 per plane), in place
     float2* d_wspec;            // [3][N2][N3][Nh] w(G); component 0 then D.w
     float* d_t;                 // [N] position of q inside its mesh interval
     uint8_t* d_k;               // [N] mesh interval of q (K_INVALID: theta = 0)
     float4* d_aux;              // [N] n dq/dn, n dq/d|grad n| / |grad n|, and the Delta E derivatives
     double* d_epart;            // per-block energy partial sums
-    int nb_point, nb_pencil;    // their counts (pointwise, pencil kernels)
+    int nb_point;               // their count for the pointwise kernel
+    // points of the half spectrum in |G| order (contract.cu)
+    long long nG, Npad;         // N2 N3 (N1/2 + 1), rounded up to whole contraction blocks
+    int nb_sorted;              // contraction blocks (and energy partials)
+    unsigned* d_pos;            // [N3 Nh][N2] sorted position of point (col, y)
+    float* d_gs;                // [Npad] |G| of each sorted point, sign = energy weight
+    float4* d_Q;                // [Nq/4][Npad][2] field quads of the sorted points
+    int batch_max;              // densities the per-density workspaces hold (vdw_plan_batch)
     // the pointwise pass runs in p0_chunks slabs of p0_nj complex rows (2 p0_nj
     // z values) with nb_p0 blocks each, so that the host entry point can copy
     // slab c + 1 while slab c is processed (nb_point = p0_chunks * nb_p0)
@@ -116,10 +147,14 @@ struct vdw_ctx {
     cudaEvent_t ev_in;          // orders the copy stream after the caller's stream
     cudaEvent_t ev_slab[4];     // slab c of the inputs is on the device
     unsigned long long* d_invalid;  // count of negative / non-finite densities
-    int pencil_cols;            // columns per pencil block
     int bulk_planes;            // inverse plane transforms load their planes by bulk copies
     float* d_gg;                // [N] g of w = g grad n (assembly -> w plane transforms)
-    int* d_flags;               // [1] set when a bounded wait in a kernel gave up
+    // give-up flags of the bounded waits, in mapped page-locked host memory so
+    // that an entry point can read them without synchronising: [0] the bulk
+    // copies of the plane kernels, [1] the tensor-core waits of the learned path
+    int* h_flags;               // host view
+    int* d_flags;               // device view of the same two words
+    int wait_seen;              // a give-up was reported since vdw_plan
     double* d_xc;               // [4 + 2 XC_BLOCKS] nonlocal E and semilocal partial sums
     // buffers of the host-pointer entry point (allocated on first use)
     float* d_in;                // [4N]
@@ -146,6 +181,11 @@ namespace vdw {
 
 void set_error(const std::string& s);
 int cuda_fail(cudaError_t e, const char* what);
+// VDW_ERR_TIMEOUT (and clears the flags) if a kernel of an earlier call gave up
+// a bounded wait since the last check, else VDW_OK
+int check_wait(vdw_ctx* c);
+// per-density workspaces for Bmax densities (api.cu)
+int alloc_density_work(vdw_ctx* c, int Bmax);
 
 #define VDW_CUDA(call)                                         \
     do {                                                       \
@@ -156,8 +196,10 @@ int cuda_fail(cudaError_t e, const char* what);
 // pipeline launchers (pipeline.cu)
 // slab_ready (optional): per slab of the pointwise pass, an event to wait on
 // before processing it (the host entry point's copies)
+// B > 1: a batch of B densities (n [B][N], grad [B][3][N], E [B][3], v [B][N],
+// w [B][3][N]), one launch per stage; needs the batch workspaces of vdw_plan_batch
 int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w,
-                 cudaStream_t s, int fd = 0, int xc = 0, const cudaEvent_t* slab_ready = nullptr);
+                 cudaStream_t s, int fd = 0, int xc = 0, const cudaEvent_t* slab_ready = nullptr, int B = 1);
 // E[4] of the functional from the nonlocal energy (d_xc[0]) and the semilocal sums
 int pipeline_xc_final(vdw_ctx* c, double* E, cudaStream_t s);
 // central-difference gradient of a field (into grad [3][N])
@@ -175,6 +217,20 @@ int pipeline_planes_inplace(vdw_ctx* c, int nfields, bool inverse, cudaStream_t 
 // forward plane transforms of w = g grad n with g in d_gg (into d_wspec)
 int pipeline_w_planes(vdw_ctx* c, const float* grad, cudaStream_t s);
 int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, double* E, cudaStream_t s);
+
+// y transforms and contraction in |G| order (contract.cu)
+size_t sorted_pencil_smem(const GridArgs& g);
+int sorted_plan(vdw_ctx* c);
+void sorted_free(vdw_ctx* c);
+int sorted_configure(vdw_ctx* c);
+int sorted_forward(vdw_ctx* c, int nfields, cudaStream_t s, int B = 1);
+int sorted_inverse(vdw_ctx* c, int nfields, cudaStream_t s, int B = 1);
+int sorted_contract(vdw_ctx* c, double* epart, int write_back, cudaStream_t s, int B = 1);
+// the same contraction of the first nq fields with another table of the same
+// layout ([nk-1][nq(nq+1)/2] float4 cubic coefficients on a uniform mesh)
+int sorted_contract_table(vdw_ctx* c, int nq, const float4* table, float inv_dk, int nk, double* epart,
+                          int write_back, cudaStream_t s, int B = 1);
+constexpr int SORTED_BLOCK = 256;  // sorted points per contraction block
 
 // learned reduced basis (learned.cu)
 int learned_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s);

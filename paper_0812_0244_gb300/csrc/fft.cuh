@@ -13,6 +13,16 @@
 //     V   = DFT_R(v)
 //     y[(j - k) R + k + r Ns] = V_r
 // Forward uses W_n, inverse its conjugate; neither scales.
+//
+// Every constant of a transform (table twiddles, the sines and cosines inside
+// the radix 3, 5, 8, 9 and 16 butterflies) is held as a pair hi + lo of FP32
+// numbers whose sum is the FP64 value, and a product x W is formed as
+// x W_hi + x W_lo.  With the constants rounded to FP32 alone, the rounding
+// errors of the few twiddles a smooth field's low frequencies go through add
+// up coherently: the transform's low-frequency amplitudes come out biased by
+// a few 1e-8, which shifts the energy of Eq. (Eoffk) (dominated by those
+// frequencies) by ~1e-7 of itself.  With the pair the constants are exact to
+// ~1e-15 and only the (unbiased) rounding of the arithmetic remains.
 #pragma once
 
 #include "common.cuh"
@@ -35,6 +45,45 @@ __device__ __forceinline__ float2 mul_mi(float2 a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
+// A twiddle W as {W_hi.x, W_hi.y, W_lo.x, W_lo.y}, W = W_hi + W_lo.
+using Tw = float4;
+// a W (the small product a W_lo first, then the main one accumulated on it)
+__device__ __forceinline__ float2 cmul_tw(float2 a, Tw w) {
+    const float lr = fmaf(a.x, w.z, -a.y * w.w);
+    const float li = fmaf(a.x, w.w, a.y * w.z);
+    return make_float2(fmaf(a.x, w.x, fmaf(-a.y, w.y, lr)), fmaf(a.x, w.y, fmaf(a.y, w.x, li)));
+}
+// a conj(W)
+__device__ __forceinline__ float2 cmulc_tw(float2 a, Tw w) {
+    const float lr = fmaf(a.x, w.z, a.y * w.w);
+    const float li = fmaf(a.y, w.z, -a.x * w.w);
+    return make_float2(fmaf(a.x, w.x, fmaf(a.y, w.y, lr)), fmaf(a.y, w.x, fmaf(-a.x, w.y, li)));
+}
+template <bool INV>
+__device__ __forceinline__ float2 tw_mul(float2 a, Tw w) {
+    return INV ? cmulc_tw(a, w) : cmul_tw(a, w);
+}
+// A twiddle held as its FP32 value only (transforms whose results tolerate
+// the constant rounding: the inverse transforms and those of w).
+template <bool INV>
+__device__ __forceinline__ float2 tw_mul(float2 a, float2 w) {
+    return INV ? cmulc(a, w) : cmul(a, w);
+}
+// store a hi/lo twiddle as a table entry of either kind
+__device__ __forceinline__ void tw_put(Tw* d, Tw s) { *d = s; }
+__device__ __forceinline__ void tw_put(float2* d, Tw s) { *d = make_float2(s.x, s.y); }
+// Real constant c = hi + lo from its FP64 value.
+struct KPair {
+    float h, l;
+};
+__host__ __device__ constexpr KPair kpair(double c) { return KPair{(float)c, (float)(c - (double)(float)c)}; }
+// x c
+__device__ __forceinline__ float kmul(float x, KPair c) { return fmaf(x, c.h, x * c.l); }
+// x c + y d (one rounding of the main products' sum)
+__device__ __forceinline__ float kmul2(float x, KPair c, float y, KPair d) {
+    return fmaf(x, c.h, fmaf(y, d.h, fmaf(x, c.l, y * d.l)));
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* v);
 
@@ -48,12 +97,13 @@ __device__ __forceinline__ void dft<2, true>(float2* v) { dft<2, false>(v); }
 
 template <bool INV>
 __device__ __forceinline__ void dft3(float2* v) {
-    const float s3 = 0.86602540378443864676f;  // sin(2 pi/3)
+    constexpr KPair s3 = kpair(0.86602540378443864676);  // sin(2 pi/3)
     float2 s = cadd(v[1], v[2]);
     float2 d = csub(v[1], v[2]);
     float2 x0 = cadd(v[0], s);
     float2 t = make_float2(fmaf(-0.5f, s.x, v[0].x), fmaf(-0.5f, s.y, v[0].y));
-    float2 u = cscale(mul_mi<INV>(d), s3);
+    const float2 dm = mul_mi<INV>(d);
+    float2 u = make_float2(kmul(dm.x, s3), kmul(dm.y, s3));
     v[0] = x0;
     v[1] = cadd(t, u);
     v[2] = csub(t, u);
@@ -79,17 +129,18 @@ __device__ __forceinline__ void dft<4, true>(float2* v) { dft4<true>(v); }
 
 template <bool INV>
 __device__ __forceinline__ void dft5(float2* v) {
-    const float c1 = 0.30901699437494742410f;   // cos(2 pi/5)
-    const float c2 = -0.80901699437494742410f;  // cos(4 pi/5)
-    const float s1 = 0.95105651629515357212f;   // sin(2 pi/5)
-    const float s2 = 0.58778525229247312917f;   // sin(4 pi/5)
+    constexpr KPair c1 = kpair(0.30901699437494742410);   // cos(2 pi/5)
+    constexpr KPair c2 = kpair(-0.80901699437494742410);  // cos(4 pi/5)
+    constexpr KPair s1 = kpair(0.95105651629515357212);   // sin(2 pi/5)
+    constexpr KPair s2 = kpair(0.58778525229247312917);   // sin(4 pi/5)
+    constexpr KPair ms1 = kpair(-0.95105651629515357212);
     float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
     float2 a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
     float2 x0 = cadd(v[0], cadd(a1, a2));
-    float2 t1 = make_float2(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
-    float2 t2 = make_float2(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
-    float2 u1 = mul_mi<INV>(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
-    float2 u2 = mul_mi<INV>(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+    float2 t1 = make_float2(v[0].x + kmul2(a1.x, c1, a2.x, c2), v[0].y + kmul2(a1.y, c1, a2.y, c2));
+    float2 t2 = make_float2(v[0].x + kmul2(a1.x, c2, a2.x, c1), v[0].y + kmul2(a1.y, c2, a2.y, c1));
+    float2 u1 = mul_mi<INV>(make_float2(kmul2(b1.x, s1, b2.x, s2), kmul2(b1.y, s1, b2.y, s2)));
+    float2 u2 = mul_mi<INV>(make_float2(kmul2(b1.x, s2, b2.x, ms1), kmul2(b1.y, s2, b2.y, ms1)));
     v[0] = x0;
     v[1] = cadd(t1, u1);
     v[4] = csub(t1, u1);
@@ -110,8 +161,8 @@ __device__ __forceinline__ int mod_magic(int j, int Ns, unsigned M) {
     return Ns > 1 ? j - (int)__umulhi((unsigned)j, M) * Ns : 0;
 }
 
-template <int R, bool INV>
-__device__ __forceinline__ void line_pass(float2* p, int es, int n, int Ns, const float2* tw, int lane) {
+template <int R, bool INV, class W>
+__device__ __forceinline__ void line_pass(float2* p, int es, int n, int Ns, const W* tw, int lane) {
     constexpr int MAXB = (MAX_DIM / R + 31) / 32;
     const int m = n / R;
     const int tstride = n / (Ns * R);
@@ -127,8 +178,8 @@ __device__ __forceinline__ void line_pass(float2* p, int es, int n, int Ns, cons
             for (int r = 0; r < R; ++r) v[b][r] = p[(j + r * m) * es];
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const float2 w = tw[r * k * tstride];  // r k n/(Ns R) < n
-                v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+                const W w = tw[r * k * tstride];  // r k n/(Ns R) < n
+                v[b][r] = tw_mul<INV>(v[b][r], w);
             }
             dft<R, INV>(v[b]);
         }
@@ -148,10 +199,10 @@ __device__ __forceinline__ void line_pass(float2* p, int es, int n, int Ns, cons
     __syncwarp();
 }
 
-// Full line transform: tw holds W_n^e = exp(-2 pi i e/n), e in [0, n).  One
+// Full line transform: tw holds W_n^e = exp(-2 pi i e/n), e in [0, n), as hi/lo pairs.  One
 // loop per radix keeps each pass's registers separate.
-template <bool INV>
-__device__ __forceinline__ void line_fft(float2* p, int es, const LinePlan& pl, const float2* tw, int lane) {
+template <bool INV, class W>
+__device__ __forceinline__ void line_fft(float2* p, int es, const LinePlan& pl, const W* tw, int lane) {
     int Ns = 1;
 #pragma unroll 1
     for (int s = 0; s < pl.c4; ++s) { line_pass<4, INV>(p, es, pl.n, Ns, tw, lane); Ns *= 4; }
@@ -238,7 +289,7 @@ namespace vdw {
 
 template <bool INV>
 __device__ __forceinline__ void dft8(float2* v) {
-    const float r2 = 0.70710678118654752440f;
+    constexpr KPair r2 = kpair(0.70710678118654752440);
     // two radix-4 transforms of the even and odd samples
     float2 e[4] = {v[0], v[2], v[4], v[6]};
     float2 o[4] = {v[1], v[3], v[5], v[7]};
@@ -246,9 +297,9 @@ __device__ __forceinline__ void dft8(float2* v) {
     dft4<INV>(o);
     // odd twiddles W8^k, k = 1..3 (conjugate for the inverse)
     const float s = INV ? 1.f : -1.f;
-    const float2 o1 = make_float2(r2 * (o[1].x - s * o[1].y), r2 * (o[1].y + s * o[1].x));
+    const float2 o1 = make_float2(kmul(o[1].x - s * o[1].y, r2), kmul(o[1].y + s * o[1].x, r2));
     const float2 o2 = make_float2(-s * o[2].y, s * o[2].x);
-    const float2 o3 = make_float2(r2 * (-o[3].x - s * o[3].y), r2 * (-o[3].y + s * o[3].x));
+    const float2 o3 = make_float2(kmul(-o[3].x - s * o[3].y, r2), kmul(-o[3].y + s * o[3].x, r2));
     v[0] = cadd(e[0], o[0]);
     v[4] = csub(e[0], o[0]);
     v[1] = cadd(e[1], o1);
@@ -267,22 +318,23 @@ __device__ __forceinline__ void dft<8, true>(float2* v) { dft8<true>(v); }
 // W_N^e = exp(-2 pi i e / N) (conjugated for the inverse) for the few
 // exponents the Cooley-Tukey splits 3x3 and 4x4 need.
 template <int N, int E>
-__device__ __forceinline__ float2 wconst() {
+__device__ __forceinline__ Tw wconst() {
     static_assert(N == 9 || N == 16, "no constants for this length");
-    float c = 1.f, s = 0.f;  // cos, sin of 2 pi E / N
+    double c = 1.0, s = 0.0;  // cos, sin of 2 pi E / N
     if (N == 9) {
-        if (E == 1) { c = 0.766044443118978035202f; s = 0.642787609686539326323f; }
-        if (E == 2) { c = 0.173648177666930348852f; s = 0.984807753012208059367f; }
-        if (E == 4) { c = -0.939692620785908384054f; s = 0.342020143325668733044f; }
+        if (E == 1) { c = 0.766044443118978035202; s = 0.642787609686539326323; }
+        if (E == 2) { c = 0.173648177666930348852; s = 0.984807753012208059367; }
+        if (E == 4) { c = -0.939692620785908384054; s = 0.342020143325668733044; }
     } else {
-        if (E == 1) { c = 0.923879532511286756128f; s = 0.382683432365089771728f; }
-        if (E == 2) { c = 0.707106781186547524401f; s = 0.707106781186547524401f; }
-        if (E == 3) { c = 0.382683432365089771728f; s = 0.923879532511286756128f; }
-        if (E == 4) { c = 0.f; s = 1.f; }
-        if (E == 6) { c = -0.707106781186547524401f; s = 0.707106781186547524401f; }
-        if (E == 9) { c = -0.923879532511286756128f; s = -0.382683432365089771728f; }
+        if (E == 1) { c = 0.923879532511286756128; s = 0.382683432365089771728; }
+        if (E == 2) { c = 0.707106781186547524401; s = 0.707106781186547524401; }
+        if (E == 3) { c = 0.382683432365089771728; s = 0.923879532511286756128; }
+        if (E == 4) { c = 0.0; s = 1.0; }
+        if (E == 6) { c = -0.707106781186547524401; s = 0.707106781186547524401; }
+        if (E == 9) { c = -0.923879532511286756128; s = -0.382683432365089771728; }
     }
-    return make_float2(c, -s);
+    const KPair cr = kpair(c), ci = kpair(-s);
+    return make_float4(cr.h, ci.h, cr.l, ci.l);
 }
 
 // Cooley-Tukey in registers, N = R1 R2, input index R2 n1 + n2, output
@@ -293,8 +345,8 @@ __device__ __forceinline__ void ct_twiddle(float2 (&Y)[R1 * R2]) {
     if constexpr (N2 < R2) {
         if constexpr (K1 < R1) {
             if constexpr (N2 > 0) {
-                const float2 w = wconst<R1 * R2, N2 * K1>();
-                Y[N2 * R1 + K1] = INV ? cmulc(Y[N2 * R1 + K1], w) : cmul(Y[N2 * R1 + K1], w);
+                const Tw w = wconst<R1 * R2, N2 * K1>();
+                Y[N2 * R1 + K1] = tw_mul<INV>(Y[N2 * R1 + K1], w);
             }
             ct_twiddle<R1, R2, INV, N2, K1 + 1>(Y);
         } else {
@@ -433,15 +485,15 @@ constexpr int ct_tw_off(int n, int s, int maxr = 16) {
                         (ct_ns_at(n, s - 1, maxr) > 1 ? (ct_radix_at(n, s - 1, maxr) - 1) * ct_ns_at(n, s - 1, maxr) : 0);
 }
 // Fills the table from the plain one (src[e] = W_N^e), all threads of the block.
-template <int N, int MAXR = 16, int S = 0>
-__device__ __forceinline__ void ct_load_twiddles(float2* dst, const float2* src) {
+template <int N, int MAXR = 16, int S = 0, class W>
+__device__ __forceinline__ void ct_load_twiddles(W* dst, const Tw* src) {
     if constexpr (S < ct_npasses(N, MAXR)) {
         constexpr int R = ct_radix_at(N, S, MAXR), Ns = ct_ns_at(N, S, MAXR);
         if constexpr (Ns > 1) {
             constexpr int TS = N / (Ns * R), off = ct_tw_off(N, S, MAXR);
             for (int i = threadIdx.x; i < (R - 1) * Ns; i += blockDim.x) {
                 const int r = 1 + i / Ns, k = i - (r - 1) * Ns;
-                dst[off + i] = src[r * k * TS];
+                tw_put(dst + off + i, src[r * k * TS]);
             }
         }
         ct_load_twiddles<N, MAXR, S + 1>(dst, src);
@@ -454,8 +506,8 @@ __device__ __forceinline__ void ct_load_twiddles(float2* dst, const float2* src)
 // whatever their distance, and consecutive butterflies of one line hit
 // distinct banks.  The first pass (Ns = 1) has no twiddles; the others read
 // the pass-ordered table of ct_load_twiddles.
-template <int N, int S, int L, bool INV, int MAXR>
-__device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const float2* tw, int lane) {
+template <int N, int S, int L, bool INV, int MAXR, class W>
+__device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const W* tw, int lane) {
     constexpr int R = ct_radix_at(N, S, MAXR);
     constexpr int Ns = ct_ns_at(N, S, MAXR);
     constexpr int M = N / R;
@@ -491,8 +543,8 @@ __device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const float2*
                 constexpr int off = ct_tw_off(N, S, MAXR);
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    const float2 w = tw[off + (r - 1) * Ns + k];
-                    v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+                    const W w = tw[off + (r - 1) * Ns + k];
+                    v[b][r] = tw_mul<INV>(v[b][r], w);
                 }
             }
             dft<R, INV>(v[b]);
@@ -531,8 +583,8 @@ __device__ __forceinline__ void ct_pass(float2* p, int es, int ls, const float2*
     __syncwarp();
 }
 
-template <int N, int L, bool INV, int MAXR = 16, int S = 0>
-__device__ __forceinline__ void ct_fft(float2* p, int es, int ls, const float2* tw, int lane) {
+template <int N, int L, bool INV, int MAXR = 16, int S = 0, class W>
+__device__ __forceinline__ void ct_fft(float2* p, int es, int ls, const W* tw, int lane) {
     if constexpr (S < ct_npasses(N, MAXR)) {
         ct_pass<N, S, L, INV, MAXR>(p, es, ls, tw, lane);
         ct_fft<N, L, INV, MAXR, S + 1>(p, es, ls, tw, lane);

@@ -10,9 +10,11 @@
 //                          theta_m to the packed real rows of the spectrum
 //                          buffer, Delta E partial sums; then the forward plane
 //                          transforms in place (k_planes_inplace)
-//   L2 k_learned_contract  y pencils of the 8 channels, u_m(G) = sum_n
-//                          K_mn(|G|) theta_n(G), FP64 energy, inverse y; in
-//                          training also dE/dK at the knots
+//   L2 y transforms into |G| order, u_m(G) = sum_n K_mn(|G|) theta_n(G) and
+//                          the FP64 energy over the sorted points (the plain
+//                          method's kernels of contract.cu with the knot
+//                          table), inverse y transforms; in training
+//                          k_learned_contract_gradk, which also gives dE/dK
 //   L3 inverse plane transforms in place (k_planes_inplace), then
 //      k_learned_usum      per point: v_loc and g of w = g grad n (Eq. Vi)
 //                          from u, the stored weights and Jacobian;
@@ -222,11 +224,16 @@ __device__ __forceinline__ void wg_mma_issue(MlpCtl* ctl, int wg, int r, const u
 // Wait for the warpgroup's last commit and agree across the warpgroup on success.
 __device__ __forceinline__ bool wg_mma_wait(MlpCtl* ctl, int wg, uint32_t& phase, int* err) {
     const bool ok = tc::mbar_wait(&ctl->bar[wg], phase);
-    phase ^= 1u;
     if (!ok) {
         atomicExch(&ctl->abort[wg], 1);
-        atomicExch(err, 1);
+        *(volatile int*)err = 1;  // page-locked host word, read by the next entry point
+        __threadfence_system();
+        // the committed MMAs may still be writing this warpgroup's tensor
+        // memory: give them a second bounded wait before the warpgroup stops
+        // and the block frees that memory
+        tc::mbar_wait(&ctl->bar[wg], phase);
     }
+    phase ^= 1u;
     wg_bar(wg);
     tc::fence_after_sync();
     return ctl->abort[wg] == 0;
@@ -520,137 +527,116 @@ __global__ void __launch_bounds__(L_NET_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// L2: pencils, learned kernel, energy (and dE/dK at the knots)
+// L2 (training form): contraction over the points in |G| order with dE/dK
 // ---------------------------------------------------------------------------
-template <int CN2, bool GRADK>
-__global__ void __launch_bounds__(256) k_learned_contract(float2* __restrict__ spec, GridArgs g, LearnedArgs la,
-                                                          const float2* __restrict__ tw, double* __restrict__ epart,
-                                                          int C, int write_back, double* __restrict__ gK,
-                                                          float halfOmega) {
+// The energy and potential forms use the plain method's sorted contraction
+// (contract.cu) with the knot table.  This form also accumulates
+//   dE/dK_p(k_i) = sum_G 1/2 Omega w_G (2 - delta_ab) Re(conj th_a th_b) c_i(|G|)
+// for the four Catmull-Rom weights c_i of the knots around |G| (Eq. Eoffk
+// differentiated through the interpolation), in shared-memory bins [P][J].
+// In |G| order the 32 points of a warp nearly always share their interval:
+// the warp then sums its contributions first and one lane adds them.
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(SORTED_BLOCK) k_learned_contract_gradk(float4* __restrict__ Q, long long qstride,
+                                                                       const float* __restrict__ gs, LearnedArgs la,
+                                                                       float invN, double* __restrict__ epart,
+                                                                       double* __restrict__ gK, float halfOmega) {
     constexpr int NQ = LRN_M;
-    extern __shared__ float2 sm[];
+    extern __shared__ float bins[];  // [P][J]
     __shared__ double red[32];
-    const int N2 = CN2 > 0 ? CN2 : g.N2;
-    float2* lines = sm;  // [NQ][C][N2]
-    float2* tw2 = lines + NQ * C * N2;
-    float* bins = reinterpret_cast<float*>(tw2 + N2);  // [P][J] (GRADK)
-    load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
-    if (GRADK)
-        for (int i = threadIdx.x; i < LRN_P * la.J; i += blockDim.x) bins[i] = 0.f;
-    const int c0 = blockIdx.x * C;
-    const SmallDiv sC = small_div(C);  // i / C in the staging loops
-    const int tot = NQ * N2 * C;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int rr = sdiv(i, sC), cc = i - rr * C, yy = rr % N2, a = rr / N2;
-        const int col = c0 + cc;
-        float2 val = make_float2(0.f, 0.f);
-        if (col < g.ncols) val = spec[((long long)a * N2 + yy) * g.ncols + col];
-        lines[(a * C + cc) * N2 + yy] = val;
+    const int J = la.J;
+    for (int i = threadIdx.x; i < LRN_P * J; i += blockDim.x) bins[i] = 0.f;
+    __syncthreads();
+    const long long r = (long long)blockIdx.x * SORTED_BLOCK + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    float2 th[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ / 4; ++q) {
+        const float4 a = Q[q * qstride + 2 * r], b = Q[q * qstride + 2 * r + 1];
+        th[4 * q] = make_float2(a.x, a.y);
+        th[4 * q + 1] = make_float2(a.z, a.w);
+        th[4 * q + 2] = make_float2(b.x, b.y);
+        th[4 * q + 3] = make_float2(b.z, b.w);
     }
-    __syncthreads();
-    pencils_fft<CN2, false>(lines, NQ * C, N2, g.p2, tw2);
-    __syncthreads();
-    const int npy = N2 / 2 + 1;
-    const int LS = C * N2;
-    double eacc = 0.0;
-    for (int task = threadIdx.x; task < C * npy; task += blockDim.x) {
-        const int cc = task / npy, ya = task - cc * npy;
-        const int col = c0 + cc;
-        if (col >= g.ncols) continue;
-        const int yb0 = N2 - ya;
-        const bool two = (ya != 0) && (yb0 != ya);
-        const int yb = two ? yb0 : ya;
-        const int kx = col % g.Nh, kz = col / g.Nh;
-        const int mz = (2 * kz <= g.N3) ? kz : kz - g.N3;
-        const float G2 = g.gx2 * (float)(kx * kx) + g.gy2 * (float)(ya * ya) + g.gz2 * (float)(mz * mz);
-        const float s = sqrtf(G2) * la.inv_dk;
-        const int j = min((int)s, la.J - 2);
-        const float t = s - (float)j;
-        const float4* cf = la.knots + (long long)j * LRN_P;
-        // Catmull-Rom weights of the knots j-1 .. j+2 (knot-gradient bins)
-        const float wm1 = 0.5f * t * (t * (2.f - t) - 1.f), w0 = 1.f + t * t * (1.5f * t - 2.5f);
-        const float w1 = 0.5f * t * (1.f + t * (4.f - 3.f * t)), w2 = 0.5f * t * t * (t - 1.f);
-        const float2* pa = lines + cc * N2 + ya;
-        const float2* pb = lines + cc * N2 + yb;
-        float2 ua[NQ], ub[NQ];
+    const float gm = gs[r];
+    const float wgt = signbit(gm) ? 1.f : 2.f;
+    const float sk = fabsf(gm) * la.inv_dk;
+    const int j = min((int)sk, J - 2);
+    const float t = sk - (float)j;
+    const float4* cf = la.knots + (long long)j * LRN_P;
+    // Catmull-Rom weights of the knots j-1 .. j+2
+    const float wm1 = 0.5f * t * (t * (2.f - t) - 1.f), w0 = 1.f + t * t * (1.5f * t - 2.5f);
+    const float w1 = 0.5f * t * (1.f + t * (4.f - 3.f * t)), w2 = 0.5f * t * t * (t - 1.f);
+    // knots of the four weights: the knot before k = 0 mirrors knot 1; past the
+    // last knot the linear extrapolation 2 K_{J-1} - K_{J-2}
+    const int km1 = j == 0 ? 1 : j - 1;
+    const bool tail = j + 2 > J - 1;
+    const bool uni = __all_sync(0xffffffffu, j == __shfl_sync(0xffffffffu, j, 0));
+    float2 u[NQ];
 #pragma unroll
-        for (int a = 0; a < NQ; ++a) {
-            ua[a] = make_float2(0.f, 0.f);
-            ub[a] = make_float2(0.f, 0.f);
-        }
-        const bool single = (kx == 0) || (2 * kx == g.N1);
-        const float wgt = single ? 1.f : 2.f;
-        int p = 0;
+    for (int a = 0; a < NQ; ++a) u[a] = make_float2(0.f, 0.f);
+    int p = 0;
 #pragma unroll
-        for (int a = 0; a < NQ; ++a) {
-            const float2 taa = pa[a * LS], tba = pb[a * LS];
+    for (int a = 0; a < NQ; ++a) {
 #pragma unroll
-            for (int b = a; b < NQ; ++b, ++p) {
-                const float4 c = cf[p];
-                const float phi = fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
-                const float2 tab = pa[b * LS], tbb = pb[b * LS];
-                ua[a].x = fmaf(phi, tab.x, ua[a].x);
-                ua[a].y = fmaf(phi, tab.y, ua[a].y);
-                ub[a].x = fmaf(phi, tbb.x, ub[a].x);
-                ub[a].y = fmaf(phi, tbb.y, ub[a].y);
-                if (b != a) {
-                    ua[b].x = fmaf(phi, taa.x, ua[b].x);
-                    ua[b].y = fmaf(phi, taa.y, ua[b].y);
-                    ub[b].x = fmaf(phi, tba.x, ub[b].x);
-                    ub[b].y = fmaf(phi, tba.y, ub[b].y);
-                }
-                if (GRADK) {
-                    // d E / d K_p at the two knots of |G|: 1/2 Omega w_G (2 - delta_ab) Re(conj th_a th_b)
-                    float rr2 = taa.x * tab.x + taa.y * tab.y;
-                    if (two) rr2 += tba.x * tbb.x + tba.y * tbb.y;
-                    const float rv = halfOmega * wgt * (b != a ? 2.f : 1.f) * rr2;
-                    float* bp = bins + p * la.J;
-                    atomicAdd(&bp[j == 0 ? 1 : j - 1], wm1 * rv);
-                    atomicAdd(&bp[j], w0 * rv);
-                    atomicAdd(&bp[j + 1], w1 * rv);
-                    if (j + 2 <= la.J - 1) {
-                        atomicAdd(&bp[j + 2], w2 * rv);
+        for (int b = a; b < NQ; ++b, ++p) {
+            const float4 c = cf[p];
+            const float phi = fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
+            u[a].x = fmaf(phi, th[b].x, u[a].x);
+            u[a].y = fmaf(phi, th[b].y, u[a].y);
+            if (b != a) {
+                u[b].x = fmaf(phi, th[a].x, u[b].x);
+                u[b].y = fmaf(phi, th[a].y, u[b].y);
+            }
+            const float rv = halfOmega * wgt * (b != a ? 2.f : 1.f) * (th[a].x * th[b].x + th[a].y * th[b].y);
+            float* bp = bins + p * J;
+            if (uni) {
+                const float s0 = warp_sum_f(wm1 * rv), s1 = warp_sum_f(w0 * rv);
+                const float s2 = warp_sum_f(w1 * rv), s3 = warp_sum_f(w2 * rv);
+                if (lane == 0) {
+                    atomicAdd(&bp[km1], s0);
+                    atomicAdd(&bp[j], s1);
+                    atomicAdd(&bp[j + 1], s2);
+                    if (!tail) {
+                        atomicAdd(&bp[j + 2], s3);
                     } else {
-                        atomicAdd(&bp[la.J - 1], 2.f * w2 * rv);
-                        atomicAdd(&bp[la.J - 2], -w2 * rv);
+                        atomicAdd(&bp[J - 1], 2.f * s3);
+                        atomicAdd(&bp[J - 2], -s3);
                     }
                 }
-            }
-        }
-        float ea = 0.f, eb = 0.f;
-#pragma unroll
-        for (int a = 0; a < NQ; ++a) {
-            const float2 taa = pa[a * LS], tba = pb[a * LS];
-            ea = fmaf(taa.x, ua[a].x, fmaf(taa.y, ua[a].y, ea));
-            eb = fmaf(tba.x, ub[a].x, fmaf(tba.y, ub[a].y, eb));
-        }
-        eacc += ((double)ea + (two ? (double)eb : 0.0)) * (double)wgt;
-        if (write_back) {
-            float2* wa = lines + cc * N2 + ya;
-            float2* wb = lines + cc * N2 + yb;
-#pragma unroll
-            for (int a = 0; a < NQ; ++a) {
-                wa[a * LS] = cscale(ua[a], g.invN);
-                if (two) wb[a * LS] = cscale(ub[a], g.invN);
+            } else {
+                atomicAdd(&bp[km1], wm1 * rv);
+                atomicAdd(&bp[j], w0 * rv);
+                atomicAdd(&bp[j + 1], w1 * rv);
+                if (!tail) {
+                    atomicAdd(&bp[j + 2], w2 * rv);
+                } else {
+                    atomicAdd(&bp[J - 1], 2.f * w2 * rv);
+                    atomicAdd(&bp[J - 2], -w2 * rv);
+                }
             }
         }
     }
-    const double es = block_sum(eacc, red);
+    float e = 0.f;
+#pragma unroll
+    for (int a = 0; a < NQ; ++a) e = fmaf(th[a].x, u[a].x, fmaf(th[a].y, u[a].y, e));
+    const double es = block_sum((double)(wgt * e), red);
     if (threadIdx.x == 0) epart[blockIdx.x] = es;
-    if (GRADK) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < LRN_P * la.J; i += blockDim.x)
-            if (bins[i] != 0.f) atomicAdd(&gK[i], (double)bins[i]);
+#pragma unroll
+    for (int q = 0; q < NQ / 4; ++q) {
+        Q[q * qstride + 2 * r] =
+            make_float4(u[4 * q].x * invN, u[4 * q].y * invN, u[4 * q + 1].x * invN, u[4 * q + 1].y * invN);
+        Q[q * qstride + 2 * r + 1] =
+            make_float4(u[4 * q + 2].x * invN, u[4 * q + 2].y * invN, u[4 * q + 3].x * invN, u[4 * q + 3].y * invN);
     }
-    if (!write_back) return;
     __syncthreads();
-    pencils_fft<CN2, true>(lines, NQ * C, N2, g.p2, tw2);
-    __syncthreads();
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int rr = sdiv(i, sC), cc = i - rr * C, yy = rr % N2, a = rr / N2;
-        const int col = c0 + cc;
-        if (col < g.ncols) spec[((long long)a * N2 + yy) * g.ncols + col] = lines[(a * C + cc) * N2 + yy];
-    }
+    for (int i = threadIdx.x; i < LRN_P * J; i += blockDim.x)
+        if (bins[i] != 0.f) atomicAdd(&gK[i], (double)bins[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -919,12 +905,12 @@ __global__ void __launch_bounds__(256) k_basis_weights(const float* __restrict__
 // ---------------------------------------------------------------------------
 template <int CN1, int CN3>
 __global__ void __launch_bounds__(PLANE_THREADS, 2) k_field_plane(const float* __restrict__ f, GridArgs g,
-                                                                   const float2* __restrict__ tw,
+                                                                   const Tw* __restrict__ tw,
                                                                    float2* __restrict__ spec) {
     extern __shared__ float2 sm[];
     float2* plane = sm;
-    float2* tw1 = plane + g.N3 * g.Nh;
-    float2* tw3 = tw1 + g.N1;
+    Tw* tw1 = twiddles_after(plane, (size_t)(g.N3 * g.Nh));
+    Tw* tw3 = tw1 + g.N1;
     const int y = blockIdx.x;
     load_line_twiddles<CN1>(tw1, tw, g.N1);
     load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
@@ -943,11 +929,11 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_field_plane(const float* _
 
 template <int CN2>
 __global__ void __launch_bounds__(256, 2) k_pencil_grad(const float2* __restrict__ spec, float2* __restrict__ wspec,
-                                                        GridArgs g, const float2* __restrict__ tw, int C) {
+                                                        GridArgs g, const Tw* __restrict__ tw, int C) {
     extern __shared__ float2 sm[];
     const int N2 = CN2 > 0 ? CN2 : g.N2;
     float2* lines = sm;  // [4][C][N2]: the field, then its three derivatives
-    float2* tw2 = lines + 4 * C * N2;
+    Tw* tw2 = twiddles_after(lines, (size_t)(4 * C * N2));
     load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
     const SmallDiv sC = small_div(C);  // i / C in the staging loops
@@ -984,12 +970,12 @@ __global__ void __launch_bounds__(256, 2) k_pencil_grad(const float2* __restrict
 
 template <int CN1, int CN3>
 __global__ void __launch_bounds__(PLANE_THREADS, 2) k_plane_inv3(const float2* __restrict__ wspec, GridArgs g,
-                                                                  const float2* __restrict__ tw,
+                                                                  const Tw* __restrict__ tw,
                                                                   float* __restrict__ out) {
     extern __shared__ float2 sm[];
     float2* plane = sm;
-    float2* tw1 = plane + g.N3 * g.Nh;
-    float2* tw3 = tw1 + g.N1;
+    Tw* tw1 = twiddles_after(plane, (size_t)(g.N3 * g.Nh));
+    Tw* tw3 = tw1 + g.N1;
     const int y = blockIdx.x, c = blockIdx.y;
     load_line_twiddles<CN1>(tw1, tw, g.N1);
     load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
@@ -1041,21 +1027,19 @@ int net_blocks(vdw_ctx* c) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     return std::max(1, std::min(nsm, c->g.N2 * L_SLOTS));
 }
-int contract_cols(const GridArgs& g) {
-    int C = 8;
-    while (C > 1 && sizeof(float2) * ((size_t)LRN_M * C * g.N2 + g.N2) > 100 * 1024) --C;
-    return C;
+// knot-gradient bins of k_learned_contract_gradk
+size_t smem_gradk(int J) { return sizeof(float) * (size_t)LRN_P * J; }
+size_t smem_plane1(const GridArgs& g) {
+    return sizeof(float2) * tw_offset((size_t)g.N3 * g.Nh) + sizeof(Tw) * (g.N1 + g.N3);
 }
-size_t smem_contract(const GridArgs& g, int C, bool gradk, int J) {
-    return sizeof(float2) * ((size_t)LRN_M * C * g.N2 + g.N2) + (gradk ? sizeof(float) * (size_t)LRN_P * J : 0);
-}
-size_t smem_plane1(const GridArgs& g) { return sizeof(float2) * ((size_t)g.N3 * g.Nh + g.N1 + g.N3); }
 size_t smem_pgrad() {
     return sizeof(float) * ((size_t)LRN_H * LRN_H + LRN_M * LRN_H + 2 * LRN_H + 2 * LRN_H + LRN_M +
                             3 * (size_t)PG_TILE * PG_LD + PG_TILE * LRN_M + 2 * PG_TILE);
 }
 constexpr int GRAD_COLS = 8;
-size_t smem_pgrad_pencil(const GridArgs& g) { return sizeof(float2) * ((size_t)4 * GRAD_COLS * g.N2 + g.N2); }
+size_t smem_pgrad_pencil(const GridArgs& g) {
+    return sizeof(float2) * tw_offset((size_t)4 * GRAD_COLS * g.N2) + sizeof(Tw) * g.N2;
+}
 const size_t SMEM_LIMIT = 227 * 1024 - 4 * 1024;
 
 template <class K>
@@ -1071,10 +1055,8 @@ int set_smem(K kernel, size_t bytes, const char* name) {
 template <int CN1, int CN2, int CN3>
 int configure(vdw_ctx* c) {
     const GridArgs& g = c->g;
-    const int C = contract_cols(g);
     int rc = set_smem(k_learned_net, smem_net(), "k_learned_net");
-    if (!rc) rc = set_smem(k_learned_contract<CN2, false>, smem_contract(g, C, false, c->lrn_J), "k_learned_contract");
-    if (!rc) rc = set_smem(k_learned_contract<CN2, true>, smem_contract(g, C, true, c->lrn_J), "k_learned_contract");
+    if (!rc) rc = set_smem(k_learned_contract_gradk, smem_gradk(c->lrn_J), "k_learned_contract_gradk");
     if (!rc) rc = set_smem(k_field_plane<CN1, CN3>, smem_plane1(g), "k_field_plane");
     if (!rc) rc = set_smem(k_plane_inv3<CN1, CN3>, smem_plane1(g), "k_plane_inv3");
     if (!rc) rc = set_smem(k_pencil_grad<CN2>, smem_pgrad_pencil(g), "k_pencil_grad");
@@ -1102,14 +1084,12 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     const GridArgs& g = c->g;
     const PointParams& P = c->pp;
     const LearnedArgs& la = c->la;
-    const int C = contract_cols(g);
-    const int nb_c = (g.ncols + C - 1) / C;
     const int nb0 = net_blocks(c);
     double* ep = lrn_epart(c);
     float* specf = reinterpret_cast<float*>(c->d_spec);
     const double Omega = c->L[0] * c->L[1] * c->L[2];
-    // stage marks for vdw_profile_read: 1 network + channel planes, 2 pencils,
-    // 3 energy, 4 assembly, 6 divergence (stages 0 and 5 are not separate)
+    // stage marks for vdw_profile_read (the network kernel is stage 0; the
+    // divergence pencils and final planes are one mark)
     auto mark = [&](int stage) {
         if (c->prof) {
             cudaEventRecord(c->ev[stage + 1], s);
@@ -1124,24 +1104,35 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     const bool want_pot = (v != nullptr) || (w != nullptr);
     k_learned_net<<<nb0, L_NET_THREADS, smem_net(), s>>>(n, grad, g, P, la, specf, ep, c->d_invalid,
                                                      (want_pot && kind != RUN_GRAD) ? c->d_lw : nullptr);
+    mark(ST_POINTWISE);
     int rc = pipeline_planes_inplace(c, LRN_M, false, s);
     if (rc) return rc;
-    mark(1);
+    mark(ST_PLANES_FWD);
+    rc = sorted_forward(c, LRN_M, s);
+    if (rc) return rc;
+    mark(ST_PENCILS_FWD);
     if (kind == RUN_GRAD) {
         VDW_CUDA(cudaMemsetAsync(c->d_gK, 0, sizeof(double) * LRN_P * c->lrn_J, s));
-        k_learned_contract<CN2, true><<<nb_c, 256, smem_contract(g, C, true, c->lrn_J), s>>>(
-            c->d_spec, g, la, c->d_tw, ep + nb0, C, 1, c->d_gK, (float)(0.5 * Omega / ((double)g.N * (double)g.N)));
+        k_learned_contract_gradk<<<c->nb_sorted, SORTED_BLOCK, smem_gradk(c->lrn_J), s>>>(
+            c->d_Q, 2 * c->Npad, c->d_gs, la, g.invN, ep + nb0, c->d_gK,
+            (float)(0.5 * Omega / ((double)g.N * (double)g.N)));
+        VDW_CUDA(cudaGetLastError());
     } else {
-        k_learned_contract<CN2, false><<<nb_c, 256, smem_contract(g, C, false, c->lrn_J), s>>>(
-            c->d_spec, g, la, c->d_tw, ep + nb0, C, want_pot ? 1 : 0, nullptr, 0.f);
-    }
-    mark(2);
-    if (E) {
-        rc = pipeline_energy_final(c, ep, nb0, nb_c, E, s);
+        rc = sorted_contract_table(c, LRN_M, la.knots, la.inv_dk, la.J, ep + nb0, want_pot ? 1 : 0, s);
         if (rc) return rc;
-        mark(3);
+    }
+    mark(ST_CONTRACT);
+    if (E) {
+        rc = pipeline_energy_final(c, ep, nb0, c->nb_sorted, E, s);
+        if (rc) return rc;
+        mark(ST_ENERGY);
     }
     const int nb_pt = (int)std::min<long long>((g.N + 255) / 256, 1 << 16);
+    if (kind == RUN_GRAD || want_pot) {
+        rc = sorted_inverse(c, LRN_M, s);
+        if (rc) return rc;
+        mark(ST_PENCILS_INV);
+    }
     if (kind == RUN_GRAD) {
         rc = pipeline_planes_inplace(c, LRN_M, true, s);
         if (rc) return rc;
@@ -1157,16 +1148,16 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
         const int mode = (w != nullptr) ? 0 : 1;
         rc = pipeline_planes_inplace(c, LRN_M, true, s);
         if (rc) return rc;
+        mark(ST_PLANES_INV);
         k_learned_usum<<<nb_pt, 256, 0, s>>>(specf, grad, g, c->d_lw, v, w, c->d_gg, mode);
+        mark(ST_USUM);
         if (mode == 1) {
             rc = pipeline_w_planes(c, grad, s);
             if (rc) return rc;
-        }
-        mark(4);
-        if (mode == 1) {
+            mark(ST_W_PLANES);
             rc = pipeline_divergence(c, v, s);
             if (rc) return rc;
-            mark(6);
+            mark(ST_DIV_FINAL);
         }
     }
     VDW_CUDA(cudaGetLastError());
@@ -1292,7 +1283,7 @@ int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], do
         la.w2f = reinterpret_cast<uint16_t*>(b + L.w2f);
         la.w3f = reinterpret_cast<uint16_t*>(b + L.w3f);
         la.knots = reinterpret_cast<float4*>(b + L.knots);
-        la.err = reinterpret_cast<int*>(b + L.err);
+        la.err = c->d_flags + 1;
         c->d_gK = reinterpret_cast<double*>(b + L.gK);
         c->lrn_J = J;
     }
@@ -1344,6 +1335,8 @@ int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], do
 int vdw_learned_energy_potential(vdw_handle c, const float* n, const float* grad, double* E, float* v, float* w,
                                  void* stream) {
     if (!c || !n || !grad) return VDW_ERR_ARG;
+    if (c->planned)
+        if (const int rw = check_wait(c)) return rw;
     return learned_run(c, n, grad, E, v, w, (cudaStream_t)stream);
 }
 
@@ -1351,6 +1344,7 @@ int vdw_learned_param_grad(vdw_handle c, const float* n, const float* grad, doub
                            void* stream) {
     if (!c || !n || !grad || !g_params) return VDW_ERR_ARG;
     if (!lrn_ready(c)) return VDW_ERR_STATE;
+    if (const int rw = check_wait(c)) return rw;
     if (!c->d_U) VDW_CUDA(cudaMalloc(&c->d_U, sizeof(float) * LRN_M * (size_t)c->g.N));
     return run_any(c, n, grad, E, nullptr, nullptr, RUN_GRAD, coef, g_params, (cudaStream_t)stream);
 }
@@ -1387,7 +1381,8 @@ int vdw_learned_channels(vdw_handle c, const float* n, const float* grad, float*
 int vdw_learned_status(vdw_handle c, int* tc_error) {
     if (!c || !tc_error) return VDW_ERR_ARG;
     if (!c->lrn_loaded) return VDW_ERR_STATE;
-    VDW_CUDA(cudaMemcpy(tc_error, c->la.err, sizeof(int), cudaMemcpyDeviceToHost));
+    VDW_CUDA(cudaDeviceSynchronize());
+    *tc_error = (((volatile int*)c->h_flags)[1] || c->wait_seen) ? 1 : 0;
     return VDW_OK;
 }
 

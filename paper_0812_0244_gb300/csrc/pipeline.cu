@@ -6,10 +6,11 @@
 //                       (Eqs. DEnl, Depsnl)
 //   P1 k_planes_inplace forward plane transforms of theta_a in place: R2C
 //                       along x and C2C along z in shared memory
-//   P2 k_pencil_contract  C2C along y of all Nq fields of a few columns, then
-//                       per G: u_a(G) = sum_b phi_ab(|G|) theta_b(G) with phi_ab
-//                       from the radial table, energy of Eq. (Eoffk) in FP64,
-//                       inverse C2C along y (Eqs. epsilon, epsofk)
+//   P2 (contract.cu)    C2C along y of all Nq fields, points written in |G|
+//                       order; per G: u_a(G) = sum_b phi_ab(|G|) theta_b(G)
+//                       with phi_ab from the radial table, energy of Eq.
+//                       (Eoffk) in FP64; inverse C2C along y (Eqs. epsilon,
+//                       epsofk)
 //   P3 k_planes_inplace inverse plane transform of u_a (in place)
 //      k_u_sum          Eq. (Vi) per point: v_loc and g of w = g grad n
 //      k_w_planes       forward plane transform of w
@@ -34,11 +35,6 @@
 
 namespace vdw {
 
-// Contraction blocks: at most this many threads, two blocks per SM (the
-// table fetches are latency bound, so resident warps matter more than
-// columns per block: at 180 x 180 x 72, 2 columns x 192 threads x 2 blocks
-// ran in 0.70 ms against 0.87 ms for 3 columns x 288 threads x 1 block).
-constexpr int CONTRACT_THREADS = 192;
 constexpr int XC_BLOCKS = 1024;  // blocks (and partial-sum slots) of the semilocal kernel
 
 // ---------------------------------------------------------------------------
@@ -65,6 +61,17 @@ __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, 
                                                    unsigned long long* __restrict__ invalid) {
     __shared__ double red[32];
     __shared__ SplineSmem sp;
+    {
+        // density blockIdx.y of a batch
+        const long long b = blockIdx.y;
+        n += b * g.N;
+        grad += 3 * b * g.N;
+        t_out += b * g.N;
+        k_out += b * g.N;
+        aux += b * g.N;
+        specf += 2 * b * g.bs_spec;
+        epart += b * g.bs_epart;
+    }
     load_spline_smem(&sp, P);
     __syncthreads();
     const int sl = slab >= 0 ? slab : (int)blockIdx.x / nbs;
@@ -119,119 +126,8 @@ __global__ void __launch_bounds__(256) k_pointwise(const float* __restrict__ n, 
     if (threadIdx.x == 0 && b > 0.0) atomicAdd(invalid, (unsigned long long)b);
 }
 
-// P1 (the forward plane transforms of theta_a) is k_planes_inplace below.
-
-// ---------------------------------------------------------------------------
-// P2: pencils along y, contraction with the radial kernel table, energy
-// ---------------------------------------------------------------------------
-// G = (kx, ky, kz) and (kx, -ky, kz) have the same |G|: one thread takes both,
-// so each table row it fetches serves two points.  The thread keeps the two
-// points' u accumulators in registers and reads their theta values from the
-// block's shared lines (only it reads those two positions).
-template <int NQ, int CN2>
-__global__ void __launch_bounds__(CONTRACT_THREADS, 2) k_pencil_contract(float2* __restrict__ spec, GridArgs g,
-                                                                       const float4* __restrict__ kcoef,
-                                                                       const float2* __restrict__ tw,
-                                                                       double* __restrict__ epart, int C,
-                                                                       int write_back) {
-    extern __shared__ float2 sm[];
-    __shared__ double red[32];
-    const int N2 = CN2 > 0 ? CN2 : g.N2;
-    float2* lines = sm;  // [NQ][C][N2]
-    float2* tw2 = lines + NQ * C * N2;
-    load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
-    const int c0 = blockIdx.x * C;
-    const SmallDiv sC = small_div(C);  // i / C in the staging loops
-    const int tot = NQ * N2 * C;
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int r = sdiv(i, sC), cc = i - r * C, yy = r % N2, a = r / N2;
-        const int col = c0 + cc;
-        float2 val = make_float2(0.f, 0.f);
-        if (col < g.ncols) val = spec[((long long)a * N2 + yy) * g.ncols + col];
-        lines[(a * C + cc) * N2 + yy] = val;
-    }
-    __syncthreads();
-    pencils_fft<CN2, false>(lines, NQ * C, N2, g.p2, tw2);
-    __syncthreads();
-
-    constexpr int NP = NQ * (NQ + 1) / 2;
-    const int npy = N2 / 2 + 1;  // y = 0 .. N2/2, each with its partner N2 - y
-    const int LS = C * N2;       // stride between fields in lines
-    double eacc = 0.0;
-    for (int task = threadIdx.x; task < C * npy; task += blockDim.x) {
-        const int cc = task / npy, ya = task - cc * npy;
-        const int col = c0 + cc;
-        if (col >= g.ncols) continue;
-        const int yb0 = N2 - ya;
-        const bool two = (ya != 0) && (yb0 != ya);
-        const int yb = two ? yb0 : ya;  // self-paired: second point is a duplicate, dropped below
-        const int kx = col % g.Nh, kz = col / g.Nh;
-        const int mz = (2 * kz <= g.N3) ? kz : kz - g.N3;
-        const float G2 = g.gx2 * (float)(kx * kx) + g.gy2 * (float)(ya * ya) + g.gz2 * (float)(mz * mz);
-        const float s = sqrtf(G2) * g.inv_dk;
-        const int j = min((int)s, g.Nk - 2);
-        const float t = s - (float)j;
-        const float4* cf = kcoef + (long long)j * NP;
-        const float2* la = lines + cc * N2 + ya;
-        const float2* lb = lines + cc * N2 + yb;
-        float2 ua[NQ], ub[NQ];
-#pragma unroll
-        for (int a = 0; a < NQ; ++a) {
-            ua[a] = make_float2(0.f, 0.f);
-            ub[a] = make_float2(0.f, 0.f);
-        }
-        int p = 0;
-#pragma unroll
-        for (int a = 0; a < NQ; ++a) {
-            const float2 taa = la[a * LS], tba = lb[a * LS];
-#pragma unroll
-            for (int b = a; b < NQ; ++b, ++p) {
-                const float4 c = __ldg(cf + p);
-                const float phi = fmaf(t, fmaf(t, fmaf(t, c.w, c.z), c.y), c.x);
-                const float2 tab = la[b * LS], tbb = lb[b * LS];
-                ua[a].x = fmaf(phi, tab.x, ua[a].x);
-                ua[a].y = fmaf(phi, tab.y, ua[a].y);
-                ub[a].x = fmaf(phi, tbb.x, ub[a].x);
-                ub[a].y = fmaf(phi, tbb.y, ub[a].y);
-                if (b != a) {
-                    ua[b].x = fmaf(phi, taa.x, ua[b].x);
-                    ua[b].y = fmaf(phi, taa.y, ua[b].y);
-                    ub[b].x = fmaf(phi, tba.x, ub[b].x);
-                    ub[b].y = fmaf(phi, tba.y, ub[b].y);
-                }
-            }
-        }
-        float ea = 0.f, eb = 0.f;
-#pragma unroll
-        for (int a = 0; a < NQ; ++a) {
-            const float2 taa = la[a * LS], tba = lb[a * LS];
-            ea = fmaf(taa.x, ua[a].x, fmaf(taa.y, ua[a].y, ea));
-            eb = fmaf(tba.x, ub[a].x, fmaf(tba.y, ub[a].y, eb));
-        }
-        const bool single = (kx == 0) || (2 * kx == g.N1);
-        eacc += ((double)ea + (two ? (double)eb : 0.0)) * (single ? 1.0 : 2.0);
-        if (write_back) {
-            float2* wa = lines + cc * N2 + ya;
-            float2* wb = lines + cc * N2 + yb;
-#pragma unroll
-            for (int a = 0; a < NQ; ++a) {
-                wa[a * LS] = cscale(ua[a], g.invN);
-                if (two) wb[a * LS] = cscale(ub[a], g.invN);
-            }
-        }
-    }
-    const double es = block_sum(eacc, red);
-    if (threadIdx.x == 0) epart[blockIdx.x] = es;
-    if (!write_back) return;
-    __syncthreads();
-    pencils_fft<CN2, true>(lines, NQ * C, N2, g.p2, tw2);
-    __syncthreads();
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        const int r = sdiv(i, sC), cc = i - r * C, yy = r % N2, a = r / N2;
-        const int col = c0 + cc;
-        if (col < g.ncols) spec[((long long)a * N2 + yy) * g.ncols + col] = lines[(a * C + cc) * N2 + yy];
-    }
-}
+// P1 (the forward plane transforms of theta_a) is k_planes_inplace below; P2
+// (y transforms and the contraction) is in contract.cu.
 
 // ---------------------------------------------------------------------------
 // P3: inverse plane transforms of u_a, in place
@@ -277,15 +173,17 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
 
 template <int CN1, int CN3, bool INV>
 __global__ void __launch_bounds__(PLANE_THREADS, 2) k_planes_inplace(float2* __restrict__ spec, GridArgs g,
-                                                                     const float2* __restrict__ tw, int bulk,
+                                                                     const Tw* __restrict__ tw, int bulk,
                                                                      int* __restrict__ wait_err) {
     extern __shared__ float2 sm[];
     __shared__ uint64_t bar;
     float2* plane = sm;
-    float2* tw1 = plane + g.N3 * g.Nh;
-    float2* tw3 = tw1 + g.N1;
+    // the forward transforms of theta feed the energy: hi/lo twiddles there
+    using W = TwOf<!INV>;
+    W* tw1 = twiddles_after<W>(plane, (size_t)(g.N3 * g.Nh));
+    W* tw3 = tw1 + g.N1;
     const int y = blockIdx.x, a = blockIdx.y;
-    float2* src = spec + ((long long)a * g.N2 + y) * g.ncols;
+    float2* src = spec + blockIdx.z * g.bs_spec + ((long long)a * g.N2 + y) * g.ncols;
     // bulk: one copy of the whole plane (16-byte aligned, a multiple of 16
     // bytes), in flight while the twiddles load
     if (bulk) {
@@ -298,10 +196,17 @@ __global__ void __launch_bounds__(PLANE_THREADS, 2) k_planes_inplace(float2* __r
     load_line_twiddles<CN1>(tw1, tw, g.N1);
     load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
     __syncthreads();
-    if (bulk && !mbar_wait_parity(&bar, 0u)) {
-        // gave up: record it, wait once more (bounded) for the copy in flight
-        atomicExch(wait_err, 1);
+    const bool got = !bulk || mbar_wait_parity(&bar, 0u);
+    if (__syncthreads_or(!got)) {
+        // a wait gave up: record it for the next entry point, give the copy in
+        // flight (it writes this block's shared memory) a second bounded wait,
+        // and leave the plane as it is rather than transform a partial one
+        if (threadIdx.x == 0) {
+            *(volatile int*)wait_err = 1;
+            __threadfence_system();
+        }
         mbar_wait_parity(&bar, 0u);
+        return;
     }
     if constexpr (INV) {
         plane_inverse<CN1, CN3>(plane, g, tw1, tw3);
@@ -344,6 +249,18 @@ __global__ void __launch_bounds__(USUM_THREADS) k_u_sum(const float* __restrict_
                                                         float* __restrict__ v, float* __restrict__ w_out,
                                                         float* __restrict__ g_out, int mode) {
     __shared__ SplineSmem sp;
+    {
+        // density blockIdx.y of a batch
+        const long long b = blockIdx.y;
+        uf += 2 * b * g.bs_spec;
+        grad += 3 * b * g.N;
+        tk += b * g.N;
+        kk += b * g.N;
+        aux += b * g.N;
+        if (v) v += b * g.N;
+        if (w_out) w_out += 3 * b * g.N;
+        if (g_out) g_out += b * g.N;
+    }
     load_spline_smem(&sp, P);
     __syncthreads();
     const long long N = g.N;
@@ -391,13 +308,16 @@ __global__ void __launch_bounds__(USUM_THREADS) k_u_sum(const float* __restrict_
 template <int CN1, int CN3>
 __global__ void __launch_bounds__(PLANE_THREADS, 2) k_w_planes(const float* __restrict__ gfield,
                                                                 const float* __restrict__ grad, GridArgs g,
-                                                                const float2* __restrict__ tw,
+                                                                const Tw* __restrict__ tw,
                                                                 float2* __restrict__ wspec) {
     extern __shared__ float2 sm[];
     float2* plane = sm;
-    float2* tw1 = plane + g.N3 * g.Nh;
+    float2* tw1 = twiddles_after<float2>(plane, (size_t)(g.N3 * g.Nh));
     float2* tw3 = tw1 + g.N1;
     const int y = blockIdx.x, c = blockIdx.y;
+    gfield += blockIdx.z * g.N;  // density blockIdx.z of a batch
+    grad += 3 * blockIdx.z * g.N;
+    wspec += blockIdx.z * g.bs_wspec;
     load_line_twiddles<CN1>(tw1, tw, g.N1);
     load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -422,11 +342,12 @@ constexpr int DIV_COLS_CT = 8;  // columns per divergence block
 
 template <int CN2>
 __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspec, GridArgs g,
-                                                       const float2* __restrict__ tw, int C) {
+                                                       const Tw* __restrict__ tw, int C) {
     extern __shared__ float2 sm[];
     const int N2 = CN2 > 0 ? CN2 : g.N2;
     float2* lines = sm;  // [3][C][N2]
-    float2* tw2 = lines + 3 * C * N2;
+    float2* tw2 = twiddles_after<float2>(lines, (size_t)(3 * C * N2));
+    wspec += blockIdx.y * g.bs_wspec;  // density blockIdx.y of a batch
     load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
     const SmallDiv sC = small_div(C);  // i / C in the staging loops
@@ -434,10 +355,10 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
     for (int i = threadIdx.x; i < tot; i += blockDim.x) {
         const int r = sdiv(i, sC), cc = i - r * C, yy = r % N2, c = r / N2;
         const int col = c0 + cc;
-        float2 val = make_float2(0.f, 0.f);
-        if (col < g.ncols) val = wspec[((long long)c * N2 + yy) * g.ncols + col];
-        lines[(c * C + cc) * N2 + yy] = val;
+        const bool ok = col < g.ncols;
+        cp_async8(lines + (c * C + cc) * N2 + yy, ok ? wspec + ((long long)c * N2 + yy) * g.ncols + col : wspec, ok);
     }
+    cp_async_wait_all();
     __syncthreads();
     pencils_fft<CN2, false>(lines, 3 * C, N2, g.p2, tw2);
     __syncthreads();
@@ -474,12 +395,14 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
 // ---------------------------------------------------------------------------
 template <int CN1, int CN3>
 __global__ void __launch_bounds__(PLANE_THREADS, 2) k_div_final(const float2* __restrict__ wspec, GridArgs g,
-                                                      const float2* __restrict__ tw, float* __restrict__ v) {
+                                                      const Tw* __restrict__ tw, float* __restrict__ v) {
     extern __shared__ float2 sm[];
     float2* plane = sm;
-    float2* tw1 = plane + g.N3 * g.Nh;
+    float2* tw1 = twiddles_after<float2>(plane, (size_t)(g.N3 * g.Nh));
     float2* tw3 = tw1 + g.N1;
     const int y = blockIdx.x;
+    wspec += blockIdx.y * g.bs_wspec;  // density blockIdx.y of a batch
+    v += blockIdx.y * g.N;
     load_line_twiddles<CN1>(tw1, tw, g.N1);
     load_line_twiddles<CN3>(tw3, tw + g.N1 + g.N2, g.N3);
     const float2* src = wspec + (long long)y * g.ncols;
@@ -618,8 +541,10 @@ __global__ void k_xc_final(const double* __restrict__ Enl, const double* __restr
 // energy: fixed-order FP64 reduction of the block partials
 // ---------------------------------------------------------------------------
 __global__ void k_energy_final(const double* __restrict__ epart, int nb0, int nb2, double s0, double s2,
-                               double* __restrict__ E) {
+                               double* __restrict__ E, int bs_epart) {
     __shared__ double red[32];
+    epart += (long long)blockIdx.x * bs_epart;  // density blockIdx.x of a batch
+    E += 3 * blockIdx.x;
     double a0 = 0.0, a2 = 0.0;
     for (int i = threadIdx.x; i < nb0; i += blockDim.x) a0 += epart[i];
     for (int i = threadIdx.x; i < nb2; i += blockDim.x) a2 += epart[nb0 + i];
@@ -634,11 +559,13 @@ __global__ void k_energy_final(const double* __restrict__ epart, int nb0, int nb
     }
 }
 
-__global__ void k_twiddles(float2* tw, int n, int off) {
+// W_n^e = exp(-2 pi i e / n) in FP64, stored as the hi/lo FP32 pair of each part
+__global__ void k_twiddles(Tw* tw, int n, int off) {
     for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < n; e += blockDim.x * gridDim.x) {
         double s, c;
         sincospi(-2.0 * (double)e / (double)n, &s, &c);
-        tw[off + e] = make_float2((float)c, (float)s);
+        const float ch = (float)c, sh = (float)s;
+        tw[off + e] = make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
     }
 }
 
@@ -656,14 +583,13 @@ int make_line_plan(int n, LinePlan* lp) {
     return m == 1 ? VDW_OK : VDW_ERR_SIZE;
 }
 
-static size_t smem_plane(const GridArgs& g) { return sizeof(float2) * ((size_t)g.N3 * g.Nh + g.N1 + g.N3); }
-static size_t smem_pencil(const GridArgs& g, int nq, int C) { return sizeof(float2) * ((size_t)nq * C * g.N2 + g.N2); }
-static size_t smem_pencil_run(const GridArgs& g, int nq, int C) { return smem_pencil(g, nq, C); }
-
-static int contract_threads(const GridArgs& g, int C) {
-    const int npy = g.N2 / 2 + 1;
-    return std::min(CONTRACT_THREADS, std::max(64, (C * npy + 31) / 32 * 32));
+static size_t smem_plane(const GridArgs& g) {
+    return sizeof(float2) * tw_offset((size_t)g.N3 * g.Nh) + sizeof(Tw) * (g.N1 + g.N3);
 }
+static size_t smem_pencil(const GridArgs& g, int nq, int C) {
+    return sizeof(float2) * tw_offset((size_t)nq * C * g.N2) + sizeof(Tw) * g.N2;
+}
+static size_t smem_pencil_run(const GridArgs& g, int nq, int C) { return smem_pencil(g, nq, C); }
 
 // dynamic shared memory per block, leaving room for the kernels' static arrays
 static const size_t SMEM_MAX = 227 * 1024 - 5 * 1024;
@@ -671,15 +597,8 @@ static const int DIV_COLS = DIV_COLS_CT;
 
 int pipeline_plan_check(vdw_ctx* c, size_t* sp, size_t* spen, size_t* sa, size_t* sd) {
     const GridArgs& g = c->g;
-    const int nq = c->p.Nq;
-    // columns per pencil block: at most 8, within ~110 KB of shared memory
-    // (two blocks per SM), and one (+-y pair) task per thread
-    const int npy = g.N2 / 2 + 1;
-    int C = 8;
-    while (C > 1 && (smem_pencil(g, nq, C) > 110 * 1024 || C * npy > CONTRACT_THREADS)) --C;
-    c->pencil_cols = C;
     *sp = smem_plane(g);
-    *spen = smem_pencil_run(g, nq, C);
+    *spen = sorted_pencil_smem(g);
     // the inverse plane transforms of u take their planes by one bulk copy when
     // a plane is a whole multiple of 16 bytes (every plane then starts 16-byte aligned)
     c->bulk_planes = (sizeof(float2) * (size_t)g.ncols) % 16 == 0;
@@ -700,28 +619,6 @@ int pipeline_make_twiddles(vdw_ctx* c) {
     return VDW_OK;
 }
 
-template <int NQ, int CN2>
-static void launch_contract(vdw_ctx* c, cudaStream_t s, int write_back) {
-    const GridArgs& g = c->g;
-    const int C = c->pencil_cols;
-    const size_t sm = smem_pencil_run(g, NQ, C);
-    const int threads = contract_threads(g, C);
-    k_pencil_contract<NQ, CN2><<<c->nb_pencil, threads, sm, s>>>(c->d_spec, g, c->d_kcoef, c->d_tw,
-                                                                 c->d_epart + c->nb_point, C, write_back);
-}
-
-template <int CN2>
-static int launch_contract_nq(vdw_ctx* c, cudaStream_t s, int write_back) {
-    switch (c->pp.Nq) {
-        case 20: launch_contract<20, CN2>(c, s, write_back); break;
-        case 8: launch_contract<8, CN2>(c, s, write_back); break;
-        case 12: launch_contract<12, CN2>(c, s, write_back); break;
-        case 16: launch_contract<16, CN2>(c, s, write_back); break;
-        default: set_error("Nq not compiled in"); return VDW_ERR_UNSUPPORTED;
-    }
-    return VDW_OK;
-}
-
 static float3 stencil_ih2(const vdw_ctx* c) {
     return make_float3((float)(c->g.N1 / (2.0 * c->L[0])), (float)(c->g.N2 / (2.0 * c->L[1])),
                        (float)(c->g.N3 / (2.0 * c->L[2])));
@@ -736,12 +633,13 @@ int pipeline_stencil_gradient(vdw_ctx* c, const float* f, float* grad, cudaStrea
 
 static int u_sum_blocks(const GridArgs& g) { return (int)std::min<long long>((g.N + USUM_THREADS - 1) / USUM_THREADS, 1 << 16); }
 
-static int launch_u_sum(vdw_ctx* c, const float* n, const float* grad, float* v, float* w, int mode, cudaStream_t s) {
+static int launch_u_sum(vdw_ctx* c, const float* n, const float* grad, float* v, float* w, int mode, cudaStream_t s,
+                        int B) {
     const GridArgs& g = c->g;
     const float* uf = reinterpret_cast<const float*>(c->d_spec);
     const int nb = u_sum_blocks(g);
 #define VDW_U_SUM(NQ) \
-    k_u_sum<NQ><<<nb, USUM_THREADS, 0, s>>>(uf, grad, c->d_t, c->d_k, c->d_aux, g, c->pp, v, w, c->d_gg, mode)
+    k_u_sum<NQ><<<dim3(nb, B), USUM_THREADS, 0, s>>>(uf, grad, c->d_t, c->d_k, c->d_aux, g, c->pp, v, w, c->d_gg, mode)
     switch (c->pp.Nq) {
         case 20: VDW_U_SUM(20); break;
         case 8: VDW_U_SUM(8); break;
@@ -755,7 +653,7 @@ static int launch_u_sum(vdw_ctx* c, const float* n, const float* grad, float* v,
 
 template <int CN1, int CN2, int CN3>
 static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s,
-                     int fd, int xc, const cudaEvent_t* slab_ready) {
+                     int fd, int xc, const cudaEvent_t* slab_ready, int B) {
     const GridArgs& g = c->g;
     const PointParams& P = c->pp;
     const bool want_pot = (v != nullptr) || (w != nullptr);
@@ -779,7 +677,7 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
         const int slab = slab_ready ? sl : -1;
         const int nblk = slab_ready ? c->nb_p0 : c->nb_point;
 #define VDW_POINTWISE(NQ)                                                                                  \
-    k_pointwise<NQ><<<nblk, 256, 0, s>>>(n, grad, g, P, slab, c->p0_nj, c->p0_mnj, c->nb_p0, c->d_t, c->d_k, \
+    k_pointwise<NQ><<<dim3(nblk, B), 256, 0, s>>>(n, grad, g, P, slab, c->p0_nj, c->p0_mnj, c->nb_p0, c->d_t, c->d_k, \
                                          c->d_aux, specf, c->d_epart, c->d_invalid)
         switch (P.Nq) {
             case 20: VDW_POINTWISE(20); break;
@@ -790,48 +688,56 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
         }
 #undef VDW_POINTWISE
     }
-    mark(0);
+    mark(ST_POINTWISE);
 
     const size_t sp = smem_plane(g);
-    k_planes_inplace<CN1, CN3, false><<<dim3(g.N2, P.Nq), PLANE_THREADS, sp, s>>>(c->d_spec, g, c->d_tw,
-                                                                                  c->bulk_planes, c->d_flags);
-    mark(1);
+    k_planes_inplace<CN1, CN3, false><<<dim3(g.N2, P.Nq, B), PLANE_THREADS, sp, s>>>(c->d_spec, g, c->d_tw,
+                                                                                     c->bulk_planes, c->d_flags);
+    mark(ST_PLANES_FWD);
 
-    int rc = launch_contract_nq<CN2>(c, s, want_pot ? 1 : 0);
+    // y transforms, contraction in |G| order, inverse y transforms (contract.cu)
+    int rc = sorted_forward(c, P.Nq, s, B);
     if (rc) return rc;
-    mark(2);
+    mark(ST_PENCILS_FWD);
+    rc = sorted_contract(c, c->d_epart + c->nb_point, want_pot ? 1 : 0, s, B);
+    if (rc) return rc;
+    mark(ST_CONTRACT);
     if (E) {
         const double Omega = c->L[0] * c->L[1] * c->L[2];
         const double Nd = (double)g.N;
-        k_energy_final<<<1, 256, 0, s>>>(c->d_epart, c->nb_point, c->nb_pencil, Omega / Nd,
-                                         0.5 * Omega / (Nd * Nd), E);
-        mark(3);
+        k_energy_final<<<B, 256, 0, s>>>(c->d_epart, c->nb_point, c->nb_sorted, Omega / Nd,
+                                         0.5 * Omega / (Nd * Nd), E, g.bs_epart);
+        mark(ST_ENERGY);
     }
     if (xc && !want_pot)
         k_semilocal<<<XC_BLOCKS, 256, 0, s>>>(n, grad, g.N, P.n_min, nullptr, nullptr, c->d_xc + 4);
     if (want_pot) {
+        rc = sorted_inverse(c, P.Nq, s, B);
+        if (rc) return rc;
+        mark(ST_PENCILS_INV);
         const int mode = (w != nullptr) ? 0 : 1;
-        k_planes_inplace<CN1, CN3, true><<<dim3(g.N2, P.Nq), PLANE_THREADS, sp, s>>>(c->d_spec, g, c->d_tw,
-                                                                                     c->bulk_planes, c->d_flags);
-        const int rcs = launch_u_sum(c, n, grad, v, w, mode, s);
+        k_planes_inplace<CN1, CN3, true><<<dim3(g.N2, P.Nq, B), PLANE_THREADS, sp, s>>>(c->d_spec, g, c->d_tw,
+                                                                                        c->bulk_planes, c->d_flags);
+        mark(ST_PLANES_INV);
+        const int rcs = launch_u_sum(c, n, grad, v, w, mode, s, B);
         if (rcs) return rcs;
         if (xc)
             k_semilocal<<<XC_BLOCKS, 256, 0, s>>>(n, grad, g.N, P.n_min, v, mode == 1 ? c->d_gg : nullptr,
                                                   c->d_xc + 4);
+        mark(ST_USUM);
         if (mode == 1 && fd) {
             // finite-difference gradient: the chain term is a stencil, no transforms
-            mark(4);
             k_stencil_div_sub<<<stencil_blocks(g), 256, 0, s>>>(c->d_gg, grad, g, stencil_ih2(c), v);
-            mark(6);
-        } else if (mode == 1)
-            k_w_planes<CN1, CN3><<<dim3(g.N2, 3), PLANE_THREADS, sp, s>>>(c->d_gg, grad, g, c->d_tw, c->d_wspec);
-        if (!(mode == 1 && fd)) mark(4);
-        if (mode == 1 && !fd) {
+            mark(ST_DIV_FINAL);
+        } else if (mode == 1) {
+            k_w_planes<CN1, CN3><<<dim3(g.N2, 3, B), PLANE_THREADS, sp, s>>>(c->d_gg, grad, g, c->d_tw, c->d_wspec);
+            mark(ST_W_PLANES);
             const size_t sd = smem_pencil_run(g, 3, DIV_COLS);
-            k_pencil_div<CN2><<<(g.ncols + DIV_COLS - 1) / DIV_COLS, 256, sd, s>>>(c->d_wspec, g, c->d_tw, DIV_COLS);
-            mark(5);
-            k_div_final<CN1, CN3><<<g.N2, PLANE_THREADS, sp, s>>>(c->d_wspec, g, c->d_tw, v);
-            mark(6);
+            k_pencil_div<CN2><<<dim3((g.ncols + DIV_COLS - 1) / DIV_COLS, B), 256, sd, s>>>(c->d_wspec, g, c->d_tw,
+                                                                                          DIV_COLS);
+            mark(ST_PENCIL_DIV);
+            k_div_final<CN1, CN3><<<dim3(g.N2, B), PLANE_THREADS, sp, s>>>(c->d_wspec, g, c->d_tw, v);
+            mark(ST_DIV_FINAL);
         }
     }
     VDW_CUDA(cudaGetLastError());
@@ -859,22 +765,14 @@ template <int CN1, int CN2, int CN3>
 static int configure_sized(vdw_ctx* c) {
     const GridArgs& g = c->g;
     const int sp = (int)smem_plane(g);
-    const int sd = (int)smem_pencil_run(g, 3, DIV_COLS), sc = (int)smem_pencil_run(g, c->p.Nq, c->pencil_cols);
-    const int tc = contract_threads(g, c->pencil_cols);
+    const int sd = (int)smem_pencil_run(g, 3, DIV_COLS);
     int rc = set_and_check(k_planes_inplace<CN1, CN3, true>, "k_planes_inplace", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_planes_inplace<CN1, CN3, false>, "k_planes_inplace", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_pencil_div<CN2>, "k_pencil_div", sd, 256);
     if (!rc) rc = set_and_check(k_div_final<CN1, CN3>, "k_div_final", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_w_planes<CN1, CN3>, "k_w_planes", sp, PLANE_THREADS);
     if (rc) return rc;
-    switch (c->p.Nq) {
-        case 20: rc = set_and_check(k_pencil_contract<20, CN2>, "k_pencil_contract", sc, tc); break;
-        case 8: rc = set_and_check(k_pencil_contract<8, CN2>, "k_pencil_contract", sc, tc); break;
-        case 12: rc = set_and_check(k_pencil_contract<12, CN2>, "k_pencil_contract", sc, tc); break;
-        case 16: rc = set_and_check(k_pencil_contract<16, CN2>, "k_pencil_contract", sc, tc); break;
-        default: return VDW_ERR_UNSUPPORTED;
-    }
-    return rc;
+    return sorted_configure(c);
 }
 
 int pipeline_configure(vdw_ctx* c) {
@@ -939,19 +837,19 @@ int pipeline_divergence(vdw_ctx* c, float* v, cudaStream_t s) {
 int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, double* E, cudaStream_t s) {
     const double Omega = c->L[0] * c->L[1] * c->L[2];
     const double Nd = (double)c->g.N;
-    k_energy_final<<<1, 256, 0, s>>>(epart, nb0, nb2, Omega / Nd, 0.5 * Omega / (Nd * Nd), E);
+    k_energy_final<<<1, 256, 0, s>>>(epart, nb0, nb2, Omega / Nd, 0.5 * Omega / (Nd * Nd), E, 0);
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
 }
 
 int pipeline_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s,
-                 int fd, int xc, const cudaEvent_t* slab_ready) {
+                 int fd, int xc, const cudaEvent_t* slab_ready, int B) {
     const GridArgs& g = c->g;
     if (g.N1 == 180 && g.N2 == 180 && g.N3 == 72)
-        return run_sized<180, 180, 72>(c, n, grad, E, v, w, s, fd, xc, slab_ready);
+        return run_sized<180, 180, 72>(c, n, grad, E, v, w, s, fd, xc, slab_ready, B);
     if (g.N1 == 256 && g.N2 == 256 && g.N3 == 96)
-        return run_sized<256, 256, 96>(c, n, grad, E, v, w, s, fd, xc, slab_ready);
-    return run_sized<0, 0, 0>(c, n, grad, E, v, w, s, fd, xc, slab_ready);
+        return run_sized<256, 256, 96>(c, n, grad, E, v, w, s, fd, xc, slab_ready, B);
+    return run_sized<0, 0, 0>(c, n, grad, E, v, w, s, fd, xc, slab_ready, B);
 }
 
 int pipeline_xc_final(vdw_ctx* c, double* E, cudaStream_t s) {

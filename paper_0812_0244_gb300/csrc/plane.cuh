@@ -3,6 +3,8 @@
 // forward / inverse transform of one y plane (N3 rows of N1 reals <-> N3 x Nh
 // half spectrum) held in shared memory.
 #pragma once
+#include <type_traits>
+
 #include "fft.cuh"
 
 namespace vdw {
@@ -29,13 +31,15 @@ __device__ inline double block_sum(double v, double* red) {
     return s;
 }
 
-__device__ __forceinline__ void load_twiddles(float2* dst, const float2* src, int n) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+template <class W>
+__device__ __forceinline__ void load_twiddles(W* dst, const Tw* src, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) tw_put(dst + i, src[i]);
 }
 // Shared-memory twiddles of a line length: the pass-ordered table of the
-// compile-time transforms when CN > 0 (CN == n), the plain table otherwise.
-template <int CN>
-__device__ __forceinline__ void load_line_twiddles(float2* dst, const float2* src, int n) {
+// compile-time transforms when CN > 0 (CN == n), the plain table otherwise;
+// W = Tw keeps the hi/lo pairs, W = float2 the FP32 values only.
+template <int CN, class W>
+__device__ __forceinline__ void load_line_twiddles(W* dst, const Tw* src, int n) {
     if constexpr (CN > 0) ct_load_twiddles<CN>(dst, src);
     else load_twiddles(dst, src, n);
 }
@@ -55,12 +59,22 @@ __device__ __forceinline__ SmallDiv small_div(int d) {
 }
 __device__ __forceinline__ int sdiv(int i, SmallDiv s) { return s.d == 1 ? i : (int)__umulhi((unsigned)i, s.m); }
 
+// 8-byte asynchronous copy global -> shared memory (cp.async), zero-filled
+// instead when !valid (src is then not read; it must still be a mapped
+// address).  A thread issues all its copies without waiting on any;
+// cp_async_wait_all then waits for the thread's own copies.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // line-transform dispatch: compile-time length when CN > 0
 // ---------------------------------------------------------------------------
 // the Nh columns of a plane (element stride Nh), several columns per warp for short lines
-template <int CN, bool INV, int MAXR = 16>
-__device__ __forceinline__ void columns_fft(float2* plane, int Nh, const LinePlan& pl, const float2* tw) {
+template <int CN, bool INV, int MAXR = 16, class W>
+__device__ __forceinline__ void columns_fft(float2* plane, int Nh, const LinePlan& pl, const W* tw) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if constexpr (CN > 0) {
         constexpr int L = ct_lines_per_warp(CN, MAXR);
@@ -73,8 +87,8 @@ __device__ __forceinline__ void columns_fft(float2* plane, int Nh, const LinePla
 }
 
 // contiguous lines of length N2 (pencils), several lines per warp for short lines
-template <int CN, bool INV>
-__device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, const LinePlan& pl, const float2* tw) {
+template <int CN, bool INV, class W>
+__device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, const LinePlan& pl, const W* tw) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if constexpr (CN > 0) {
         constexpr int L = ct_lines_per_warp(CN);
@@ -136,8 +150,8 @@ __device__ __forceinline__ int packed_offset(int x, int j, int s, int Nh) { retu
 // x transform, several rows per warp at compile-time lengths; each row is
 // then untangled into the two half spectra (forward), or tangled before the
 // transform (inverse).
-template <int CN1, bool INV, int MAXR = 16>
-__device__ __forceinline__ void plane_rows(float2* plane, const GridArgs& g, const float2* tw1) {
+template <int CN1, bool INV, int MAXR = 16, class W>
+__device__ __forceinline__ void plane_rows(float2* plane, const GridArgs& g, const W* tw1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nrows = g.N3 / 2, rs = 2 * g.Nh;
     if constexpr (CN1 > 0) {
@@ -168,8 +182,8 @@ __device__ __forceinline__ void plane_rows(float2* plane, const GridArgs& g, con
 }
 
 // Forward: packed real rows -> half spectrum (x R2C, then z C2C).
-template <int CN1, int CN3, int MAXR = 16>
-__device__ void plane_forward(float2* plane, const GridArgs& g, const float2* tw1, const float2* tw3) {
+template <int CN1, int CN3, int MAXR = 16, class W>
+__device__ void plane_forward(float2* plane, const GridArgs& g, const W* tw1, const W* tw3) {
     plane_rows<CN1, false, MAXR>(plane, g, tw1);
     __syncthreads();
     columns_fft<CN3, false, MAXR>(plane, g.Nh, g.p3, tw3);
@@ -177,8 +191,8 @@ __device__ void plane_forward(float2* plane, const GridArgs& g, const float2* tw
 }
 
 // Inverse: half spectrum -> packed real rows (z C2C inverse, then x C2R), unscaled.
-template <int CN1, int CN3, int MAXR = 16>
-__device__ void plane_inverse(float2* plane, const GridArgs& g, const float2* tw1, const float2* tw3) {
+template <int CN1, int CN3, int MAXR = 16, class W>
+__device__ void plane_inverse(float2* plane, const GridArgs& g, const W* tw1, const W* tw3) {
     columns_fft<CN3, true, MAXR>(plane, g.Nh, g.p3, tw3);
     __syncthreads();
     plane_rows<CN1, true, MAXR>(plane, g, tw1);
@@ -186,5 +200,15 @@ __device__ void plane_inverse(float2* plane, const GridArgs& g, const float2* tw
 }
 
 constexpr int PLANE_THREADS = 256;  // threads of the plane kernels (P1, P5)
+
+// Twiddles in shared memory after n float2 values, on a 16-byte boundary.
+__host__ __device__ __forceinline__ size_t tw_offset(size_t n) { return (n + 1) & ~(size_t)1; }
+template <class W = Tw>
+__device__ __forceinline__ W* twiddles_after(float2* base, size_t n) {
+    return reinterpret_cast<W*>(base + tw_offset(n));
+}
+// The twiddle kind of a transform: hi/lo pairs (EXACT) or FP32 values.
+template <bool EXACT>
+using TwOf = typename std::conditional<EXACT, Tw, float2>::type;
 
 }  // namespace vdw

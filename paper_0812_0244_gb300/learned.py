@@ -73,17 +73,27 @@ class Sample:
     cfg: dict = field(default_factory=dict)
 
 
-def make_samples(configs, shape, ctx20, device="cuda"):
-    """Densities on the device, their spectral gradients and the plain targets."""
+def make_samples(configs, shape, ctx20, device="cuda", batch=8):
+    """Densities on the device, their spectral gradients and the plain
+    targets, the latter batch densities per call (vdw_energy_potential_batched)."""
     import torch
     out = []
-    for cfg in configs:
-        n64, L, na = S.tube_density_torch(cfg["seed"], shape=shape, shift_ang=cfg["shift_ang"],
-                                          rot_deg=cfg["rot_deg"], device=device)
-        n = n64.to(torch.float32).contiguous()
-        g = ctx20.spectral_gradient(n)
-        E, v, _ = ctx20.compute(n, g)
-        out.append(Sample(n, g, float(E[0]), v, na, cfg))
+    L = None
+    ctx20.plan_batch(batch)
+    for b0 in range(0, len(configs), batch):
+        part = configs[b0:b0 + batch]
+        ns, nas = [], []
+        for cfg in part:
+            n64, L, na = S.tube_density_torch(cfg["seed"], shape=shape, shift_ang=cfg["shift_ang"],
+                                              rot_deg=cfg["rot_deg"], device=device)
+            ns.append(n64.to(torch.float32))
+            nas.append(na)
+        n = torch.stack(ns).contiguous()
+        g = torch.stack([ctx20.spectral_gradient(n[k]) for k in range(len(part))]).contiguous()
+        E, v = ctx20.energy_potential_batched(n, g, v=torch.empty_like(n))
+        Eh = E.cpu().numpy()
+        for k, cfg in enumerate(part):
+            out.append(Sample(n[k], g[k], float(Eh[k, 0]), v[k], nas[k], cfg))
     torch.cuda.synchronize()
     return out, L
 

@@ -49,50 +49,97 @@ def fit_energy_map(z_ang, phi_deg, E_mev, r_out_ang):
                 rms=float(np.sqrt(np.mean(resid ** 2))))
 
 
-def run(nz=8, nphi=8, shape=(72, 180, 180), seed=0, learned=True, log=print):
-    """Energies on an nz x nphi lattice of outer-wall shifts in [0, 2.46 A)
-    and rotations in [0, 36 deg) (one density seed, so the sites move
-    rigidly), their energy maps, and the timing."""
+def translations(shape, L, sub):
+    """Rigid translations of the whole cell by multiples of 1/sub of the grid
+    spacing along each axis (sub^3 of them, bohr)."""
+    N3, N2, N1 = shape
+    h = np.asarray(L, np.float64) / np.array([N1, N2, N3], np.float64)
+    f = np.arange(sub) / sub
+    return [(a * h[0], b * h[1], c * h[2]) for a in f for b in f for c in f]
+
+
+def scan_energies(ctx, shape, z, phi, seed, dr_out, sub, learned, batch):
+    """Energies (Hartree) of the nz x nphi wall positions, each averaged over
+    the sub^3 rigid translations of the whole cell: the plain path through
+    the batched entry point, and the learned path (per density) if loaded.
+    Averaging over translations by half a grid spacing cancels the odd
+    harmonics of the energy's dependence on the position of the density
+    relative to the grid (the "egg-box" term), which a rigid wall scan would
+    otherwise read as part of the energy map."""
+    import torch
+    _, L, _ = S.tube_density_torch(seed, shape=(8, 8, 8), device="cpu")
+    shifts = translations(shape, L, sub)
+    jobs = [(i, j, t) for i in range(len(z)) for j in range(len(phi)) for t in shifts]
+    Ep = np.zeros((len(z), len(phi)))
+    El = np.zeros((len(z), len(phi)))
+    E1 = torch.empty(3, dtype=torch.float64, device="cuda")
+    for b0 in range(0, len(jobs), batch):
+        part = jobs[b0:b0 + batch]
+        ns = []
+        for i, j, t in part:
+            n64, _, _ = S.tube_density_torch(seed, shape=shape, shift_ang=float(z[i]), rot_deg=float(phi[j]),
+                                             dr_out_ang=dr_out, origin_bohr=t, device="cuda")
+            ns.append(n64.to(torch.float32))
+        n = torch.stack(ns).contiguous()
+        g = torch.stack([ctx.spectral_gradient(n[k]) for k in range(len(part))]).contiguous()
+        E, _ = ctx.energy_potential_batched(n, g)
+        Eh = E.cpu().numpy()
+        for k, (i, j, _) in enumerate(part):
+            Ep[i, j] += Eh[k, 0] / len(shifts)
+            if learned:
+                ctx.learned_energy_potential(n[k], g[k], E1)
+                El[i, j] += float(E1[0]) / len(shifts)
+    return Ep, (El if learned else None)
+
+
+def run(nz=8, nphi=8, grids=(144, 180, 200), dr_out=(-0.2, 0.0, 0.2), seed=0, learned=True, sub=2, batch=8,
+        log=print):
+    """The wall scan: for each grid N x N x 72 and each outer-wall radius
+    change dr (Angstrom), energies on an nz x nphi lattice of outer-wall
+    shifts in [0, 2.46 A) and rotations in [0, 36 deg) (one density seed, so
+    the sites move rigidly), averaged over the sub^3 half-spacing
+    translations, and their energy maps (Eq. Uofx).  The learned path runs on
+    the grids whose largest |G| lies within its knots."""
     import torch
     z = np.arange(nz) * (2.0 * DZ_ANG) / nz
     phi = np.arange(nphi) * (2.0 * DPHI_DEG) / nphi
+    zz, pp = np.meshgrid(z, phi, indexing="ij")
     _, L, natoms = S.tube_density_torch(seed, shape=(8, 8, 8), device="cpu")
-    ctx = vdwnl.VdwNL(vdwnl.Params()).plan(shape, L)
     mdl = None
     if learned:
         try:
             mdl = LR.load()
-            params = torch.tensor(mdl["params"], dtype=torch.float32, device="cuda")
-            ctx.learned_load(params, mdl["J"], mdl["k_max"], mdl["feat"], mdl["base"])
-        except (OSError, vdwnl.VdwError) as ex:
+        except OSError as ex:
             log("learned path skipped: %s" % ex)
-            mdl = None
-    Ep = np.zeros((nz, nphi))
-    El = np.zeros((nz, nphi))
-    E = torch.empty(3, dtype=torch.float64, device="cuda")
     t0 = time.time()
-    for i, zi in enumerate(z):
-        for j, pj in enumerate(phi):
-            n64, _, _ = S.tube_density_torch(seed, shape=shape, shift_ang=float(zi), rot_deg=float(pj), device="cuda")
-            n = n64.to(torch.float32).contiguous()
-            g = ctx.spectral_gradient(n)
-            ctx.energy_potential(n, g, E)
-            Ep[i, j] = float(E[0])
-            if mdl is not None:
-                ctx.learned_energy_potential(n, g, E)
-                El[i, j] = float(E[0])
+    cases = []
+    for N in grids:
+        shape = (72, N, N)
+        ctx = vdwnl.VdwNL(vdwnl.Params()).plan(shape, L)
+        ctx.plan_batch(batch)
+        use_l = False
+        if mdl is not None:
+            try:
+                params = torch.tensor(mdl["params"], dtype=torch.float32, device="cuda")
+                ctx.learned_load(params, mdl["J"], mdl["k_max"], mdl["feat"], mdl["base"])
+                use_l = True
+            except vdwnl.VdwError as ex:
+                log("grid %d: learned path skipped (%s)" % (N, ex))
+        for dr in dr_out:
+            Ep, El = scan_energies(ctx, shape, z, phi, seed, dr, sub, use_l, batch)
+            r_out = 3.0 * S.A_CC * 10 / (2.0 * np.pi) + dr
+            case = dict(grid=N, dr_out_ang=dr,
+                        plain=fit_energy_map(zz, pp, (Ep - Ep.mean()) * MEV_PER_HA / OUTER_ATOMS, r_out),
+                        E_plain_ha=Ep.tolist())
+            if El is not None:
+                case["learned"] = fit_energy_map(zz, pp, (El - El.mean()) * MEV_PER_HA / OUTER_ATOMS, r_out)
+                case["learned_minus_plain_mev_per_atom"] = float(np.abs(El - Ep).max() * MEV_PER_HA / natoms)
+                case["E_learned_ha"] = El.tolist()
+            cases.append(case)
+            log(json.dumps({k: v for k, v in case.items() if not k.startswith("E_")}))
+        ctx.close()
     torch.cuda.synchronize()
-    zz, pp = np.meshgrid(z, phi, indexing="ij")
-    r_out = 3.0 * S.A_CC * 10 / (2.0 * np.pi)
-    out = dict(nz=nz, nphi=nphi, shape=list(shape), seconds=time.time() - t0,
-               plain=fit_energy_map(zz, pp, (Ep - Ep.mean()) * MEV_PER_HA / OUTER_ATOMS, r_out),
-               E_plain_ha=Ep.tolist())
-    if mdl is not None:
-        out["learned"] = fit_energy_map(zz, pp, (El - El.mean()) * MEV_PER_HA / OUTER_ATOMS, r_out)
-        out["learned_minus_plain_mev_per_atom"] = float(np.abs(El - Ep).max() * MEV_PER_HA / natoms)
-        out["E_learned_ha"] = El.tolist()
-    log(json.dumps({k: v for k, v in out.items() if not k.startswith("E_")}))
-    return out
+    return dict(nz=nz, nphi=nphi, sub=sub, seconds=time.time() - t0, cases=cases)
 
 
 if __name__ == "__main__":
@@ -100,8 +147,12 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser(description="outer-wall shift/rotation scan and Eq. (Uofx) fit")
     ap.add_argument("--nz", type=int, default=8)
     ap.add_argument("--nphi", type=int, default=8)
+    ap.add_argument("--grids", default="144,180,200")
+    ap.add_argument("--dr", default="-0.2,0,0.2")
+    ap.add_argument("--sub", type=int, default=2)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    res = run(a.nz, a.nphi)
+    res = run(a.nz, a.nphi, grids=tuple(int(x) for x in a.grids.split(",")),
+              dr_out=tuple(float(x) for x in a.dr.split(",")), sub=a.sub)
     if a.out:
         json.dump(res, open(a.out, "w"))

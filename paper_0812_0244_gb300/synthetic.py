@@ -98,10 +98,12 @@ def _gaussian_sum_torch(shape, L, centers, amps, sigmas, floor, device, cut=8.0)
 
 
 def tube_density_torch(seed=0, shape=(72, 180, 180), inner=5, outer=10, shift_ang=0.0, rot_deg=0.0,
-                       dr_in_ang=0.0, dr_out_ang=0.0, cell_ang=(25.0, 25.0, 9.84), floor=1e-6, device="cuda"):
+                       dr_in_ang=0.0, dr_out_ang=0.0, cell_ang=(25.0, 25.0, 9.84), floor=1e-6, device="cuda",
+                       origin_bohr=(0.0, 0.0, 0.0)):
     """tube_density's density (same seeded draws) evaluated on a torch device;
     returns (n as an FP64 tensor, L, natoms).  For generating many training
-    densities quickly; the gradient is left to the caller."""
+    densities quickly; the gradient is left to the caller.  origin_bohr moves
+    the whole tube rigidly (periodic images included)."""
     rng = np.random.default_rng(seed)
     L = np.asarray(cell_ang, np.float64) * BOHR_PER_ANG
     R_in = 3.0 * A_CC * inner / (2.0 * np.pi) + dr_in_ang
@@ -110,9 +112,9 @@ def tube_density_torch(seed=0, shape=(72, 180, 180), inner=5, outer=10, shift_an
     s_in = armchair_sites(inner, R_in, n_periods)
     s_out = armchair_sites(outer, R_out, n_periods, np.deg2rad(rot_deg), shift_ang)
     sites = np.concatenate([s_in, s_out]) * BOHR_PER_ANG
-    sites[:, 0] += 0.5 * L[0]
-    sites[:, 1] += 0.5 * L[1]
-    sites[:, 2] = np.mod(sites[:, 2], L[2])
+    sites[:, 0] += 0.5 * L[0] + origin_bohr[0]
+    sites[:, 1] += 0.5 * L[1] + origin_bohr[1]
+    sites[:, 2] = np.mod(sites[:, 2] + origin_bohr[2], L[2])
     centers, amps, sigmas = [], [], []
     for c in sites:
         w = rng.uniform(0.3, 0.7)

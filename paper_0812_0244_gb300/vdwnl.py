@@ -71,6 +71,7 @@ class Params:
 
 
 EXPORTS = ["vdw_params_default", "vdw_kernel_table", "vdw_create", "vdw_plan", "vdw_energy_potential",
+           "vdw_plan_batch", "vdw_energy_potential_batched",
            "vdw_energy_potential_fd", "vdw_xc_energy_potential",
            "vdw_energy_potential_host", "vdw_last_invalid_points", "vdw_profile_enable", "vdw_profile_read",
            "vdw_delta_energy_noalloc", "vdw_spectral_gradient", "vdw_learned_param_count", "vdw_learned_load",
@@ -100,6 +101,8 @@ def lib():
     L.vdw_plan.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
     L.vdw_energy_potential.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.vdw_energy_potential_host.argtypes = [vp, fp, fp, dp, fp, vp]
+    L.vdw_plan_batch.argtypes = [vp, ctypes.c_int]
+    L.vdw_energy_potential_batched.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp]
     L.vdw_energy_potential_fd.argtypes = [vp, vp, vp, vp, vp, vp]
     L.vdw_xc_energy_potential.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, vp]
     L.vdw_last_invalid_points.argtypes = [vp, P(ctypes.c_longlong)]
@@ -229,6 +232,28 @@ class VdwNL:
         _check(lib().vdw_energy_potential(self._h, ptr(n), ptr(grad), ptr(E), ptr(v), ptr(w),
                                           _stream_handle(stream)), "vdw_energy_potential")
         return E, v, w
+
+    def plan_batch(self, Bmax):
+        """vdw_plan_batch: workspaces for Bmax densities per call (after plan())."""
+        _check(lib().vdw_plan_batch(self._h, int(Bmax)), "vdw_plan_batch")
+        self.batch_max = int(Bmax)
+        return self
+
+    def energy_potential_batched(self, n, grad, E=None, v=None, stream=None):
+        """vdw_energy_potential_batched on device tensors n (B, N3, N2, N1),
+        grad (B, 3, N3, N2, N1); returns (E (B, 3) float64, v (B, ...) or None)."""
+        import torch
+        B = int(n.shape[0])
+        _cuda_f32(n, (B,) + self.shape)
+        _cuda_f32(grad, (B, 3) + self.shape)
+        if E is None:
+            E = torch.empty((B, 3), dtype=torch.float64, device=n.device)
+        assert E.is_cuda and E.dtype == torch.float64 and E.is_contiguous() and E.numel() >= 3 * B
+        if v is not None:
+            _cuda_f32(v, (B,) + self.shape)
+        _check(lib().vdw_energy_potential_batched(self._h, B, _ptr(n), _ptr(grad), _ptr(E), _ptr(v),
+                                                  _stream_handle(stream)), "vdw_energy_potential_batched")
+        return E, v
 
     def energy_potential_fd(self, n, grad=None, E=None, v=None, stream=None):
         """vdw_energy_potential_fd: central-difference gradient (given, or
@@ -384,15 +409,15 @@ class VdwNL:
                                               _stream_handle(stream)), "vdw_delta_energy_noalloc")
         return dE
 
-    STAGES = ("pointwise", "theta_plane", "pencil_contract", "energy_final", "assemble", "pencil_div",
-              "div_final")
+    STAGES = ("pointwise", "planes_fwd", "pencils_fwd", "contract", "energy_final", "pencils_inv", "planes_inv",
+              "usum", "w_planes", "pencil_div", "div_final")
 
     def profile(self, enable=True):
         _check(lib().vdw_profile_enable(self._h, 1 if enable else 0), "vdw_profile_enable")
 
     def profile_read(self):
         """Stage durations (ms) of the last call, as a dict (skipped stages omitted)."""
-        ms = (ctypes.c_float * 7)()
+        ms = (ctypes.c_float * len(self.STAGES))()
         _check(lib().vdw_profile_read(self._h, ms), "vdw_profile_read")
         return {name: float(t) for name, t in zip(self.STAGES, ms) if t >= 0}
 

@@ -8,16 +8,28 @@ import bench
 
 
 def test_stage_bytes_add_up_to_the_call():
-    """At Nq = 20 on 180 points along x the stages move 766 B per grid point
-    (117 + 160.9 + 161.8 + 298.1 + 16.2 + 12.0), against the 396 B/pt floor."""
+    """At Nq = 20 on 180 points along x: the per-stage algorithmic bytes match
+    the names of the library's stages, the contraction moves the half
+    spectrum in and out once, and the whole call moves more than the
+    396 B/pt floor (the y stage is three passes over the spectrum)."""
+    from paper_0812_0244_gb300 import vdwnl
     sb = bench.stage_bytes_per_point(20, 180)
-    assert set(sb) == {"pointwise", "theta_plane", "pencil_contract", "energy_final", "assemble", "pencil_div",
-                       "div_final"}
+    assert tuple(sb) == vdwnl.VdwNL.STAGES
     h = 91 / 180
     assert sb["pointwise"] == pytest.approx(117)
-    assert sb["pencil_contract"] == pytest.approx(2 * 20 * 8 * h)
-    assert sum(sb.values()) == pytest.approx(766.0, abs=0.1)
+    assert sb["contract"] == pytest.approx(2 * 20 * 8 * h + 4 * h)
+    assert sb["pencils_fwd"] == sb["pencils_inv"] == pytest.approx(2 * 20 * 8 * h)
+    assert sum(sb.values()) == pytest.approx(117 + 160.9 + 3 * 161.8 + 2 + 160.9 + 109 + 28.1 + 16.2 + 12.0, abs=0.2)
     assert bench.b_alg(20) == 396 < sum(sb.values())
+
+
+def test_contraction_flops_and_fp32_peak():
+    """Nq = 20: 210 pair evaluations of 3 FMA, 4 FMA per off-diagonal and 2 per
+    diagonal pair, 2 FMA per field of energy, 2 products per field of
+    scaling: 2980 flops per half-spectrum point; the FP32 peak at 2070 MHz is
+    152 x 128 x 2 x 2.07e9 = 80.5 TFLOP/s."""
+    assert bench.contract_flops_per_point(20, 180) == pytest.approx(2980 * 91 / 180)
+    assert bench.fp32_peak_tflops(2070) == pytest.approx(80.55, abs=0.01)
 
 
 def test_traffic_reported_only_for_matching_sources(tmp_path, monkeypatch):
@@ -28,15 +40,15 @@ def test_traffic_reported_only_for_matching_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     sha = bench.source_sha1()
     (tmp_path / "profiles" / "dram_traffic_dwnt_180x180x72_nq20.txt").write_text(
-        "# comment\nsource_sha1 %s\npencil_contract 123456\n" % sha)
-    assert bench.captured_traffic("pencil_contract") == 123456
-    assert bench.captured_traffic("assemble") is None  # not captured
+        "# comment\nsource_sha1 %s\ncontract 123456\n" % sha)
+    assert bench.captured_traffic("contract") == 123456
+    assert bench.captured_traffic("usum") is None  # not captured
     (csrc / "a.cu").write_text("kernel two")               # sources changed since the capture
     assert bench.source_sha1() != sha
-    assert bench.captured_traffic("pencil_contract") is None
+    assert bench.captured_traffic("contract") is None
 
 
 def test_committed_traffic_file_names_its_sources():
     path = os.path.join(os.path.dirname(bench.__file__), "profiles", "dram_traffic_dwnt_180x180x72_nq20.txt")
     keys = [line.split()[0] for line in open(path) if line.strip() and not line.startswith("#")]
-    assert keys[0] == "source_sha1" and "pencil_contract" in keys
+    assert keys[0] == "source_sha1" and "contract" in keys

@@ -21,17 +21,37 @@ def test_fit_energy_map_recovers_barriers():
     assert f["rms"] < 1e-12
 
 
+def test_translations_are_fractions_of_the_grid_spacing():
+    L = (10.0, 20.0, 30.0)
+    t = scan.translations((6, 8, 10), L, 2)
+    assert len(t) == 8 and t[0] == (0.0, 0.0, 0.0)
+    assert set(round(x[0], 12) for x in t) == {0.0, 0.5}        # h_x = 10 / 10
+    assert set(round(x[1], 12) for x in t) == {0.0, 1.25}       # h_y = 20 / 8
+    assert set(round(x[2], 12) for x in t) == {0.0, 2.5}        # h_z = 30 / 6
+
+
 @pytest.mark.gpu
 @pytest.mark.slow
 def test_scan_energies_match_oracle(table):
+    """Four sampled wall positions of the 180 x 180 x 72 scan: the plain
+    energies (batched entry point) against the FP64 oracle, and the learned
+    energies against the FP64 oracle of the learned basis with the stored
+    model."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import oracle as O
+    import oracle.learned as LO
+    from paper_0812_0244_gb300 import learned as LR
     from paper_0812_0244_gb300 import synthetic as S
     from paper_0812_0244_gb300 import vdwnl
-    res = scan.run(nz=2, nphi=2, learned=False, log=lambda s: None)
-    Ep = np.array(res["E_plain_ha"])
+    res = scan.run(nz=2, nphi=2, grids=(180,), dr_out=(0.0,), sub=1, learned=True, log=lambda s: None)
+    case = res["cases"][0]
+    Ep, El = np.array(case["E_plain_ha"]), np.array(case["E_learned_ha"])
+    mdl = LR.load()
+    mo = LO.random_model(0, J=mdl["J"], k_max=mdl["k_max"], base=mdl["base"]).with_flat(
+        np.asarray(mdl["params"], np.float64))
+    mo.mu1, mo.sig1, mo.mu2, mo.sig2, mo.eps = mdl["feat"]
     z = np.arange(2) * (2.0 * scan.DZ_ANG) / 2
     phi = np.arange(2) * (2.0 * scan.DPHI_DEG) / 2
     ctx = None
@@ -49,3 +69,5 @@ def test_scan_energies_match_oracle(table):
             n = n32.double().cpu().numpy()
             Eo = O.energy(n, g, L, table)
             assert abs(Ep[i, j] - Eo) < 1e-6, (i, j, Ep[i, j], Eo)
+            Elo = LO.energy_potential(n, g, L, mo, table, want_v=False)["E"]
+            assert abs(El[i, j] - Elo) <= 1e-5 * abs(Elo), (i, j, El[i, j], Elo)
