@@ -514,6 +514,32 @@ def main():
     except Exception:
         ag_ms = None
 
+    # several densities per call (NEXT-3): B = 8 tube densities (outer wall
+    # shifted and rotated), one launch per stage for the whole batch
+    batched = None
+    try:
+        Bb = 8
+        nb = []
+        for b in range(Bb):
+            n64b, _, _ = S.tube_density_torch(100 + b, shape=n_h.shape, shift_ang=0.3 * b, rot_deg=4.5 * b,
+                                              device=dev)
+            nb.append(n64b.to(torch.float32))
+        nb = torch.stack(nb).contiguous()
+        gb = torch.stack([ctx.spectral_gradient(nb[b]) for b in range(Bb)]).contiguous()
+        vb = torch.empty_like(nb)
+        Eb = torch.empty((Bb, 3), dtype=torch.float64, device=dev)
+        ctx.plan_batch(Bb)
+        for _ in range(3):
+            ctx.energy_potential_batched(nb, gb, Eb, vb)
+        b_ms = timed(lambda: ctx.energy_potential_batched(nb, gb, Eb, vb), min(K, 50), flush, stream)
+        batched = {"B": Bb, "ms_per_call": b_ms, "ms_per_density": b_ms / Bb,
+                   "value": Bb * N / (b_ms * 1e-3), "unit": UNIT,
+                   "what": "vdw_energy_potential_batched: E and v of 8 tube densities per call"}
+        ctx.plan_batch(1)
+        del nb, gb, vb
+    except Exception as ex:  # reported, never silently replaced
+        batched = {"error": str(ex)[:200]}
+
     # plain potential of the same density, for the learned comparison
     ctx.energy_potential(n, g, E, v)
     v_plain = v.clone()
@@ -573,6 +599,7 @@ def main():
                                         "alone, no pointwise work or contraction; reference only"
                                         % (params.Nq + 3, params.Nq + 1)},
             "learned_m8": learned,
+            "batched_b8": batched,
             "autograd_256x256x96": {"ms_per_step": ag_ms,
                                     "value": (256 * 256 * 96 / (ag_ms * 1e-3)) if ag_ms else None, "unit": UNIT,
                                     "what": "torch.autograd.Function forward (E) + backward (theta recomputed, "

@@ -46,7 +46,8 @@ extern "C" {
 
 /* ---- method parameters --------------------------------------------------
  * Nq, q_c, m_c   interpolation mesh size (paper: "N_alpha ~ 20"), saturation
- *                cutoff and order of Eq. (Sat) ("m_c ~ 12 and q_c ~ 5 a.u.").
+ *                cutoff and order of Eq. (Sat) ("m_c ~ 12 and q_c ~ 5 a.u.");
+ *                m_c <= 32.
  * q_1, lambda    first point and ratio of the logarithmic mesh
  *                (q_{a+1}-q_a) = lambda (q_a - q_{a-1}), q_Nq = q_c.
  * d_s            radius of the soft kernel of Eq. (PhiSoft) in

@@ -226,6 +226,80 @@ def mlp_jacobian(f, jac_bf16=True):
 
 
 # --------------------------------------------------------------------------
+# the network tabulated on a node grid of the two features
+# --------------------------------------------------------------------------
+# The network's output depends on the point only through (x1, x2).  The
+# tabulated form evaluates it once on the nodes x = -D + (i - 1) h, i = 0 ..
+# T + 1, h = 2 D / (T - 1) (T nodes on [-D, D] and one padding node on each
+# side), and a point's outputs are the tensor product of Catmull-Rom cubics
+# in x1 and x2 through the 4 x 4 nodes around it.  That interpolant is C1 and
+# reproduces quadratics; its x derivatives are the Jacobian the potential
+# uses, so v stays the exact derivative of the tabulated E.  Features outside
+# [-D, D] are clamped to it (zero derivative along a clamped axis).
+
+
+@dataclass
+class NetworkTable:
+    T: int
+    D: float
+    vals: np.ndarray  # (M, T + 2, T + 2): vals[m, i1, i2] at (x1, x2) node (i1, i2)
+
+    @property
+    def h(self):
+        return 2.0 * self.D / (self.T - 1)
+
+    def nodes(self):
+        return -self.D + (np.arange(self.T + 2) - 1.0) * self.h
+
+
+def network_table(mdl: LearnedModel, T, D):
+    """The network (mlp_forward, bf16 roundings mirrored) on the (T+2)^2 nodes."""
+    xs = -D + (np.arange(T + 2) - 1.0) * (2.0 * D / (T - 1))
+    X1, X2 = np.meshgrid(xs, xs, indexing="ij")
+    w = mlp_forward(X1.ravel(), X2.ravel(), mdl)["w"]
+    return NetworkTable(T=T, D=float(D), vals=w.reshape(mdl.M, T + 2, T + 2))
+
+
+def catmull_rom(s):
+    """Weights of the nodes i-1, i, i+1, i+2 at local position s in [0, 1] of
+    interval i, and their s derivatives: arrays (4,) + s.shape."""
+    s = np.asarray(s, np.float64)
+    w = np.stack([0.5 * (-s ** 3 + 2 * s ** 2 - s), 0.5 * (3 * s ** 3 - 5 * s ** 2 + 2),
+                  0.5 * (-3 * s ** 3 + 4 * s ** 2 + s), 0.5 * (s ** 3 - s ** 2)])
+    dw = np.stack([0.5 * (-3 * s ** 2 + 4 * s - 1), 0.5 * (9 * s ** 2 - 10 * s),
+                   0.5 * (-9 * s ** 2 + 8 * s + 1), 0.5 * (3 * s ** 2 - 2 * s)])
+    return w, dw
+
+
+def table_eval(tab: NetworkTable, x1, x2):
+    """Outputs o (M, m) and Jacobian J (M, 2, m) at flat feature arrays."""
+    x1 = np.asarray(x1, np.float64)
+    x2 = np.asarray(x2, np.float64)
+    h = tab.h
+    out_c = []
+    for x in (x1, x2):
+        xc = np.clip(x, -tab.D, tab.D)
+        u = (xc + tab.D) / h                      # node index of the interval start, in [0, T-1]
+        i = np.minimum(np.floor(u).astype(np.int64), tab.T - 2)
+        s = u - i
+        w, dw = catmull_rom(s)
+        inside = (x >= -tab.D) & (x <= tab.D)
+        out_c.append((i, w, dw * (inside / h)[None]))
+    (i1, a, da), (i2, b, db) = out_c
+    M = tab.vals.shape[0]
+    o = np.zeros((M, x1.size))
+    j1 = np.zeros((M, x1.size))
+    j2 = np.zeros((M, x1.size))
+    for k in range(4):
+        for l in range(4):
+            v = tab.vals[:, i1 + k, i2 + l]       # padded index: interval i starts at node i + 1
+            o += a[k] * b[l] * v
+            j1 += da[k] * b[l] * v
+            j2 += a[k] * db[l] * v
+    return o, np.stack([j1, j2], axis=1)
+
+
+# --------------------------------------------------------------------------
 # learned kernel
 # --------------------------------------------------------------------------
 
@@ -275,11 +349,13 @@ def kernel_eval(mdl: LearnedModel, kmod):
 
 
 def energy_potential(n, grad, cell, mdl: LearnedModel, T: V.KernelTable, want_v=True, jac_bf16=True,
-                     want_grad=False):
+                     want_grad=False, table: NetworkTable | None = None):
     """E (= E_soft + Delta E), and optionally v and dE/dparams of the learned
     basis on the periodic grid (conventions of the plain oracle: theta(G) =
     (1/N) sum_i theta_i exp(-i G.r_i)).  T supplies the plain method's Delta E
-    (C_s and q0 with its saturation)."""
+    (C_s and q0 with its saturation).  With a network table the outputs and
+    their Jacobian come from its interpolation (table_eval) instead of the
+    network at each point."""
     L = V.check_cell(cell)
     shape = n.shape
     N = n.size
@@ -288,9 +364,14 @@ def energy_potential(n, grad, cell, mdl: LearnedModel, T: V.KernelTable, want_v=
     ft = features(n, grad, mdl, T.p.n_min)
     ok = ft["ok"]
     nn = ft["n"]
-    f = mlp_forward(ft["x1"].ravel(), ft["x2"].ravel(), mdl)
+    if table is None:
+        f = mlp_forward(ft["x1"].ravel(), ft["x2"].ravel(), mdl)
+        o = f["w"]
+    else:
+        assert not want_grad, "parameter gradients are those of the network itself"
+        o, Jt = table_eval(table, ft["x1"].ravel(), ft["x2"].ravel())
     Pb, dPb, dq_dn_b, dq_dg_b = base_basis(n, grad, mdl, T)
-    w = (f["w"].reshape((mdl.M,) + shape) + Pb) * ok[None]
+    w = (o.reshape((mdl.M,) + shape) + Pb) * ok[None]
     theta = nn[None] * w
     th_hat = np.fft.fftn(theta, axes=(1, 2, 3)) / N
     g1, g2, g3 = V.g_vectors(shape, L)
@@ -307,7 +388,7 @@ def energy_potential(n, grad, cell, mdl: LearnedModel, T: V.KernelTable, want_v=
     u = np.real(np.fft.ifftn(u_hat, axes=(1, 2, 3))) * N
     out["u"] = u
     if want_v:
-        Jm = mlp_jacobian(f, jac_bf16)
+        Jm = mlp_jacobian(f, jac_bf16) if table is None else Jt
         c = np.einsum("mjp,mp->jp", Jm, u.reshape(mdl.M, -1)).reshape((2,) + shape)
         S0 = np.sum(u * w, axis=0)
         q4 = np.where(pw["ok"], q ** 4, 1.0)

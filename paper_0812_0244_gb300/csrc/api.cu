@@ -5,12 +5,19 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
 namespace vdw {
 
 static thread_local std::string g_last_error;
+static std::mutex g_smem_mu;
+
+void smem_limit_lock(bool lock) {
+    if (lock) g_smem_mu.lock();
+    else g_smem_mu.unlock();
+}
 
 void set_error(const std::string& s) { g_last_error = s; }
 

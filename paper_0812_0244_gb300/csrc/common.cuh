@@ -28,6 +28,7 @@ enum Stage {
 static_assert(ST_COUNT == VDW_NSTAGES, "stage list");
 
 constexpr int MAX_NQ = 32;     // largest interpolation mesh the kernels take
+constexpr int MAX_MC = 32;     // largest order m_c of the saturation sum of Eq. (Sat)
 constexpr int MAX_DIM = 256;   // largest grid dimension (FFT line length)
 constexpr uint8_t K_INVALID = 255;  // interval code of a point with theta = 0
 
@@ -45,6 +46,7 @@ struct PointParams {
     float q_c;
     float n_min;
     float C_s;
+    float inv_m[MAX_MC + 1];     // 1/m, m = 1 .. m_c (terms of the saturation sum)
     float qm[MAX_NQ];            // q mesh
     float Mq[MAX_NQ][MAX_NQ];    // Mq[a][k]: second derivative of p_a at knot k
 };
@@ -138,6 +140,8 @@ struct vdw_ctx {
     float* d_gs;                // [Npad] |G| of each sorted point, sign = energy weight
     float4* d_Q;                // [Nq/4][Npad][2] field quads of the sorted points
     int batch_max;              // densities the per-density workspaces hold (vdw_plan_batch)
+    int nsm;                    // SMs of the device (persistent grids)
+    int usum_per_sm;            // resident blocks per SM of the field-sum kernel
     // the pointwise pass runs in p0_chunks slabs of p0_nj complex rows (2 p0_nj
     // z values) with nb_p0 blocks each, so that the host entry point can copy
     // slab c + 1 while slab c is processed (nb_point = p0_chunks * nb_p0)
@@ -193,6 +197,26 @@ int alloc_density_work(vdw_ctx* c, int Bmax);
         if (_e != cudaSuccess) return ::vdw::cuda_fail(_e, #call); \
     } while (0)
 
+// Serialises raise_smem_limit across threads (api.cu).
+void smem_limit_lock(bool lock);
+
+// Raises (never lowers) a kernel's dynamic shared-memory limit to bytes.
+// The limit belongs to the kernel, for the whole process, not to a context:
+// contexts of different grids (or learned models of different knot counts)
+// that share a kernel would otherwise lower each other's limit, and their
+// launches would then fail.
+template <class K>
+int raise_smem_limit(K kernel, size_t bytes) {
+    smem_limit_lock(true);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < bytes)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    smem_limit_lock(false);
+    if (e != cudaSuccess) return cuda_fail(e, "raise_smem_limit");
+    return VDW_OK;
+}
+
 // pipeline launchers (pipeline.cu)
 // slab_ready (optional): per slab of the pointwise pass, an event to wait on
 // before processing it (the host entry point's copies)
@@ -230,7 +254,7 @@ int sorted_contract(vdw_ctx* c, double* epart, int write_back, cudaStream_t s, i
 // layout ([nk-1][nq(nq+1)/2] float4 cubic coefficients on a uniform mesh)
 int sorted_contract_table(vdw_ctx* c, int nq, const float4* table, float inv_dk, int nk, double* epart,
                           int write_back, cudaStream_t s, int B = 1);
-constexpr int SORTED_BLOCK = 256;  // sorted points per contraction block
+constexpr int SORTED_BLOCK = 128;  // sorted points per contraction block
 
 // learned reduced basis (learned.cu)
 int learned_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s);

@@ -48,8 +48,9 @@ __global__ void __launch_bounds__(PEN_THREADS) k_pencil_fwd(const float2* __rest
                                                             long long qstride, int C) {
     extern __shared__ float2 sm[];
     const int N2 = CN2 > 0 ? CN2 : g.N2;
-    float2* lines = sm;  // [4][C][N2]
-    Tw* tw2 = twiddles_after(lines, (size_t)(4 * C * N2));
+    const int S = pencil_stride(N2);
+    float2* lines = sm;  // [4][C][S]
+    Tw* tw2 = twiddles_after(lines, (size_t)(4 * C * S));
     load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C, q = blockIdx.y;
     spec += blockIdx.z * g.bs_spec;  // density blockIdx.z of a batch
@@ -64,21 +65,21 @@ __global__ void __launch_bounds__(PEN_THREADS) k_pencil_fwd(const float2* __rest
         const int a = sdiv(r, sN2), y = r - a * N2;
         const int col = c0 + cc;
         const bool ok = col < g.ncols;
-        cp_async8(lines + (a * C + cc) * N2 + y, ok ? src + (long long)r * g.ncols + col : src, ok);
+        cp_async8(lines + (a * C + cc) * S + y, ok ? src + (long long)r * g.ncols + col : src, ok);
     }
     cp_async_wait_all();
     __syncthreads();
-    pencils_fft<CN2, false>(lines, 4 * C, N2, g.p2, tw2);
+    pencils_fft<CN2, false>(lines, 4 * C, N2, g.p2, tw2, S);
     __syncthreads();
     float4* Qq = Q + q * qstride;
-    const int LS = C * N2;
+    const int LS = C * S;
 #pragma unroll 4
     for (int task = threadIdx.x; task < C * N2; task += blockDim.x) {
         const int cc = sdiv(task, sN2), y = task - cc * N2;
         const int col = c0 + cc;
         if (col >= g.ncols) continue;
         const long long p = pos[(long long)col * N2 + y];
-        const float2* l = lines + cc * N2 + y;
+        const float2* l = lines + cc * S + y;
         const float2 v0 = l[0], v1 = l[LS], v2 = l[2 * LS], v3 = l[3 * LS];
         Qq[2 * p] = make_float4(v0.x, v0.y, v1.x, v1.y);
         Qq[2 * p + 1] = make_float4(v2.x, v2.y, v3.x, v3.y);
@@ -95,15 +96,16 @@ __global__ void __launch_bounds__(PEN_THREADS) k_pencil_inv(float2* __restrict__
                                                             const float4* __restrict__ Q, long long qstride, int C) {
     extern __shared__ float2 sm[];
     const int N2 = CN2 > 0 ? CN2 : g.N2;
-    float2* lines = sm;  // [4][C][N2]
-    float2* tw2 = twiddles_after<float2>(lines, (size_t)(4 * C * N2));
+    const int S = pencil_stride(N2);
+    float2* lines = sm;  // [4][C][S]
+    float2* tw2 = twiddles_after<float2>(lines, (size_t)(4 * C * S));
     load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C, q = blockIdx.y;
     spec += blockIdx.z * g.bs_spec;  // density blockIdx.z of a batch
     Q += blockIdx.z * g.bs_Q;
     const SmallDiv sC = small_div(C), sN2 = small_div(N2);
     const float2* Qq = reinterpret_cast<const float2*>(Q + q * qstride);
-    const int LS = C * N2;
+    const int LS = C * S;
     // the four values of a point go to four lines: 8-byte asynchronous copies
 #pragma unroll 4
     for (int task = threadIdx.x; task < C * N2; task += blockDim.x) {
@@ -111,13 +113,13 @@ __global__ void __launch_bounds__(PEN_THREADS) k_pencil_inv(float2* __restrict__
         const int col = c0 + cc;
         const bool ok = col < g.ncols;
         const long long p = ok ? (long long)pos[(long long)col * N2 + y] : 0;
-        float2* l = lines + cc * N2 + y;
+        float2* l = lines + cc * S + y;
 #pragma unroll
         for (int a = 0; a < 4; ++a) cp_async8(l + a * LS, Qq + 4 * p + a, ok);
     }
     cp_async_wait_all();
     __syncthreads();
-    pencils_fft<CN2, true>(lines, 4 * C, N2, g.p2, tw2);
+    pencils_fft<CN2, true>(lines, 4 * C, N2, g.p2, tw2, S);
     __syncthreads();
     float2* dst = spec + (long long)4 * q * N2 * g.ncols;
     const int tot = 4 * N2 * C;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(PEN_THREADS) k_pencil_inv(float2* __restrict__
         const int r = sdiv(i, sC), cc = i - r * C;
         const int a = sdiv(r, sN2), y = r - a * N2;
         const int col = c0 + cc;
-        if (col < g.ncols) dst[(long long)r * g.ncols + col] = lines[(a * C + cc) * N2 + y];
+        if (col < g.ncols) dst[(long long)r * g.ncols + col] = lines[(a * C + cc) * S + y];
     }
 }
 
@@ -167,7 +169,7 @@ __device__ __forceinline__ void pair_loop(const float4* cf, float t, const float
 }
 
 template <int NQ>
-__global__ void __launch_bounds__(SORT_THREADS, 2) k_contract_sorted(float4* __restrict__ Q, long long qstride,
+__global__ void __launch_bounds__(SORT_THREADS, 4) k_contract_sorted(float4* __restrict__ Q, long long qstride,
                                                                     const float* __restrict__ gs,
                                                                     const float4* __restrict__ kcoef, float inv_dk,
                                                                     int Nk, float invN, double* __restrict__ epart,
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) k_contract_sorted(float4* __r
 // host side
 // ---------------------------------------------------------------------------
 size_t sorted_pencil_smem(const GridArgs& g) {
-    return sizeof(float2) * tw_offset((size_t)4 * PEN_COLS * g.N2) + sizeof(Tw) * g.N2;
+    return sizeof(float2) * tw_offset((size_t)4 * PEN_COLS * pencil_stride(g.N2)) + sizeof(Tw) * g.N2;
 }
 
 // |G| order of the half spectrum: pos[col N2 + y] = sorted position of the
@@ -288,8 +290,12 @@ void sorted_free(vdw_ctx* c) {
 template <int CN2>
 static int configure_sorted_sized(vdw_ctx* c) {
     const int sm = (int)sorted_pencil_smem(c->g);
-    VDW_CUDA(cudaFuncSetAttribute(k_pencil_fwd<CN2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    VDW_CUDA(cudaFuncSetAttribute(k_pencil_inv<CN2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    int rc = raise_smem_limit(k_pencil_fwd<CN2>, sm);
+    if (!rc) rc = raise_smem_limit(k_pencil_inv<CN2>, sm);
+    if (rc) return rc;
+    int dev = 0;
+    VDW_CUDA(cudaGetDevice(&dev));
+    VDW_CUDA(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
     return VDW_OK;
 }
 
@@ -342,7 +348,7 @@ int sorted_contract_table(vdw_ctx* c, int nq, const float4* table, float inv_dk,
                           int write_back, cudaStream_t s, int B) {
     const GridArgs& g = c->g;
     const long long qs = 2 * c->Npad;
-#define VDW_CONTRACT(NQ)                                                                                         \
+#define VDW_CONTRACT(NQ)                                                                                  \
     k_contract_sorted<NQ><<<dim3(c->nb_sorted, B), SORT_THREADS, 0, s>>>(c->d_Q, qs, c->d_gs, table, inv_dk, nk, \
                                                                          g.invN, epart, write_back, g.bs_Q,      \
                                                                          g.bs_epart)

@@ -1048,8 +1048,7 @@ int set_smem(K kernel, size_t bytes, const char* name) {
         set_error(std::string(name) + ": shared memory beyond the limit");
         return VDW_ERR_SIZE;
     }
-    VDW_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    return VDW_OK;
+    return raise_smem_limit(kernel, bytes);
 }
 
 template <int CN1, int CN2, int CN3>
@@ -1071,7 +1070,7 @@ int configure_all(vdw_ctx* c) {
     return configure<0, 0, 0>(c);
 }
 
-// learned scratch: partial sums [N2 * 8 + ncols]
+// learned scratch: partial sums [N2 * 8 + nb_sorted]
 double* lrn_epart(vdw_ctx* c) {
     return reinterpret_cast<double*>(static_cast<unsigned char*>(c->d_lrn) + 0);
 }
@@ -1199,7 +1198,7 @@ bool lrn_ready(vdw_ctx* c) {
 struct LrnLayout {
     size_t epart, w1, b1, b2, b3, w2r, w3r, w2f, w3f, knots, err, gK, total;
 };
-static LrnLayout lrn_layout(const GridArgs& g, int J) {
+static LrnLayout lrn_layout(const GridArgs& g, int J, int nb_sorted) {
     LrnLayout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -1207,7 +1206,9 @@ static LrnLayout lrn_layout(const GridArgs& g, int J) {
         o = (o + bytes + 255) & ~(size_t)255;
         return at;
     };
-    L.epart = take(sizeof(double) * ((size_t)g.N2 * L_SLOTS + g.ncols + 1));
+    // energy partials: the network blocks (at most N2 L_SLOTS), then the
+    // contraction's blocks over the sorted points
+    L.epart = take(sizeof(double) * ((size_t)g.N2 * L_SLOTS + (size_t)nb_sorted + 1));
     L.w1 = take(sizeof(float) * 2 * LRN_H);
     L.b1 = take(sizeof(float) * LRN_H);
     L.b2 = take(sizeof(float) * LRN_H);
@@ -1269,7 +1270,7 @@ int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], do
     if (!c->d_lrn || c->lrn_J != J) {
         cudaFree(c->d_lrn);
         c->d_lrn = nullptr;
-        const LrnLayout L = lrn_layout(g, J);
+        const LrnLayout L = lrn_layout(g, J, c->nb_sorted);
         VDW_CUDA(cudaMalloc(&c->d_lrn, L.total));
         VDW_CUDA(cudaMemset(c->d_lrn, 0, L.total));
         unsigned char* b = static_cast<unsigned char*>(c->d_lrn);
@@ -1356,7 +1357,7 @@ int vdw_learned_fit_grad(vdw_handle c, const float* n, const float* grad, const 
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    VDW_CUDA(cudaFuncSetAttribute(k_learned_param_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pgrad()));
+    if (const int rs = raise_smem_limit(k_learned_param_grad, smem_pgrad())) return rs;
     k_learned_param_grad<<<nsm, PG_THREADS, smem_pgrad(), (cudaStream_t)stream>>>(
         n, grad, c->g.N, c->pp.n_min, c->la, target, weight, 1, (float)coef, g_params);
     VDW_CUDA(cudaGetLastError());
@@ -1367,7 +1368,7 @@ int vdw_learned_channels(vdw_handle c, const float* n, const float* grad, float*
     if (!c || !n || !grad || !w_out) return VDW_ERR_ARG;
     if (!lrn_ready(c)) return VDW_ERR_STATE;
     const size_t sm = sizeof(MlpShared) + 2 * sizeof(MlpWG);
-    VDW_CUDA(cudaFuncSetAttribute(k_learned_channels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (const int rs = raise_smem_limit(k_learned_channels, sm)) return rs;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

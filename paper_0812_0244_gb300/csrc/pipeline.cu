@@ -345,8 +345,9 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
                                                        const Tw* __restrict__ tw, int C) {
     extern __shared__ float2 sm[];
     const int N2 = CN2 > 0 ? CN2 : g.N2;
-    float2* lines = sm;  // [3][C][N2]
-    float2* tw2 = twiddles_after<float2>(lines, (size_t)(3 * C * N2));
+    const int S = pencil_stride(N2);
+    float2* lines = sm;  // [3][C][S]
+    float2* tw2 = twiddles_after<float2>(lines, (size_t)(3 * C * S));
     wspec += blockIdx.y * g.bs_wspec;  // density blockIdx.y of a batch
     load_line_twiddles<CN2>(tw2, tw + g.N1, N2);
     const int c0 = blockIdx.x * C;
@@ -356,11 +357,11 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
         const int r = sdiv(i, sC), cc = i - r * C, yy = r % N2, c = r / N2;
         const int col = c0 + cc;
         const bool ok = col < g.ncols;
-        cp_async8(lines + (c * C + cc) * N2 + yy, ok ? wspec + ((long long)c * N2 + yy) * g.ncols + col : wspec, ok);
+        cp_async8(lines + (c * C + cc) * S + yy, ok ? wspec + ((long long)c * N2 + yy) * g.ncols + col : wspec, ok);
     }
     cp_async_wait_all();
     __syncthreads();
-    pencils_fft<CN2, false>(lines, 3 * C, N2, g.p2, tw2);
+    pencils_fft<CN2, false>(lines, 3 * C, N2, g.p2, tw2, S);
     __syncthreads();
     for (int pt = threadIdx.x; pt < C * N2; pt += blockDim.x) {
         const int cc = pt / N2, yy = pt % N2;
@@ -371,22 +372,22 @@ __global__ void __launch_bounds__(256, 2) k_pencil_div(float2* __restrict__ wspe
         const int mx = (2 * kx == g.N1) ? 0 : kx;
         const int my = (2 * yy == N2) ? 0 : ((2 * yy < N2) ? yy : yy - N2);
         const int mz = (2 * kz == g.N3) ? 0 : ((2 * kz < g.N3) ? kz : kz - g.N3);
-        const float2 wx = lines[(0 * C + cc) * N2 + yy];
-        const float2 wy = lines[(1 * C + cc) * N2 + yy];
-        const float2 wz = lines[(2 * C + cc) * N2 + yy];
+        const float2 wx = lines[(0 * C + cc) * S + yy];
+        const float2 wy = lines[(1 * C + cc) * S + yy];
+        const float2 wz = lines[(2 * C + cc) * S + yy];
         const float Gx = g.gx * mx, Gy = g.gy * my, Gz = g.gz * mz;
         // i G . w / N
         const float re = Gx * wx.x + Gy * wy.x + Gz * wz.x;
         const float im = Gx * wx.y + Gy * wy.y + Gz * wz.y;
-        lines[(0 * C + cc) * N2 + yy] = make_float2(-im * g.invN, re * g.invN);
+        lines[(0 * C + cc) * S + yy] = make_float2(-im * g.invN, re * g.invN);
     }
     __syncthreads();
-    pencils_fft<CN2, true>(lines, C, N2, g.p2, tw2);
+    pencils_fft<CN2, true>(lines, C, N2, g.p2, tw2, S);
     __syncthreads();
     for (int i = threadIdx.x; i < N2 * C; i += blockDim.x) {
         const int yy = sdiv(i, sC), cc = i - yy * C;
         const int col = c0 + cc;
-        if (col < g.ncols) wspec[(long long)yy * g.ncols + col] = lines[cc * N2 + yy];
+        if (col < g.ncols) wspec[(long long)yy * g.ncols + col] = lines[cc * S + yy];
     }
 }
 
@@ -540,14 +541,29 @@ __global__ void k_xc_final(const double* __restrict__ Enl, const double* __restr
 // ---------------------------------------------------------------------------
 // energy: fixed-order FP64 reduction of the block partials
 // ---------------------------------------------------------------------------
-__global__ void k_energy_final(const double* __restrict__ epart, int nb0, int nb2, double s0, double s2,
-                               double* __restrict__ E, int bs_epart) {
+// Fixed order: thread i sums entries i, i + 4 B, i + 8 B, ... into four
+// interleaved accumulators (B threads), then the block sum.
+__device__ __forceinline__ double strided_sum4(const double* __restrict__ p, int n) {
+    const int B = blockDim.x;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += 4 * B) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i + k * B < n) a[k] += p[i + k * B];
+    }
+    return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
+constexpr int ENERGY_THREADS = 1024;
+
+__global__ void __launch_bounds__(ENERGY_THREADS) k_energy_final(const double* __restrict__ epart, int nb0, int nb2,
+                                                                 double s0, double s2, double* __restrict__ E,
+                                                                 int bs_epart) {
     __shared__ double red[32];
     epart += (long long)blockIdx.x * bs_epart;  // density blockIdx.x of a batch
     E += 3 * blockIdx.x;
-    double a0 = 0.0, a2 = 0.0;
-    for (int i = threadIdx.x; i < nb0; i += blockDim.x) a0 += epart[i];
-    for (int i = threadIdx.x; i < nb2; i += blockDim.x) a2 += epart[nb0 + i];
+    const double a0 = strided_sum4(epart, nb0);
+    const double a2 = strided_sum4(epart + nb0, nb2);
     const double t0 = block_sum(a0, red);
     __syncthreads();
     const double t2 = block_sum(a2, red);
@@ -587,7 +603,7 @@ static size_t smem_plane(const GridArgs& g) {
     return sizeof(float2) * tw_offset((size_t)g.N3 * g.Nh) + sizeof(Tw) * (g.N1 + g.N3);
 }
 static size_t smem_pencil(const GridArgs& g, int nq, int C) {
-    return sizeof(float2) * tw_offset((size_t)nq * C * g.N2) + sizeof(Tw) * g.N2;
+    return sizeof(float2) * tw_offset((size_t)nq * C * pencil_stride(g.N2)) + sizeof(Tw) * g.N2;
 }
 static size_t smem_pencil_run(const GridArgs& g, int nq, int C) { return smem_pencil(g, nq, C); }
 
@@ -631,13 +647,19 @@ int pipeline_stencil_gradient(vdw_ctx* c, const float* f, float* grad, cudaStrea
     return VDW_OK;
 }
 
-static int u_sum_blocks(const GridArgs& g) { return (int)std::min<long long>((g.N + USUM_THREADS - 1) / USUM_THREADS, 1 << 16); }
+// one wave of resident blocks, each thread striding over several points: the
+// spline table is staged once per block
+static int u_sum_blocks(const vdw_ctx* c) {
+    const GridArgs& g = c->g;
+    return (int)std::min<long long>((g.N + USUM_THREADS - 1) / USUM_THREADS,
+                                    (long long)std::max(c->usum_per_sm, 1) * std::max(c->nsm, 1));
+}
 
 static int launch_u_sum(vdw_ctx* c, const float* n, const float* grad, float* v, float* w, int mode, cudaStream_t s,
                         int B) {
     const GridArgs& g = c->g;
     const float* uf = reinterpret_cast<const float*>(c->d_spec);
-    const int nb = u_sum_blocks(g);
+    const int nb = u_sum_blocks(c);
 #define VDW_U_SUM(NQ) \
     k_u_sum<NQ><<<dim3(nb, B), USUM_THREADS, 0, s>>>(uf, grad, c->d_t, c->d_k, c->d_aux, g, c->pp, v, w, c->d_gg, mode)
     switch (c->pp.Nq) {
@@ -705,7 +727,7 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
     if (E) {
         const double Omega = c->L[0] * c->L[1] * c->L[2];
         const double Nd = (double)g.N;
-        k_energy_final<<<B, 256, 0, s>>>(c->d_epart, c->nb_point, c->nb_sorted, Omega / Nd,
+        k_energy_final<<<B, ENERGY_THREADS, 0, s>>>(c->d_epart, c->nb_point, c->nb_sorted, Omega / Nd,
                                          0.5 * Omega / (Nd * Nd), E, g.bs_epart);
         mark(ST_ENERGY);
     }
@@ -749,7 +771,7 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
 // it will be launched with fits its register use.
 template <class K>
 static int set_and_check(K kernel, const char* name, int smem, int threads) {
-    VDW_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (const int rs = raise_smem_limit(kernel, (size_t)smem)) return rs;
     cudaFuncAttributes fa;
     VDW_CUDA(cudaFuncGetAttributes(&fa, kernel));
     if (fa.maxThreadsPerBlock < threads) {
@@ -772,7 +794,18 @@ static int configure_sized(vdw_ctx* c) {
     if (!rc) rc = set_and_check(k_div_final<CN1, CN3>, "k_div_final", sp, PLANE_THREADS);
     if (!rc) rc = set_and_check(k_w_planes<CN1, CN3>, "k_w_planes", sp, PLANE_THREADS);
     if (rc) return rc;
-    return sorted_configure(c);
+    rc = sorted_configure(c);
+    if (rc) return rc;
+    // resident blocks per SM of the field sum (its grid is one wave of them)
+    int per_sm = 0;
+    switch (c->p.Nq) {
+        case 20: VDW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_u_sum<20>, USUM_THREADS, 0)); break;
+        case 16: VDW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_u_sum<16>, USUM_THREADS, 0)); break;
+        case 12: VDW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_u_sum<12>, USUM_THREADS, 0)); break;
+        default: VDW_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_u_sum<8>, USUM_THREADS, 0));
+    }
+    c->usum_per_sm = per_sm;
+    return VDW_OK;
 }
 
 int pipeline_configure(vdw_ctx* c) {
@@ -837,7 +870,7 @@ int pipeline_divergence(vdw_ctx* c, float* v, cudaStream_t s) {
 int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, double* E, cudaStream_t s) {
     const double Omega = c->L[0] * c->L[1] * c->L[2];
     const double Nd = (double)c->g.N;
-    k_energy_final<<<1, 256, 0, s>>>(epart, nb0, nb2, Omega / Nd, 0.5 * Omega / (Nd * Nd), E, 0);
+    k_energy_final<<<1, ENERGY_THREADS, 0, s>>>(epart, nb0, nb2, Omega / Nd, 0.5 * Omega / (Nd * Nd), E, 0);
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
 }

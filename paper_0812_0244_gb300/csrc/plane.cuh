@@ -86,19 +86,28 @@ __device__ __forceinline__ void columns_fft(float2* plane, int Nh, const LinePla
     }
 }
 
-// contiguous lines of length N2 (pencils), several lines per warp for short lines
+// lines of length N2 (pencils) at a stride of ls values (ls = N2: contiguous),
+// several lines per warp for short lines
 template <int CN, bool INV, class W>
-__device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, const LinePlan& pl, const W* tw) {
+__device__ __forceinline__ void pencils_fft(float2* lines, int nlines, int N2, const LinePlan& pl, const W* tw,
+                                            int ls = 0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (ls == 0) ls = N2;
     if constexpr (CN > 0) {
         constexpr int L = ct_lines_per_warp(CN);
         const int full = (nlines / L) * L;
-        for (int l = warp * L; l < full; l += nw * L) ct_fft<CN, L, INV>(lines + l * CN, 1, CN, tw, lane);
-        for (int l = full + warp; l < nlines; l += nw) ct_fft<CN, 1, INV>(lines + l * CN, 1, 0, tw, lane);
+        for (int l = warp * L; l < full; l += nw * L) ct_fft<CN, L, INV>(lines + l * ls, 1, ls, tw, lane);
+        for (int l = full + warp; l < nlines; l += nw) ct_fft<CN, 1, INV>(lines + l * ls, 1, 0, tw, lane);
     } else {
-        for (int l = warp; l < nlines; l += nw) line_fft<INV>(lines + l * N2, 1, pl, tw, lane);
+        for (int l = warp; l < nlines; l += nw) line_fft<INV>(lines + l * ls, 1, pl, tw, lane);
     }
 }
+
+// Line stride of the pencil kernels' shared-memory lines [field][column][y]:
+// the staging loops give the 16 lanes of a half-warp 8 columns x 2 rows, at
+// (column S + y) float2 values; with S = 2 (mod 16) those are the 16
+// distinct 8-byte banks.
+__host__ __device__ __forceinline__ int pencil_stride(int N2) { return N2 + ((2 - N2) % 16 + 16) % 16; }
 
 // ---------------------------------------------------------------------------
 // plane helpers (one y plane, N3 rows of N1 reals <-> N3 x Nh half spectrum)

@@ -60,7 +60,7 @@ __device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz,
         for (int m = 1; m <= P.m_c; ++m) {
             dS += yp;
             yp *= y;
-            S = fmaf(yp, __frcp_rn((float)m), S);
+            S = fmaf(yp, P.inv_m[m], S);
         }
         // 1 - exp(-S) through expm1: no cancellation for small q0
         const float em1 = expm1f(-S);

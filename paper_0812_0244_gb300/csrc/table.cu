@@ -370,7 +370,7 @@ struct DevBuf {
 
 int check_params(const vdw_params* p) {
     if (!p) return VDW_ERR_ARG;
-    if (p->Nq < 4 || p->Nq > MAX_NQ || p->q_1 <= 0 || p->q_c <= p->q_1 || p->lambda <= 1.0 || p->m_c < 1 ||
+    if (p->Nq < 4 || p->Nq > MAX_NQ || p->q_1 <= 0 || p->q_c <= p->q_1 || p->lambda <= 1.0 || p->m_c < 1 || p->m_c > MAX_MC ||
         p->d_s <= 0 || p->na < 8 || p->na > 4096 || p->a_max <= 0 || p->d_asym <= p->d_s || p->r_c <= 0 ||
         p->Nr < 2 || (p->Nr & 1) || p->k_max <= 0 || p->Nk < 4 || p->n_cs < 2 || !(p->n_min >= 0))
         return VDW_ERR_ARG;
@@ -444,8 +444,8 @@ int table_build(const vdw_params* p, double* h_qmesh, double* h_phik, double* h_
     k_dion_nodes<<<(na + 255) / 256, 256>>>(d_a, d_wa, na, d_c, d_j0, d_k);
     Nodes nd{d_a, d_c, d_j0, d_k, na};
     const size_t smq = sizeof(double) * 7 * na;
-    cudaFuncSetAttribute(k_dion_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
-    cudaFuncSetAttribute(k_phi_r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
+    raise_smem_limit(k_dion_points, smq);
+    raise_smem_limit(k_phi_r, smq);
     k_dion_points<<<npairs + 1, 128, smq>>>(d_pd1, d_pd2, npairs + 1, nd, d_F, d_dF);
     k_soft_coeffs<<<1, 256>>>(d_F, d_dF, npairs, p->d_s, d_phi0, d_phi2, d_phi4);
     const double dr = p->r_c / Nr;
@@ -453,7 +453,7 @@ int table_build(const vdw_params* p, double* h_qmesh, double* h_phik, double* h_
                                                 d_phir);
     const double dk = p->k_max / (Nk - 1);
     const size_t smj = sizeof(double) * (Nr + 1);
-    cudaFuncSetAttribute(k_radial_ft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj);
+    raise_smem_limit(k_radial_ft, smj);
     k_radial_ft<<<Nk, 256, smj>>>(d_phir, npairs, Nr, dr, dk, d_phik);
     k_dion_points<<<p->n_cs, 128, smq>>>(d_cx, d_cx, p->n_cs, nd, d_cphi, nullptr);
     k_softening<<<1, 256>>>(d_cx, d_cw, d_cphi, p->n_cs, d_phi0, d_phi2, d_phi4, d_Cs);
@@ -502,8 +502,13 @@ int table_upload(vdw_ctx* c, const double* h_phik, double C_s) {
     std::vector<double> M((size_t)Nq * Nq);
     VDW_CUDA(cudaMemcpy(M.data(), d_M, sizeof(double) * M.size(), cudaMemcpyDeviceToHost));
     PointParams& P = c->pp;
+    if (p->m_c < 1 || p->m_c > MAX_MC) {
+        set_error("m_c must be in [1, 32]");
+        return VDW_ERR_ARG;
+    }
     P.Nq = Nq;
     P.m_c = p->m_c;
+    for (int m = 0; m <= MAX_MC; ++m) P.inv_m[m] = m > 0 ? 1.0f / (float)m : 0.f;  // correctly rounded
     P.q_c = (float)p->q_c;
     P.n_min = (float)p->n_min;
     P.C_s = (float)C_s;

@@ -203,3 +203,25 @@ def test_xc_functional_matches_oracle(torch_cuda, table, fd):
     assert abs(E[0] - ref["E_xc"]) <= 1e-6 * abs(ref["E_xc"])
     vv = v.cpu().numpy()
     assert np.abs(vv - ref["v"]).max() <= V_REL * np.abs(ref["v"]).max()
+
+
+def test_two_live_contexts_of_different_grids(torch_cuda, vd, table):
+    """The dynamic shared-memory limit of a kernel is process-wide: a context
+    planned for a smaller grid after one for a larger grid (both on the
+    runtime-length kernels) must not lower the larger one's limit.  Both keep
+    working, interleaved, and match the oracle."""
+    torch = torch_cuda
+    big = S.two_atom_density(5, shape=(30, 36, 40))
+    small = S.two_atom_density(6, shape=(8, 10, 12))
+    cb = vd.VdwNL(vd.Params()).plan(big["n"].shape, big["L"])
+    cs = vd.VdwNL(vd.Params()).plan(small["n"].shape, small["L"])
+    for _ in range(2):
+        for c, d in ((cb, big), (cs, small)):
+            n, g = f32(d["n"]), f32(d["grad"])
+            E, v, _ = c.compute(torch.tensor(np.asarray(n, np.float32), device="cuda"),
+                                torch.tensor(np.asarray(g, np.float32), device="cuda"))
+            torch.cuda.synchronize()
+            ref = O.energy_potential(n, g, d["L"], table)
+            assert abs(float(E[0]) - ref["E"]) <= E_TOL
+            vv = v.cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(vv - ref["v"])) <= V_REL * np.abs(ref["v"]).max()

@@ -259,3 +259,85 @@ def test_spline_base_reproduces_plain_method_basis(table):
     T8 = O.KernelTable(p=p8, qm=qm, Mq=O.cardinal_M(qm), phi0=0.0, C_s=table.C_s, k=None, phik=None)
     pw = O.pointwise(n, g, T8)
     np.testing.assert_allclose(r["theta"], pw["theta"], rtol=1e-12, atol=1e-15)
+
+
+def test_catmull_rom_weights_reproduce_quadratics():
+    """The Catmull-Rom weights of nodes -1, 0, 1, 2 at s in [0, 1]: a partition
+    of unity whose interpolant and s derivative are exact for polynomials of
+    degree up to two, and which passes through nodes 0 and 1."""
+    s = np.linspace(0.0, 1.0, 101)
+    w, dw = LO.catmull_rom(s)
+    np.testing.assert_allclose(w.sum(0), 1.0, atol=1e-14)
+    np.testing.assert_allclose(dw.sum(0), 0.0, atol=1e-13)
+    nodes = np.array([-1.0, 0.0, 1.0, 2.0])
+    for f, df in ((lambda x: 0 * x + 1.0, lambda x: 0 * x), (lambda x: x, lambda x: 0 * x + 1.0),
+                  (lambda x: 3 - 2 * x + 0.5 * x * x, lambda x: -2 + x)):
+        np.testing.assert_allclose((w * f(nodes)[:, None]).sum(0), f(s), atol=1e-13)
+        np.testing.assert_allclose((dw * f(nodes)[:, None]).sum(0), df(s), atol=1e-12)
+    np.testing.assert_allclose(w[:, 0], [0, 1, 0, 0], atol=1e-15)
+    np.testing.assert_allclose(w[:, -1], [0, 0, 1, 0], atol=1e-15)
+
+
+def test_network_table_reproduces_quadratics_and_clamps():
+    """A table filled from biquadratic functions (one per channel) gives them
+    and their gradients back exactly inside [-D, D]; outside, the feature is
+    clamped to the edge and the derivative along that axis is zero."""
+    T, D, M = 17, 3.0, 3
+    xs = -D + (np.arange(T + 2) - 1.0) * (2.0 * D / (T - 1))
+    X1, X2 = np.meshgrid(xs, xs, indexing="ij")
+    coef = np.array([[0.3, 1.0, -2.0, 0.5, -0.25, 0.7], [-1.0, 0.2, 0.4, -0.3, 0.1, 0.05], [2.0, 0, 0, 1.0, 0, 0]])
+
+    def g(c, a, b):
+        return c[0] + c[1] * a + c[2] * b + c[3] * a * b + c[4] * a * a + c[5] * b * b
+
+    def dg(c, a, b):
+        return c[1] + c[3] * b + 2 * c[4] * a, c[2] + c[3] * a + 2 * c[5] * b
+
+    tab = LO.NetworkTable(T=T, D=D, vals=np.stack([g(c, X1, X2) for c in coef]))
+    rng = np.random.default_rng(5)
+    a, b = rng.uniform(-D, D, 200), rng.uniform(-D, D, 200)
+    o, J = tab_eval = LO.table_eval(tab, a, b)
+    for m, c in enumerate(coef):
+        np.testing.assert_allclose(o[m], g(c, a, b), atol=1e-12)
+        d1, d2 = dg(c, a, b)
+        np.testing.assert_allclose(J[m, 0], d1, atol=1e-11)
+        np.testing.assert_allclose(J[m, 1], d2, atol=1e-11)
+    o2, J2 = LO.table_eval(tab, np.array([D + 1.0, 0.3]), np.array([0.2, -D - 2.0]))
+    for m, c in enumerate(coef):
+        np.testing.assert_allclose(o2[m], g(c, np.array([D, 0.3]), np.array([0.2, -D])), atol=1e-12)
+        np.testing.assert_allclose(J2[m, 0], [0.0, dg(c, 0.3, -D)[0]], atol=1e-11)
+        np.testing.assert_allclose(J2[m, 1], [dg(c, D, 0.2)[1], 0.0], atol=1e-11)
+
+
+def test_tabulated_potential_matches_finite_differences(table, monkeypatch):
+    """With the network tabulated, E is smooth in n even with the bf16
+    roundings of the network (the table is fixed): v = dE/dn_i / dOmega by
+    central differences at seeded points.  With the roundings off (the network
+    then smooth) the tabulated outputs converge to the network's at third
+    order in the node spacing h."""
+    n, g, L = _tiny()
+    mdl = LO.random_model(6, base=(0.6, 1.45))
+    tab = LO.network_table(mdl, 129, 8.0)
+    r = LO.energy_potential(n, g, L, mdl, table, table=tab)
+    dOmega = float(np.prod(L)) / n.size
+    rng = np.random.default_rng(4)
+    vmax = np.abs(r["v"]).max()
+    for i in rng.choice(n.size, 6, replace=False):
+        pt = np.unravel_index(i, n.shape)
+        h = 1e-4 * n[pt]
+        m1, m2 = n.copy(), n.copy()
+        m1[pt] += h
+        m2[pt] -= h
+        E1 = LO.energy_potential(m1, O.spectral_gradient(m1, L), L, mdl, table, want_v=False, table=tab)["E"]
+        E2 = LO.energy_potential(m2, O.spectral_gradient(m2, L), L, mdl, table, want_v=False, table=tab)["E"]
+        fd = (E1 - E2) / (2 * h) / dOmega
+        assert abs(fd - r["v"][pt]) < 1e-6 * vmax, (pt, fd, r["v"][pt])
+    monkeypatch.setattr(LO, "bf16_round", lambda a: np.asarray(a, np.float64))
+    ft = LO.features(n, g, mdl, 1e-12)
+    od = LO.mlp_forward(ft["x1"].ravel(), ft["x2"].ravel(), mdl)["w"]
+    errs = []
+    for T in (65, 129, 257):
+        ot, _ = LO.table_eval(LO.network_table(mdl, T, 8.0), ft["x1"].ravel(), ft["x2"].ravel())
+        errs.append(np.abs(ot - od).max())
+    assert errs[1] < errs[0] / 5 and errs[2] < errs[1] / 5, errs
+    assert errs[2] < 1e-4 * np.abs(od).max(), errs
