@@ -288,6 +288,13 @@ def learned_leg(ctx, n, g, E, v, flush, stream, K, E_plain, v_plain, natoms, ms_
         feat, base, kind = (-8.0, 4.0, 2.0, 3.0, 0.1), (LR.Q1_8, LR.LAM_8), "untrained initialisation"
         J, kmax = LR.J_KNOTS, LR.K_MAX
     ctx.learned_load(params, J, kmax, feat, base)
+    # the network itself at every point (the training form), for reference
+    for _ in range(3):
+        ctx.learned_energy_potential(n, g, E, v)
+    ms_direct = timed(lambda: ctx.learned_energy_potential(n, g, E, v), min(K, 20), flush, stream)
+    E_direct = float(E[0])
+    # inference: the network tabulated on the feature nodes
+    ctx.learned_tabulate(LR.TAB_T, LR.TAB_D)
     for _ in range(3):
         ctx.learned_energy_potential(n, g, E, v)
     torch.cuda.synchronize()
@@ -309,8 +316,13 @@ def learned_leg(ctx, n, g, E, v, flush, stream, K, E_plain, v_plain, natoms, ms_
     ctx.learned_energy_potential(n, g, E, v)
     stages = {k: round(t, 4) for k, t in ctx.profile_read().items()}
     ctx.profile(False)
-    return {"model": kind, "ms_per_step": ms_l, "value": N / (ms_l * 1e-3), "unit": UNIT,
+    return {"model": kind, "network": "tabulated on %d x %d feature nodes over [-%g, %g]^2, Catmull-Rom"
+                                      % (LR.TAB_T, LR.TAB_T, LR.TAB_D, LR.TAB_D),
+            "ms_per_step": ms_l, "value": N / (ms_l * 1e-3), "unit": UNIT,
             "speedup_vs_plain_nq20": ms_plain / ms_l, "stages_ms": stages,
+            "network_at_every_point": {"ms_per_step": ms_direct, "speedup_vs_plain_nq20": ms_plain / ms_direct,
+                                       "energy_minus_tabulated_mev_per_atom": (E_direct - El) / natoms
+                                       * 27211.386245988},
             "energy_error_mev_per_atom_vs_plain_nq20": (El - E_plain) / natoms * 27211.386245988,
             "potential_vs_plain_nq20": {"density_weighted_rms_rel": vrms, "max_abs_rel": vmax},
             "tc_error": ctx.learned_status()}
@@ -338,6 +350,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-only", action="store_true",
                     help="time the plain call alone (no stage profile, other legs or host-buffer figure)")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="time the plain call, then the learned leg alone (for profiling the learned kernels)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -349,7 +363,7 @@ def main():
 
     # CPU baseline first (child processes, before this process touches the GPU)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.plain_only:
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.plain_only or args.learned_only):
         cpu = cpu_baselines()
 
     import torch
@@ -422,7 +436,11 @@ def main():
         "gpu_launches": 11 * K,
         "clocks": clocks,
     }
-    if args.plain_only:
+    if args.plain_only or args.learned_only:
+        if args.learned_only:
+            ctx.energy_potential(n, g, E, v)
+            base["learned_m8"] = learned_leg(ctx, n, g, E, v, flush, stream, min(K, 5), float(E[0]), v.clone(),
+                                             int(d["natoms"]), ms, N)
         if rank == 0:
             print(json.dumps(base), flush=True)
         ctx.close()

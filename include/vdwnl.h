@@ -293,6 +293,21 @@ long long vdw_learned_param_count(int J);
 int vdw_learned_load(vdw_handle h, int J, double k_max, const double feat[5], double base_q1,
                      double base_lambda, const float* params, void* stream);
 
+/* Tabulate the loaded network for inference.  The network's outputs depend
+ * on a point only through its two features (x1, x2); this evaluates the
+ * network (tensor cores, bf16 as above) once on the (T+2)^2 nodes
+ * x = -D + (i - 1) h, i = 0 .. T + 1, h = 2 D / (T - 1), and from then on
+ * vdw_learned_energy_potential takes each point's outputs and their Jacobian
+ * from the tensor product of Catmull-Rom cubics through the 4 x 4 nodes
+ * around its features (clamped to [-D, D], with zero derivative along a
+ * clamped axis), so that v stays the exact derivative of that energy.  The
+ * interpolation error is third order in h.  The table follows the parameters
+ * of the last vdw_learned_load, which drops it: call this again after a load
+ * (training steps run the network itself).  T = 0 drops the table; otherwise
+ * 4 <= T <= 4096, D > 0.  Allocates (T+2)^2 x 32 bytes on the first call with
+ * a given T.  Asynchronous on stream. */
+int vdw_learned_tabulate(vdw_handle h, int T, double D, void* stream);
+
 /* E and v of the learned model; arguments and outputs exactly as
  * vdw_energy_potential (E[1] holds the learned soft part, E[2] Delta E).
  * grad must be given.  Asynchronous on stream. */

@@ -107,6 +107,12 @@ struct LearnedArgs {
     const float4* knots;    // [J-1][P]: cubic coefficients in t of the Catmull-Rom piece on interval j
     int* err;               // set when a tensor-core wait gives up
     int base;               // channel weights = spline base + network (1) or network alone (0)
+    // the network tabulated on the feature nodes (vdw_learned_tabulate): node
+    // (i1, i2), i = 0 .. T + 1, at x = -D + (i - 1) h, its 8 outputs at
+    // tab[((i1 (T + 2) + i2) 2] and [... + 1]; tabT = 0: no table
+    const float4* tab;
+    int tabT;
+    float tabD, tab_h, tab_inv_h;
     float bqm[LRN_M];       // base mesh
     float bMq[LRN_M * LRN_M];  // bMq[m * M + k]: second derivative of base spline m at knot k
 };
@@ -175,6 +181,8 @@ struct vdw_ctx {
     float* d_U;                 // [M][N] real-space u_m for the parameter gradient (on first use)
     float* d_lw;                // [2M + 2][N] per-point coefficients of the learned assembly (on first use)
     double* d_gK;               // [P][J] knot-gradient accumulator (on first use)
+    float4* d_lrn_tab;          // the tabulated network (vdw_learned_tabulate)
+    size_t lrn_tab_bytes;
     // per-stage timing (vdw_profile_enable)
     int prof;
     cudaEvent_t ev[VDW_NSTAGES + 1];

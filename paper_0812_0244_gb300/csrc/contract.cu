@@ -22,7 +22,9 @@
 // the 32-byte record r of quad q: Q[q * qstride + 2 r], Q[... + 2 r + 1]
 // (float4 units), qstride = 2 Npad.  Npad is the number of half-spectrum
 // points N2 N3 (N1/2 + 1) rounded up to a whole number of contraction blocks;
-// the padding records stay zero.
+// the padding records stay zero.  (Writing u in pencil order instead, so that
+// the inverse y kernel reads contiguous runs, moves the scattered accesses
+// into the contraction's stores and measured no faster.)
 #include "plane.cuh"
 
 #include <algorithm>

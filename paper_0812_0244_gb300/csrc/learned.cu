@@ -111,7 +111,10 @@ __device__ __forceinline__ Feat features(float n, float gx, float gy, float gz, 
 // Cardinal cubic splines of the base mesh (Eq. fofx on an M-point mesh): p_m
 // and dp_m/dq at q clamped to the mesh; returns false where the clamp acts
 // (the derivative of the clamped basis is then zero).
-__device__ __forceinline__ bool base_weights(float q, const LearnedArgs& la, float* p, float* dp) {
+// bMq: the base splines' second derivatives (la.bMq, or a shared-memory copy
+// of it: indexed by the lane's interval, a parameter-space read serialises)
+__device__ __forceinline__ bool base_weights(float q, const LearnedArgs& la, float* p, float* dp,
+                                             const float* bMq) {
     const float lo = la.bqm[0], hi = la.bqm[LRN_M - 1];
     const bool inside = (q >= lo) && (q <= hi);
     const float qc = fminf(fmaxf(q, lo), hi);
@@ -125,7 +128,7 @@ __device__ __forceinline__ bool base_weights(float q, const LearnedArgs& la, flo
     const float dA = -(3.f * A * A - 1.f) * (1.f / 6.f) * h, dB = (3.f * B * B - 1.f) * (1.f / 6.f) * h;
 #pragma unroll
     for (int m = 0; m < LRN_M; ++m) {
-        const float Ma = la.bMq[m * LRN_M + k], Mb = la.bMq[m * LRN_M + k + 1];
+        const float Ma = bMq[m * LRN_M + k], Mb = bMq[m * LRN_M + k + 1];
         const float ya = (m == k) ? 1.f : 0.f, yb = (m == k + 1) ? 1.f : 0.f;
         p[m] = A * ya + B * yb + cA * Ma + cB * Mb;
         dp[m] = (yb - ya) * ih + dA * Ma + dB * Mb;
@@ -447,12 +450,14 @@ __global__ void __launch_bounds__(L_NET_THREADS, 1)
     __shared__ MlpCtl ctl;
     __shared__ double red[32];
     __shared__ float qm[MAX_NQ];
+    __shared__ float bMq_s[LRN_M * LRN_M];
     MlpShared* S = reinterpret_cast<MlpShared*>(smraw);
     MlpWG3* Wb = reinterpret_cast<MlpWG3*>(smraw + sizeof(MlpShared));
     const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
     MlpWG3* W = Wb + wg;
     mlp_load_weights(S, la);
     for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
+    for (int i = threadIdx.x; i < LRN_M * LRN_M; i += blockDim.x) bMq_s[i] = la.bMq[i];
     mlp_setup(&ctl, 128);
     const long long N = g.N;
     const long long ntiles = (N + L_TILE - 1) / L_TILE;
@@ -491,7 +496,7 @@ __global__ void __launch_bounds__(L_NET_THREADS, 1)
                     dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
                     dEg = -cn * qp.dq_dg;
                     // the clamped base has no q derivative
-                    if (la.base && base_weights(qq, la, pb, dpb)) {
+                    if (la.base && base_weights(qq, la, pb, dpb, bMq_s)) {
                         bn = qp.dq_dn;
                         bg = qp.dq_dg;
                     }
@@ -524,6 +529,174 @@ __global__ void __launch_bounds__(L_NET_THREADS, 1)
     __syncthreads();
     const double b = block_sum((double)bad, red);
     if (threadIdx.x == 0 && b > 0.0) atomicAdd(invalid, (unsigned long long)b);
+}
+
+// ---------------------------------------------------------------------------
+// L1' the network tabulated on the features' node grid, and its lookup
+// ---------------------------------------------------------------------------
+// The network's outputs o(x1, x2) depend on a point only through its two
+// features.  k_learned_tabulate runs the network (tensor cores, as
+// k_learned_channels) once on the (T+2)^2 nodes x = -D + (i - 1) h; the
+// inference kernel k_learned_lookup then takes each point's o and its
+// Jacobian from the tensor product of Catmull-Rom cubics through the 4 x 4
+// nodes around (x1, x2) (features clamped to [-D, D], zero derivative along a
+// clamped axis): the interpolant is C1 and its derivative is what the
+// potential uses, so v is the exact derivative of the tabulated energy.
+__global__ void __launch_bounds__(L_THREADS, 1) k_learned_tabulate(LearnedArgs la, float4* __restrict__ tab) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ MlpCtl ctl;
+    MlpShared* S = reinterpret_cast<MlpShared*>(smraw);
+    MlpWG* Wb = reinterpret_cast<MlpWG*>(smraw + sizeof(MlpShared));
+    const int wg = threadIdx.x >> 7, r = threadIdx.x & 127;
+    mlp_load_weights(S, la);
+    mlp_setup(&ctl, 128);
+    uint32_t phase = 0;
+    const int T2 = la.tabT + 2;
+    const long long nodes = (long long)T2 * T2;
+    const long long ntiles = (nodes + L_TILE - 1) / L_TILE;
+    for (long long T = 2 * (long long)blockIdx.x + wg; T < ntiles; T += 2 * (long long)gridDim.x) {
+        const long long i = T * L_TILE + r;
+        const bool in = i < nodes;
+        const int i1 = in ? (int)(i / T2) : 0, i2 = in ? (int)(i - (long long)i1 * T2) : 0;
+        const float x1 = -la.tabD + (float)(i1 - 1) * la.tab_h, x2 = -la.tabD + (float)(i2 - 1) * la.tab_h;
+        float o[LRN_M];
+        if (!mlp_forward(S, Wb + wg, &ctl, wg, r, phase, x1, x2, o, la.err)) break;
+        if (in) {
+            tab[2 * i] = make_float4(o[0], o[1], o[2], o[3]);
+            tab[2 * i + 1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
+    }
+    mlp_teardown(&ctl);
+}
+
+// Catmull-Rom weights of nodes i-1 .. i+2 at local position s, and d/ds.
+__device__ __forceinline__ void catmull_rom(float s, float* w, float* dw) {
+    const float s2 = s * s, s3 = s2 * s;
+    w[0] = 0.5f * (-s3 + 2.f * s2 - s);
+    w[1] = 0.5f * (3.f * s3 - 5.f * s2) + 1.f;
+    w[2] = 0.5f * (-3.f * s3 + 4.f * s2 + s);
+    w[3] = 0.5f * (s3 - s2);
+    dw[0] = 0.5f * (-3.f * s2 + 4.f * s - 1.f);
+    dw[1] = 0.5f * (9.f * s2 - 10.f * s);
+    dw[2] = 0.5f * (-9.f * s2 + 8.f * s + 1.f);
+    dw[3] = 0.5f * (3.f * s2 - 2.f * s);
+}
+
+// node index of the interval start, local position and the axis's d/dx factor
+__device__ __forceinline__ int table_axis(float x, const LearnedArgs& la, float& s, float& dscale) {
+    const float xc = fminf(fmaxf(x, -la.tabD), la.tabD);
+    const float u = (xc + la.tabD) * la.tab_inv_h;
+    const int i = min((int)u, la.tabT - 2);
+    s = u - (float)i;
+    dscale = (x >= -la.tabD && x <= la.tabD) ? la.tab_inv_h : 0.f;
+    return i;
+}
+
+// One thread per point (packed order, grid-stride); writes what k_learned_net
+// writes (theta channels, the assembly coefficients, Delta E partials).
+constexpr int LOOKUP_THREADS = 256;
+__global__ void __launch_bounds__(LOOKUP_THREADS) k_learned_lookup(const float* __restrict__ n,
+                                                                  const float* __restrict__ grad, GridArgs g,
+                                                                  PointParams P, LearnedArgs la,
+                                                                  float* __restrict__ specf,
+                                                                  double* __restrict__ epart,
+                                                                  unsigned long long* __restrict__ invalid,
+                                                                  float* __restrict__ lw) {
+    __shared__ double red[32];
+    __shared__ float qm[MAX_NQ];
+    __shared__ float bMq_s[LRN_M * LRN_M];
+    for (int i = threadIdx.x; i < MAX_NQ; i += blockDim.x) qm[i] = P.qm[i];
+    for (int i = threadIdx.x; i < LRN_M * LRN_M; i += blockDim.x) bMq_s[i] = la.bMq[i];
+    __syncthreads();
+    const long long N = g.N;
+    const long long fstride = 2LL * g.N2 * g.ncols;  // floats between the planes of two channels
+    const int T2 = la.tabT + 2;
+    double eacc = 0.0;
+    unsigned int bad = 0;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
+        int y, z, x, j;
+        const long long gi = packed_point(q, g, y, z, x, j);
+        const float ni = n[gi], gx = grad[gi], gy = grad[N + gi], gz = grad[2 * N + gi];
+        bad += (!(ni >= 0.f) || !isfinite(ni)) ? 1u : 0u;
+        const Feat f = features(ni, gx, gy, gz, la, P.n_min);
+        const bool ok = f.ok;
+        // the network from the table
+        float s1, s2, ds1, ds2;
+        const int i1 = table_axis(ok ? f.x1 : 0.f, la, s1, ds1);
+        const int i2 = table_axis(ok ? f.x2 : 0.f, la, s2, ds2);
+        float a[4], da[4], b[4], db[4];
+        catmull_rom(s1, a, da);
+        catmull_rom(s2, b, db);
+        float o[LRN_M], J1[LRN_M], J2[LRN_M];
+#pragma unroll
+        for (int m = 0; m < LRN_M; ++m) o[m] = J1[m] = J2[m] = 0.f;
+        // per row k of nodes: R = sum_l b_l v, S = sum_l b'_l v; then
+        // o = sum_k a_k R_k, d/dx1 = sum_k a'_k R_k, d/dx2 = sum_k a_k S_k
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4* row = la.tab + 2LL * ((long long)(i1 + k) * T2 + i2);
+            float R[LRN_M], Sd[LRN_M];
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) R[m] = Sd[m] = 0.f;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const float4 v0 = __ldg(row + 2 * l), v1 = __ldg(row + 2 * l + 1);
+                const float v[LRN_M] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                for (int m = 0; m < LRN_M; ++m) {
+                    R[m] = fmaf(b[l], v[m], R[m]);
+                    Sd[m] = fmaf(db[l], v[m], Sd[m]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) {
+                o[m] = fmaf(a[k], R[m], o[m]);
+                J1[m] = fmaf(da[k], R[m], J1[m]);
+                J2[m] = fmaf(a[k], Sd[m], J2[m]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < LRN_M; ++m) {
+            J1[m] *= ds1;
+            J2[m] *= ds2;
+        }
+        // q chain: Delta E and the spline base
+        float pb[LRN_M], dpb[LRN_M];
+#pragma unroll
+        for (int m = 0; m < LRN_M; ++m) pb[m] = dpb[m] = 0.f;
+        float bn = 0.f, bg = 0.f, dEn = 0.f, dEg = 0.f;
+        const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
+        if (qp.k != K_INVALID) {
+            const float qq = qp.q, q3 = qq * qq * qq, q4 = q3 * qq;
+            eacc += (double)(0.5f * P.C_s * ni * ni / q3);
+            const float cn = 1.5f * P.C_s * ni * ni / q4;
+            dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
+            dEg = -cn * qp.dq_dg;
+            if (la.base && base_weights(qq, la, pb, dpb, bMq_s)) {
+                bn = qp.dq_dn;
+                bg = qp.dq_dg;
+            }
+        }
+        float* dst = specf + 2LL * y * g.ncols + packed_offset(x, j, z & 1, g.Nh);
+#pragma unroll
+        for (int m = 0; m < LRN_M; ++m) dst[m * fstride] = ok ? ni * (o[m] + pb[m]) : 0.f;
+        if (lw) {
+#pragma unroll
+            for (int m = 0; m < LRN_M; ++m) {
+                const float dwn = J1[m] * f.dx1_dn + J2[m] * f.dx2_dn + dpb[m] * bn;
+                const float dwg = J2[m] * f.gx2 + dpb[m] * bg;
+                lw[m * N + q] = ok ? o[m] + pb[m] + ni * dwn : 0.f;
+                lw[(LRN_M + m) * N + q] = ok ? ni * dwg : 0.f;
+            }
+            lw[2 * LRN_M * N + q] = ok ? dEn : 0.f;
+            lw[(2 * LRN_M + 1) * N + q] = ok ? dEg : 0.f;
+        }
+    }
+    const double es = block_sum(eacc, red);
+    if (threadIdx.x == 0) epart[blockIdx.x] = es;
+    __syncthreads();
+    const double bsum = block_sum((double)bad, red);
+    if (threadIdx.x == 0 && bsum > 0.0) atomicAdd(invalid, (unsigned long long)bsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -723,7 +896,7 @@ __global__ void __launch_bounds__(L_THREADS, 1) k_learned_channels(const float* 
         for (int m = 0; m < LRN_M; ++m) pb[m] = 0.f;
         if (ok && la.base) {
             const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
-            if (qp.k != K_INVALID) base_weights(qp.q, la, pb, dpb);
+            if (qp.k != K_INVALID) base_weights(qp.q, la, pb, dpb, la.bMq);
         }
         float o[LRN_M];
         if (!mlp_forward(S, Wb + wg, &ctl, wg, r, phase, ok ? f.x1 : 0.f, ok ? f.x2 : 0.f, o, la.err)) break;
@@ -1027,6 +1200,12 @@ int net_blocks(vdw_ctx* c) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     return std::max(1, std::min(nsm, c->g.N2 * L_SLOTS));
 }
+// blocks of the table lookup: grid-stride over the points, at most the
+// partial-sum slots the network kernel has
+int lookup_blocks(vdw_ctx* c) {
+    const long long want = (c->g.N + LOOKUP_THREADS - 1) / LOOKUP_THREADS;
+    return (int)std::max(1LL, std::min<long long>(want, (long long)c->g.N2 * L_SLOTS));
+}
 // knot-gradient bins of k_learned_contract_gradk
 size_t smem_gradk(int J) { return sizeof(float) * (size_t)LRN_P * J; }
 size_t smem_plane1(const GridArgs& g) {
@@ -1083,7 +1262,10 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     const GridArgs& g = c->g;
     const PointParams& P = c->pp;
     const LearnedArgs& la = c->la;
-    const int nb0 = net_blocks(c);
+    // the inference form takes the network from its table when there is one;
+    // the training form (parameter gradients) always runs the network
+    const bool lookup = la.tabT > 0 && kind != RUN_GRAD;
+    const int nb0 = lookup ? lookup_blocks(c) : net_blocks(c);
     double* ep = lrn_epart(c);
     float* specf = reinterpret_cast<float*>(c->d_spec);
     const double Omega = c->L[0] * c->L[1] * c->L[2];
@@ -1101,8 +1283,12 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     }
     VDW_CUDA(cudaMemsetAsync(c->d_invalid, 0, sizeof(unsigned long long), s));
     const bool want_pot = (v != nullptr) || (w != nullptr);
-    k_learned_net<<<nb0, L_NET_THREADS, smem_net(), s>>>(n, grad, g, P, la, specf, ep, c->d_invalid,
-                                                     (want_pot && kind != RUN_GRAD) ? c->d_lw : nullptr);
+    if (lookup)
+        k_learned_lookup<<<nb0, LOOKUP_THREADS, 0, s>>>(n, grad, g, P, la, specf, ep, c->d_invalid,
+                                                       want_pot ? c->d_lw : nullptr);
+    else
+        k_learned_net<<<nb0, L_NET_THREADS, smem_net(), s>>>(n, grad, g, P, la, specf, ep, c->d_invalid,
+                                                         (want_pot && kind != RUN_GRAD) ? c->d_lw : nullptr);
     mark(ST_POINTWISE);
     int rc = pipeline_planes_inplace(c, LRN_M, false, s);
     if (rc) return rc;
@@ -1225,6 +1411,11 @@ static LrnLayout lrn_layout(const GridArgs& g, int J, int nb_sorted) {
 }
 
 void learned_free(vdw_ctx* c) {
+    cudaFree(c->d_lrn_tab);
+    c->d_lrn_tab = nullptr;
+    c->lrn_tab_bytes = 0;
+    c->la.tabT = 0;
+    c->la.tab = nullptr;
     cudaFree(c->d_lrn);
     cudaFree(c->d_U);
     cudaFree(c->d_lw);
@@ -1329,6 +1520,7 @@ int vdw_learned_load(vdw_handle c, int J, double k_max, const double feat[5], do
     VDW_CUDA(cudaGetLastError());
     const int rc = configure_all(c);
     if (rc) return rc;
+    c->la.tabT = 0;  // a table made for the previous parameters no longer applies
     c->lrn_loaded = 1;
     return VDW_OK;
 }
@@ -1375,6 +1567,36 @@ int vdw_learned_channels(vdw_handle c, const float* n, const float* grad, float*
     const long long tiles = (c->g.N + 2 * L_TILE - 1) / (2 * L_TILE);
     const int nb = (int)std::min<long long>(tiles, 2LL * nsm);
     k_learned_channels<<<nb, L_THREADS, sm, (cudaStream_t)stream>>>(n, grad, c->g.N, c->pp, c->la, w_out);
+    VDW_CUDA(cudaGetLastError());
+    return VDW_OK;
+}
+
+int vdw_learned_tabulate(vdw_handle c, int T, double D, void* stream) {
+    if (!c || T < 0 || T == 1 || T == 2 || T == 3 || T > 4096 || (T > 0 && !(D > 0.0))) return VDW_ERR_ARG;
+    if (!lrn_ready(c)) return VDW_ERR_STATE;
+    LearnedArgs& la = c->la;
+    if (T == 0) {
+        la.tabT = 0;
+        return VDW_OK;
+    }
+    const size_t bytes = sizeof(float4) * 2 * (size_t)(T + 2) * (size_t)(T + 2);
+    if (bytes != c->lrn_tab_bytes) {
+        cudaFree(c->d_lrn_tab);
+        c->d_lrn_tab = nullptr;
+        c->lrn_tab_bytes = 0;
+        VDW_CUDA(cudaMalloc(&c->d_lrn_tab, bytes));
+        c->lrn_tab_bytes = bytes;
+    }
+    la.tab = c->d_lrn_tab;
+    la.tabT = T;
+    la.tabD = (float)D;
+    la.tab_h = (float)(2.0 * D / (T - 1));
+    la.tab_inv_h = (float)((T - 1) / (2.0 * D));
+    const size_t sm = sizeof(MlpShared) + 2 * sizeof(MlpWG);
+    if (const int rs = raise_smem_limit(k_learned_tabulate, sm)) return rs;
+    const long long tiles = ((long long)(T + 2) * (T + 2) + L_TILE - 1) / L_TILE;
+    const int nb = (int)std::max(1LL, std::min<long long>((tiles + 1) / 2, 2LL * std::max(c->nsm, 1)));
+    k_learned_tabulate<<<nb, L_THREADS, sm, (cudaStream_t)stream>>>(la, c->d_lrn_tab);
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
 }

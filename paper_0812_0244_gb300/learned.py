@@ -56,6 +56,12 @@ OFF_K = 2 * H + H + H * H + H + M * H + M
 
 TRAINED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "trained", "learned_m8_tube.npz")
 
+# Inference table of the network (vdw_learned_tabulate): 769 nodes per
+# feature over [-12, 12] (h = 1/32), covering the standardised features of the
+# tube densities on grids from 90 x 90 x 36 (where the spectral gradient's
+# ringing at the density floor reaches x2 ~ 11) up.
+TAB_T, TAB_D = 769, 12.0
+
 
 def tube_config(seed, rng_seed=None):
     """Seeded nanotube variant: outer wall shift U(0, 2.46 A), rotation U(0, 36 deg)."""
@@ -198,14 +204,17 @@ def energy_error_per_atom(ctx, samples, learned=True):
     return np.array(out)
 
 
-def potential_error(ctx, samples):
+def potential_error(ctx, samples, learned=True):
     """Density-weighted RMS of v - v* for each sample (Hartree)."""
     import torch
     out = []
     for s in samples:
         E = torch.empty(3, dtype=torch.float64, device=s.n.device)
         v = torch.empty_like(s.n)
-        ctx.learned_energy_potential(s.n, s.g, E, v)
+        if learned:
+            ctx.learned_energy_potential(s.n, s.g, E, v)
+        else:
+            ctx.energy_potential(s.n, s.g, E, v)
         out.append(float(torch.sqrt((s.n * (v - s.v_ref) ** 2).sum() / s.n.sum())))
     return np.array(out)
 

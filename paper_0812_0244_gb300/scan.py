@@ -122,6 +122,7 @@ def run(nz=8, nphi=8, grids=(144, 180, 200), dr_out=(-0.2, 0.0, 0.2), seed=0, le
             try:
                 params = torch.tensor(mdl["params"], dtype=torch.float32, device="cuda")
                 ctx.learned_load(params, mdl["J"], mdl["k_max"], mdl["feat"], mdl["base"])
+                ctx.learned_tabulate(LR.TAB_T, LR.TAB_D)
                 use_l = True
             except vdwnl.VdwError as ex:
                 log("grid %d: learned path skipped (%s)" % (N, ex))

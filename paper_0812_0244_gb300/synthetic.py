@@ -68,16 +68,20 @@ def _gaussian_sum(shape, L, centers, amps, sigmas, floor, cut=8.0):
 
 def _gaussian_sum_torch(shape, L, centers, amps, sigmas, floor, device, cut=8.0):
     """Density part of _gaussian_sum evaluated with torch on a device (FP64):
-    the same Gaussians, boxes and images, accumulated by index_put_."""
+    the same Gaussians, boxes and images.  A Gaussian's box is the tensor
+    product of one index range per axis and its value the product of three
+    1D profiles, so the whole sum is sum_g A_g pz_g (x) py_g (x) px_g over
+    profiles that vanish outside each box: one matrix product."""
     import torch
     N3, N2, N1 = shape
     L = np.asarray(L, np.float64)
     h = L / np.array([N1, N2, N3], np.float64)
-    n = torch.full(tuple(shape), float(floor), dtype=torch.float64, device=device)
-    for c, A, s in zip(centers, amps, sigmas):
-        R = cut * s
-        idx, dis = [], []
-        for d, Nd in enumerate((N1, N2, N3)):
+    G = len(centers)
+    prof = []
+    for d, Nd in enumerate((N1, N2, N3)):
+        P = np.zeros((G, Nd))
+        for k, (c, s) in enumerate(zip(centers, sigmas)):
+            R = cut * s
             lo = int(np.floor((c[d] - R) / h[d]))
             hi = int(np.ceil((c[d] + R) / h[d]))
             ii = np.arange(lo, hi + 1)
@@ -87,14 +91,13 @@ def _gaussian_sum_torch(shape, L, centers, amps, sigmas, floor, device, cut=8.0)
                 x = x - L[d] * np.round(x / L[d])
             else:
                 x = ii * h[d] - c[d]
-            idx.append(torch.as_tensor(np.mod(ii, Nd), device=device))
-            dis.append(torch.as_tensor(x, dtype=torch.float64, device=device))
-        x, y, z = dis
-        r2 = x[None, None, :] ** 2 + y[None, :, None] ** 2 + z[:, None, None] ** 2
-        val = A * torch.exp(-r2 / (2.0 * s * s))
-        iz, iy, ix = torch.meshgrid(idx[2], idx[1], idx[0], indexing="ij")
-        n.index_put_((iz.reshape(-1), iy.reshape(-1), ix.reshape(-1)), val.reshape(-1), accumulate=True)
-    return n
+            np.add.at(P[k], np.mod(ii, Nd), np.exp(-x * x / (2.0 * s * s)))
+        prof.append(torch.as_tensor(P, dtype=torch.float64, device=device))
+    px, py, pz = prof
+    A = torch.as_tensor(np.asarray(amps, np.float64), device=device)
+    M = (py[:, :, None] * px[:, None, :]).reshape(G, N2 * N1)
+    n = ((pz * A[:, None]).transpose(0, 1) @ M).reshape(N3, N2, N1)
+    return n + float(floor)
 
 
 def tube_density_torch(seed=0, shape=(72, 180, 180), inner=5, outer=10, shift_ang=0.0, rot_deg=0.0,

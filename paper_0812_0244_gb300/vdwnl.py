@@ -76,7 +76,7 @@ EXPORTS = ["vdw_params_default", "vdw_kernel_table", "vdw_create", "vdw_plan", "
            "vdw_energy_potential_host", "vdw_last_invalid_points", "vdw_profile_enable", "vdw_profile_read",
            "vdw_delta_energy_noalloc", "vdw_spectral_gradient", "vdw_learned_param_count", "vdw_learned_load",
            "vdw_learned_energy_potential", "vdw_learned_param_grad", "vdw_learned_fit_grad",
-           "vdw_learned_channels", "vdw_learned_status", "vdw_basis_weights", "vdw_adam_step", "vdw_wait_status",
+           "vdw_learned_channels", "vdw_learned_status", "vdw_learned_tabulate", "vdw_basis_weights", "vdw_adam_step", "vdw_wait_status",
            "vdw_workspace_bytes", "vdw_destroy", "vdw_error_string", "vdw_last_error"]
 
 LEARNED_M = 8
@@ -117,6 +117,7 @@ def lib():
     L.vdw_learned_fit_grad.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, vp, vp]
     L.vdw_learned_channels.argtypes = [vp, vp, vp, vp, vp]
     L.vdw_learned_status.argtypes = [vp, P(ctypes.c_int)]
+    L.vdw_learned_tabulate.argtypes = [vp, ctypes.c_int, ctypes.c_double, vp]
     L.vdw_basis_weights.argtypes = [vp, vp, vp, vp, vp]
     L.vdw_adam_step.argtypes = [vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
@@ -314,6 +315,12 @@ class VdwNL:
         self._lrn_params = params  # keep alive until the prepare kernel ran
         _check(lib().vdw_learned_load(self._h, int(J), float(k_max), _dptr(f), float(base[0]), float(base[1]),
                                       _ptr(params), _stream_handle(stream)), "vdw_learned_load")
+
+    def learned_tabulate(self, T, D, stream=None):
+        """vdw_learned_tabulate: the loaded network on (T+2)^2 feature nodes over
+        [-D, D]^2 for inference (T = 0: evaluate the network at every point)."""
+        _check(lib().vdw_learned_tabulate(self._h, int(T), float(D), _stream_handle(stream)),
+               "vdw_learned_tabulate")
 
     def learned_energy_potential(self, n, grad, E=None, v=None, w=None, stream=None):
         _cuda_f32(n, self.shape)

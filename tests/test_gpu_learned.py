@@ -224,3 +224,71 @@ def test_learned_full_tube_matches_oracle(torch_cuda, table):
     vmax = np.abs(ref["v"]).max()
     assert np.median(err) < 1e-5 * vmax
     assert err.max() < 1e-2 * vmax
+
+
+TAB_T, TAB_D = 257, 12.0
+
+
+@pytest.mark.parametrize("base", [(0.0, 0.0), BASE], ids=["network", "spline_base"])
+def test_tabulated_network_matches_oracle(torch_cuda, table, base):
+    """vdw_learned_tabulate: the network evaluated on the feature nodes by the
+    tensor cores, then interpolated per point, against the oracle's table of
+    the same network (oracle.learned.network_table / table_eval).  The two
+    tables differ only where a node's bf16 activation rounds the other way,
+    so the tolerances are those of the network itself."""
+    torch = torch_cuda
+    d = S.two_atom_density(8, shape=(24, 24, 24))
+    n, g, L = f32(d["n"]), f32(d["grad"]), d["L"]
+    n64, g64 = n.astype(np.float64), g.astype(np.float64)
+    mdl = model_for(n64, g64, 41, base=base)
+    ctx, _ = gpu_ctx(torch, n.shape, L, mdl)
+    ctx.learned_tabulate(TAB_T, TAB_D)
+    E, v, _ = ctx.learned_compute(torch.tensor(n, device="cuda"), torch.tensor(g, device="cuda"))
+    E = E.cpu().numpy()
+    v = v.cpu().numpy()
+    assert ctx.learned_status() == 0
+    tab = LO.network_table(mdl, TAB_T, TAB_D)
+    ref = LO.energy_potential(n64, g64, L, mdl, table, table=tab)
+    assert abs(E[1] - ref["E_soft"]) <= 1e-5 * abs(ref["E_soft"]) + 1e-7, (E, ref["E_soft"])
+    assert abs(E[2] - ref["dE"]) <= 1e-6 * abs(ref["dE"])
+    err = np.abs(v - ref["v"])
+    vmax = np.abs(ref["v"]).max()
+    assert np.median(err) < 1e-5 * vmax
+    assert err.max() < 1e-2 * vmax
+    # T = 0 drops the table: the network itself again
+    ctx.learned_tabulate(0, 0.0)
+    E0, _, _ = ctx.learned_compute(torch.tensor(n, device="cuda"), torch.tensor(g, device="cuda"), want_v=False)
+    ref0 = LO.energy_potential(n64, g64, L, mdl, table, want_v=False)
+    assert abs(float(E0[1]) - ref0["E_soft"]) <= 1e-5 * abs(ref0["E_soft"]) + 1e-7
+
+
+@pytest.mark.slow
+def test_tabulated_trained_model_on_tube(torch_cuda, table):
+    """The stored trained model, tabulated as the benchmark runs it (769 x 769
+    nodes on [-12, 12]^2), on the 180 x 180 x 72 tube against the oracle with
+    the same table."""
+    torch = torch_cuda
+    from paper_0812_0244_gb300 import learned as LR
+    mdl_t = LR.load()
+    d = S.tube_density(2, shift_ang=0.4, rot_deg=7.0)
+    n, L = f32(d["n"]), d["L"]
+    n64 = n.astype(np.float64)
+    g64 = O.spectral_gradient(n64, L).astype(np.float32).astype(np.float64)
+    mo = LO.random_model(0, J=mdl_t["J"], k_max=mdl_t["k_max"], base=mdl_t["base"]).with_flat(
+        np.asarray(mdl_t["params"], np.float64))
+    mo.mu1, mo.sig1, mo.mu2, mo.sig2, mo.eps = mdl_t["feat"]
+    from paper_0812_0244_gb300 import vdwnl
+    ctx = vdwnl.VdwNL(vdwnl.Params()).plan(n.shape, L)
+    params = torch.tensor(np.asarray(mdl_t["params"], np.float32), device="cuda")
+    ctx.learned_load(params, mdl_t["J"], mdl_t["k_max"], mdl_t["feat"], mdl_t["base"])
+    ctx.learned_tabulate(LR.TAB_T, LR.TAB_D)
+    E, v, _ = ctx.learned_compute(torch.tensor(n, device="cuda"), torch.tensor(g64.astype(np.float32), device="cuda"))
+    E = E.cpu().numpy()
+    v = v.cpu().numpy()
+    assert ctx.learned_status() == 0
+    ref = LO.energy_potential(n64, g64, L, mo, table, table=LO.network_table(mo, LR.TAB_T, LR.TAB_D))
+    assert abs(E[0] - ref["E"]) <= 1e-5 * abs(ref["E"]), (E, ref["E"])
+    err = np.abs(v - ref["v"])
+    vmax = np.abs(ref["v"]).max()
+    assert np.median(err) < 1e-5 * vmax
+    assert err.max() < 1e-2 * vmax

@@ -52,6 +52,7 @@ def test_scan_energies_match_oracle(table):
     mo = LO.random_model(0, J=mdl["J"], k_max=mdl["k_max"], base=mdl["base"]).with_flat(
         np.asarray(mdl["params"], np.float64))
     mo.mu1, mo.sig1, mo.mu2, mo.sig2, mo.eps = mdl["feat"]
+    tab = LO.network_table(mo, LR.TAB_T, LR.TAB_D)  # the scan runs the tabulated network
     z = np.arange(2) * (2.0 * scan.DZ_ANG) / 2
     phi = np.arange(2) * (2.0 * scan.DPHI_DEG) / 2
     ctx = None
@@ -69,5 +70,5 @@ def test_scan_energies_match_oracle(table):
             n = n32.double().cpu().numpy()
             Eo = O.energy(n, g, L, table)
             assert abs(Ep[i, j] - Eo) < 1e-6, (i, j, Ep[i, j], Eo)
-            Elo = LO.energy_potential(n, g, L, mo, table, want_v=False)["E"]
+            Elo = LO.energy_potential(n, g, L, mo, table, want_v=False, table=tab)["E"]
             assert abs(El[i, j] - Elo) <= 1e-5 * abs(Elo), (i, j, El[i, j], Elo)
