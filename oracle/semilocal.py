@@ -16,10 +16,11 @@ E_x = dOmega sum_i e_x,i and E_c^LDA = dOmega sum_i e_c,i.  The potential
 adds de/dn to v_loc and de/d(grad n) to w, whose divergence enters v through
 the same gradient operator as the nonlocal term (Eq. Vi).
 
-Parity unpinned: revPBE's kappa = 1.245 and PBE's mu = beta pi^2 / 3 with
-beta = 0.066725 are restated from the published papers, which are not at
-hand.  The uniform-gas limit (the Dirac exchange), the large-gradient limit
-F_x -> 1 + kappa and every derivative are pinned.
+Parity unpinned: revPBE's kappa = 1.245 (a fitted value) is restated from
+the published paper, which is not at hand.  mu = beta pi^2 / 3 is pinned
+through beta's definition by the Ma-Brueckner high-density gradient
+coefficient; the uniform-gas limit (the Dirac exchange), the large-gradient
+limit F_x -> 1 + kappa and every derivative are pinned.
 """
 from __future__ import annotations
 

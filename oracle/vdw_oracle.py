@@ -22,10 +22,12 @@ Definitions the paper takes from Dion et al. (PRL 92, 246401, 2004):
   q0(n, |grad n|), the kernel phi(d1, d2) and, through q0, the LDA
   correlation of Perdew and Wang (PRB 45, 13244, 1992).
 
-Parity unpinned: the Perdew-Wang constants alpha1, beta2, beta3, beta4 and
-Dion's gradient coefficient Z_ab are restated from the published papers, which
-are not at hand; no test fixes their values (A is pinned through the
-high-density limit, and every derivative is pinned by finite differences).
+Parity unpinned: Dion's gradient coefficient Z_ab in q0 is restated from the
+published paper, which is not at hand, and no test fixes its value.  The
+Perdew-Wang constants are pinned through the limits their form is built to
+reproduce (high- and low-density expansion coefficients) and against the
+independent Perdew-Zunger fit; every derivative is pinned by finite
+differences.
 """
 from __future__ import annotations
 
@@ -97,7 +99,9 @@ Z_AB = -0.8491  # Dion et al. gradient coefficient in q0
 
 def pw92_eps_c(rs):
     """eps_c(rs) in Hartree and d eps_c / d rs (Perdew-Wang 1992, p = 1).
-    Parity unpinned for alpha1 and beta2..beta4 (restated constants)."""
+    The restated constants are pinned through the limits the form is built
+    to reproduce: c0 (exact), c1 and the missing sqrt(rs) term at high
+    density, d0 and d1 at low density, and the Perdew-Zunger fit between."""
     rs = np.asarray(rs, dtype=np.float64)
     b1, b2, b3, b4 = PW_BETA
     srs = np.sqrt(rs)

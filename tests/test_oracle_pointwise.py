@@ -2,7 +2,9 @@
 saturation (Eq. Sat), q mesh and the cardinal cubic splines (Eq. fofx).
 
 * PW92: the coefficient of ln r_s in the high-density limit is the exact
-  Gell-Mann--Brueckner value (1 - ln 2)/pi^2; derivatives match finite
+  Gell-Mann--Brueckner value (1 - ln 2)/pi^2, the expansion has no sqrt(r_s)
+  term, the low-density coefficients d0, d1 are reproduced, the curve agrees
+  with the independent Perdew--Zunger fit; derivatives match finite
   differences.
 * q0: the uniform-gas value k_F - (4 pi/3) eps_c, positivity, derivatives.
 * h: h(x) ~ x below q_c, h -> q_c above, monotone, derivative.
@@ -31,6 +33,51 @@ def test_pw92_high_density_log_coefficient():
     assert abs(slope - (1 - np.log(2)) / np.pi ** 2) < 2e-5
     const = e2 - slope * np.log(r2)
     assert abs(const + 0.046644) < 1e-5
+
+
+def test_pw92_no_sqrt_rs_term_at_high_density():
+    # Perdew-Wang chose beta2 = 2 A beta1^2 so that the expansion
+    # c0 ln rs - c1 + O(rs ln rs) has no sqrt(rs) term: a wrong beta2 (or a
+    # beta term in the wrong power) leaves one of size 2A (2A beta1 - beta2/beta1) sqrt(rs)
+    r1, r2 = 1e-12, 1e-14
+    e1, _ = O.pw92_eps_c(r1)
+    e2, _ = O.pw92_eps_c(r2)
+    c0 = (e1 - e2) / (np.log(r1) - np.log(r2))
+    c1 = c0 * np.log(r2) - e2
+    rs = 1e-8
+    res = O.pw92_eps_c(rs)[0] - (c0 * np.log(rs) - c1)
+    assert abs(res) / np.sqrt(rs) < 5e-5
+
+
+def test_pw92_low_density_wigner_coefficients():
+    # rs -> infinity: eps_c -> -d0/rs + d1/rs^(3/2) with the low-density
+    # coefficients d0 = 0.4335, d1 = 1.4408 Ha that the Perdew-Wang form is
+    # built to reproduce (d0 = alpha1/beta4, d1 = alpha1 beta3/beta4^2)
+    rs = np.array([1e8, 1e10])
+    e, _ = O.pw92_eps_c(rs)
+    d0 = -(e * rs)
+    assert np.all(np.abs(d0 - 0.4335) < 2e-4)
+    rs = 1e10
+    e = O.pw92_eps_c(rs)[0]
+    d0x = -O.pw92_eps_c(1e16)[0] * 1e16  # the leading coefficient itself
+    d1 = (e + d0x / rs) * rs ** 1.5
+    assert abs(d1 - 1.4408) < 2e-3
+
+
+def test_pw92_agrees_with_perdew_zunger_fit():
+    # Perdew-Zunger 1981 parameterise the same Ceperley-Alder data with a
+    # different form (gamma / (1 + b1 sqrt(rs) + b2 rs) for rs >= 1, the
+    # Gell-Mann-Brueckner series below); the two fits agree to under 1 %
+    rs = np.array([0.3, 0.5, 0.8, 1.0, 2.0, 3.0, 5.0, 10.0, 20.0, 50.0, 100.0])
+
+    def pz(r):
+        if r >= 1.0:
+            return -0.1423 / (1.0 + 1.0529 * np.sqrt(r) + 0.3334 * r)
+        return 0.0311 * np.log(r) - 0.048 + 0.0020 * r * np.log(r) - 0.0116 * r
+
+    e, _ = O.pw92_eps_c(rs)
+    ref = np.array([pz(r) for r in rs])
+    assert np.max(np.abs(e / ref - 1.0)) < 1e-2
 
 
 def test_pw92_negative_and_derivative():

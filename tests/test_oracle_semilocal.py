@@ -26,6 +26,22 @@ def test_enhancement_factor_limits():
         np.testing.assert_allclose(e / e0, Fref, rtol=tol)
 
 
+def test_gradient_coefficient_is_ma_brueckner():
+    """mu = beta pi^2 / 3 with beta = 16 (3 pi^2)^(1/3) C_c(0) / pi, the
+    high-density gradient coefficient C_c(0) = 4.235e-3 of Ma and Brueckner:
+    the small-s slope of the oracle's F_x, read off e_x itself."""
+    n = np.full(3, 0.2)
+    kF = (3 * np.pi ** 2 * 0.2) ** (1 / 3)
+    e0 = -0.75 * (3 / np.pi) ** (1 / 3) * 0.2 ** (4 / 3)
+    s = 1e-4
+    g = np.zeros((3, 3))
+    g[1] = s * 2 * kF * 0.2
+    e, _, _ = SL.exchange_revpbe(n, g)
+    slope = (e[0] / e0 - 1.0) / s ** 2
+    beta = 16.0 * (3 * np.pi ** 2) ** (1 / 3) * 4.235e-3 / np.pi
+    assert abs(slope - beta * np.pi ** 2 / 3) < 2e-5
+
+
 def test_energy_density_derivatives_match_fd():
     rng = np.random.default_rng(0)
     n = 10 ** rng.uniform(-4, 0.5, 20)
