@@ -109,7 +109,8 @@ struct LearnedArgs {
     int base;               // channel weights = spline base + network (1) or network alone (0)
     // the network tabulated on the feature nodes (vdw_learned_tabulate): node
     // (i1, i2), i = 0 .. T + 1, at x = -D + (i - 1) h, its 8 outputs at
-    // tab[((i1 (T + 2) + i2) 2] and [... + 1]; tabT = 0: no table
+    // node (i1, i2): channels 0-3 at tab[i1 (T + 2) + i2], 4-7 at the same
+    // index + (T + 2)^2; tabT = 0: no table
     const float4* tab;
     int tabT;
     float tabD, tab_h, tab_inv_h;

@@ -113,27 +113,46 @@ __device__ __forceinline__ Feat features(float n, float gx, float gy, float gz, 
 // (the derivative of the clamped basis is then zero).
 // bMq: the base splines' second derivatives (la.bMq, or a shared-memory copy
 // of it: indexed by the lane's interval, a parameter-space read serialises)
-__device__ __forceinline__ bool base_weights(float q, const LearnedArgs& la, float* p, float* dp,
-                                             const float* bMq) {
+// The coefficients shared by the channels at one q: interval k, A = (x1 - q)/h,
+// B = 1 - A and the cubic terms of the value and of d/dq.
+struct BaseCoef {
+    int k;
+    float A, B, cA, cB, dA, dB, ih;
+    bool inside;
+};
+__device__ __forceinline__ BaseCoef base_coef(float q, const LearnedArgs& la) {
+    BaseCoef c;
     const float lo = la.bqm[0], hi = la.bqm[LRN_M - 1];
-    const bool inside = (q >= lo) && (q <= hi);
+    c.inside = (q >= lo) && (q <= hi);
     const float qc = fminf(fmaxf(q, lo), hi);
     int k = 0;  // knots <= q among the interior ones: interval in [0, M - 2]
 #pragma unroll
     for (int i = 1; i < LRN_M - 1; ++i) k += (qc >= la.bqm[i]) ? 1 : 0;
-    const float x0 = la.bqm[k], x1 = la.bqm[k + 1], h = x1 - x0, ih = 1.f / h;
-    const float A = (x1 - qc) * ih, B = 1.f - A;
+    const float x0 = la.bqm[k], x1 = la.bqm[k + 1], h = x1 - x0;
+    c.k = k;
+    c.ih = 1.f / h;
+    c.A = (x1 - qc) * c.ih;
+    c.B = 1.f - c.A;
     const float h6 = h * h * (1.f / 6.f);
-    const float cA = (A * A * A - A) * h6, cB = (B * B * B - B) * h6;
-    const float dA = -(3.f * A * A - 1.f) * (1.f / 6.f) * h, dB = (3.f * B * B - 1.f) * (1.f / 6.f) * h;
+    c.cA = (c.A * c.A * c.A - c.A) * h6;
+    c.cB = (c.B * c.B * c.B - c.B) * h6;
+    c.dA = -(3.f * c.A * c.A - 1.f) * (1.f / 6.f) * h;
+    c.dB = (3.f * c.B * c.B - 1.f) * (1.f / 6.f) * h;
+    return c;
+}
+// p_m and dp_m/dq of channel m
+__device__ __forceinline__ void base_channel(const BaseCoef& c, int m, const float* bMq, float& p, float& dp) {
+    const float Ma = bMq[m * LRN_M + c.k], Mb = bMq[m * LRN_M + c.k + 1];
+    const float ya = (m == c.k) ? 1.f : 0.f, yb = (m == c.k + 1) ? 1.f : 0.f;
+    p = c.A * ya + c.B * yb + c.cA * Ma + c.cB * Mb;
+    dp = (yb - ya) * c.ih + c.dA * Ma + c.dB * Mb;
+}
+__device__ __forceinline__ bool base_weights(float q, const LearnedArgs& la, float* p, float* dp,
+                                             const float* bMq) {
+    const BaseCoef c = base_coef(q, la);
 #pragma unroll
-    for (int m = 0; m < LRN_M; ++m) {
-        const float Ma = bMq[m * LRN_M + k], Mb = bMq[m * LRN_M + k + 1];
-        const float ya = (m == k) ? 1.f : 0.f, yb = (m == k + 1) ? 1.f : 0.f;
-        p[m] = A * ya + B * yb + cA * Ma + cB * Mb;
-        dp[m] = (yb - ya) * ih + dA * Ma + dB * Mb;
-    }
-    return inside;
+    for (int m = 0; m < LRN_M; ++m) base_channel(c, m, bMq, p[m], dp[m]);
+    return c.inside;
 }
 
 // ---------------------------------------------------------------------------
@@ -562,8 +581,8 @@ __global__ void __launch_bounds__(L_THREADS, 1) k_learned_tabulate(LearnedArgs l
         float o[LRN_M];
         if (!mlp_forward(S, Wb + wg, &ctl, wg, r, phase, x1, x2, o, la.err)) break;
         if (in) {
-            tab[2 * i] = make_float4(o[0], o[1], o[2], o[3]);
-            tab[2 * i + 1] = make_float4(o[4], o[5], o[6], o[7]);
+            tab[i] = make_float4(o[0], o[1], o[2], o[3]);
+            tab[nodes + i] = make_float4(o[4], o[5], o[6], o[7]);
         }
     }
     mlp_teardown(&ctl);
@@ -593,15 +612,17 @@ __device__ __forceinline__ int table_axis(float x, const LearnedArgs& la, float&
 }
 
 // One thread per point (packed order, grid-stride); writes what k_learned_net
-// writes (theta channels, the assembly coefficients, Delta E partials).
+// writes (theta channels, the assembly coefficients, Delta E partials).  The
+// channels go in two halves of four (one float4 of each node per half), so
+// that a thread holds one half's sums at a time.
 constexpr int LOOKUP_THREADS = 256;
-__global__ void __launch_bounds__(LOOKUP_THREADS) k_learned_lookup(const float* __restrict__ n,
-                                                                  const float* __restrict__ grad, GridArgs g,
-                                                                  PointParams P, LearnedArgs la,
-                                                                  float* __restrict__ specf,
-                                                                  double* __restrict__ epart,
-                                                                  unsigned long long* __restrict__ invalid,
-                                                                  float* __restrict__ lw) {
+__global__ void __launch_bounds__(LOOKUP_THREADS, 3) k_learned_lookup(const float* __restrict__ n,
+                                                                     const float* __restrict__ grad, GridArgs g,
+                                                                     PointParams P, LearnedArgs la,
+                                                                     float* __restrict__ specf,
+                                                                     double* __restrict__ epart,
+                                                                     unsigned long long* __restrict__ invalid,
+                                                                     float* __restrict__ lw) {
     __shared__ double red[32];
     __shared__ float qm[MAX_NQ];
     __shared__ float bMq_s[LRN_M * LRN_M];
@@ -611,6 +632,7 @@ __global__ void __launch_bounds__(LOOKUP_THREADS) k_learned_lookup(const float* 
     const long long N = g.N;
     const long long fstride = 2LL * g.N2 * g.ncols;  // floats between the planes of two channels
     const int T2 = la.tabT + 2;
+    const long long hstride = (long long)T2 * T2;    // float4s between the two halves of the table
     double eacc = 0.0;
     unsigned int bad = 0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N; q += (long long)gridDim.x * blockDim.x) {
@@ -620,51 +642,10 @@ __global__ void __launch_bounds__(LOOKUP_THREADS) k_learned_lookup(const float* 
         bad += (!(ni >= 0.f) || !isfinite(ni)) ? 1u : 0u;
         const Feat f = features(ni, gx, gy, gz, la, P.n_min);
         const bool ok = f.ok;
-        // the network from the table
-        float s1, s2, ds1, ds2;
-        const int i1 = table_axis(ok ? f.x1 : 0.f, la, s1, ds1);
-        const int i2 = table_axis(ok ? f.x2 : 0.f, la, s2, ds2);
-        float a[4], da[4], b[4], db[4];
-        catmull_rom(s1, a, da);
-        catmull_rom(s2, b, db);
-        float o[LRN_M], J1[LRN_M], J2[LRN_M];
-#pragma unroll
-        for (int m = 0; m < LRN_M; ++m) o[m] = J1[m] = J2[m] = 0.f;
-        // per row k of nodes: R = sum_l b_l v, S = sum_l b'_l v; then
-        // o = sum_k a_k R_k, d/dx1 = sum_k a'_k R_k, d/dx2 = sum_k a_k S_k
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float4* row = la.tab + 2LL * ((long long)(i1 + k) * T2 + i2);
-            float R[LRN_M], Sd[LRN_M];
-#pragma unroll
-            for (int m = 0; m < LRN_M; ++m) R[m] = Sd[m] = 0.f;
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const float4 v0 = __ldg(row + 2 * l), v1 = __ldg(row + 2 * l + 1);
-                const float v[LRN_M] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-#pragma unroll
-                for (int m = 0; m < LRN_M; ++m) {
-                    R[m] = fmaf(b[l], v[m], R[m]);
-                    Sd[m] = fmaf(db[l], v[m], Sd[m]);
-                }
-            }
-#pragma unroll
-            for (int m = 0; m < LRN_M; ++m) {
-                o[m] = fmaf(a[k], R[m], o[m]);
-                J1[m] = fmaf(da[k], R[m], J1[m]);
-                J2[m] = fmaf(a[k], Sd[m], J2[m]);
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < LRN_M; ++m) {
-            J1[m] *= ds1;
-            J2[m] *= ds2;
-        }
-        // q chain: Delta E and the spline base
-        float pb[LRN_M], dpb[LRN_M];
-#pragma unroll
-        for (int m = 0; m < LRN_M; ++m) pb[m] = dpb[m] = 0.f;
+        // q chain: Delta E and the spline base's coefficients
         float bn = 0.f, bg = 0.f, dEn = 0.f, dEg = 0.f;
+        BaseCoef bc = {};
+        bool base_on = false;
         const QPoint qp = q_point(ni, gx, gy, gz, P, qm);
         if (qp.k != K_INVALID) {
             const float qq = qp.q, q3 = qq * qq * qq, q4 = q3 * qq;
@@ -672,22 +653,70 @@ __global__ void __launch_bounds__(LOOKUP_THREADS) k_learned_lookup(const float* 
             const float cn = 1.5f * P.C_s * ni * ni / q4;
             dEn = P.C_s * ni / q3 - cn * qp.dq_dn;
             dEg = -cn * qp.dq_dg;
-            if (la.base && base_weights(qq, la, pb, dpb, bMq_s)) {
-                bn = qp.dq_dn;
-                bg = qp.dq_dg;
+            if (la.base) {
+                // the clamped base has no q derivative
+                bc = base_coef(qq, la);
+                base_on = true;
+                if (bc.inside) {
+                    bn = qp.dq_dn;
+                    bg = qp.dq_dg;
+                }
             }
         }
+        // the network from the table: Catmull-Rom weights along both axes
+        float s1, s2, ds1, ds2;
+        const int i1 = table_axis(ok ? f.x1 : 0.f, la, s1, ds1);
+        const int i2 = table_axis(ok ? f.x2 : 0.f, la, s2, ds2);
+        float a[4], da[4], b[4], db[4];
+        catmull_rom(s1, a, da);
+        catmull_rom(s2, b, db);
         float* dst = specf + 2LL * y * g.ncols + packed_offset(x, j, z & 1, g.Nh);
+        const float4* node = la.tab + (long long)i1 * T2 + i2;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h, node += hstride) {
+            // per row k of nodes: R = sum_l b_l v, S = sum_l b'_l v; then
+            // o = sum_k a_k R_k, d/dx1 = sum_k a'_k R_k, d/dx2 = sum_k a_k S_k
+            float o[4], J1[4], J2[4];
 #pragma unroll
-        for (int m = 0; m < LRN_M; ++m) dst[m * fstride] = ok ? ni * (o[m] + pb[m]) : 0.f;
-        if (lw) {
+            for (int m = 0; m < 4; ++m) o[m] = J1[m] = J2[m] = 0.f;
 #pragma unroll
-            for (int m = 0; m < LRN_M; ++m) {
-                const float dwn = J1[m] * f.dx1_dn + J2[m] * f.dx2_dn + dpb[m] * bn;
-                const float dwg = J2[m] * f.gx2 + dpb[m] * bg;
-                lw[m * N + q] = ok ? o[m] + pb[m] + ni * dwn : 0.f;
-                lw[(LRN_M + m) * N + q] = ok ? ni * dwg : 0.f;
+            for (int k = 0; k < 4; ++k) {
+                float R[4], Sd[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) R[m] = Sd[m] = 0.f;
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const float4 v4 = __ldg(node + k * T2 + l);
+                    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        R[m] = fmaf(b[l], v[m], R[m]);
+                        Sd[m] = fmaf(db[l], v[m], Sd[m]);
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    o[m] = fmaf(a[k], R[m], o[m]);
+                    J1[m] = fmaf(da[k], R[m], J1[m]);
+                    J2[m] = fmaf(a[k], Sd[m], J2[m]);
+                }
             }
+#pragma unroll
+            for (int mm = 0; mm < 4; ++mm) {
+                const int m = 4 * h + mm;
+                float pb = 0.f, dpb = 0.f;
+                if (base_on) base_channel(bc, m, bMq_s, pb, dpb);
+                const float j1 = J1[mm] * ds1, j2 = J2[mm] * ds2;
+                dst[m * fstride] = ok ? ni * (o[mm] + pb) : 0.f;
+                if (lw) {
+                    const float dwn = j1 * f.dx1_dn + j2 * f.dx2_dn + dpb * bn;
+                    const float dwg = j2 * f.gx2 + dpb * bg;
+                    lw[m * N + q] = ok ? o[mm] + pb + ni * dwn : 0.f;
+                    lw[(LRN_M + m) * N + q] = ok ? ni * dwg : 0.f;
+                }
+            }
+        }
+        if (lw) {
             lw[2 * LRN_M * N + q] = ok ? dEn : 0.f;
             lw[(2 * LRN_M + 1) * N + q] = ok ? dEg : 0.f;
         }
@@ -1202,9 +1231,18 @@ int net_blocks(vdw_ctx* c) {
 }
 // blocks of the table lookup: grid-stride over the points, at most the
 // partial-sum slots the network kernel has
+// one wave of resident blocks (grid-stride loop), within the partial-sum slots
 int lookup_blocks(vdw_ctx* c) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_learned_lookup, LOOKUP_THREADS, 0) != cudaSuccess)
+            b = 1;
+        per_sm = std::max(1, b);
+    }
     const long long want = (c->g.N + LOOKUP_THREADS - 1) / LOOKUP_THREADS;
-    return (int)std::max(1LL, std::min<long long>(want, (long long)c->g.N2 * L_SLOTS));
+    const long long wave = (long long)std::max(1, c->nsm) * per_sm;
+    return (int)std::max(1LL, std::min(std::min(want, wave), (long long)c->g.N2 * L_SLOTS));
 }
 // knot-gradient bins of k_learned_contract_gradk
 size_t smem_gradk(int J) { return sizeof(float) * (size_t)LRN_P * J; }

@@ -16,6 +16,29 @@ struct QPoint {
     int k;        // mesh interval, or K_INVALID when theta = 0
 };
 
+// S = sum_{m=1}^{mc} y^m / m and dS/dy = sum_{m=0}^{mc-1} y^m by Horner's rule
+// (inv_m[m] = 1/m).
+template <int MC>
+__device__ __forceinline__ void saturation_sum(float y, const float* inv_m, float& S, float& dS) {
+    float a = inv_m[MC], d = 1.f;
+#pragma unroll
+    for (int m = MC - 1; m >= 1; --m) {
+        a = fmaf(a, y, inv_m[m]);
+        d = fmaf(d, y, 1.f);
+    }
+    S = a * y;
+    dS = d;
+}
+__device__ __forceinline__ void saturation_sum_n(float y, int mc, const float* inv_m, float& S, float& dS) {
+    float a = inv_m[mc], d = 1.f;
+    for (int m = mc - 1; m >= 1; --m) {
+        a = fmaf(a, y, inv_m[m]);
+        d = fmaf(d, y, 1.f);
+    }
+    S = a * y;
+    dS = d;
+}
+
 // qm: the q mesh (Nq values), normally a shared-memory copy of P.qm so that
 // the divergent interval search does not serialise on the constant bank.
 __device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz, const PointParams& P,
@@ -56,12 +79,9 @@ __device__ __forceinline__ QPoint q_point(float n, float gx, float gy, float gz,
     if (y > 4.f) {
         h = P.q_c; hp = 0.f;
     } else {
-        float S = 0.f, dS = 0.f, yp = 1.f;
-        for (int m = 1; m <= P.m_c; ++m) {
-            dS += yp;
-            yp *= y;
-            S = fmaf(yp, P.inv_m[m], S);
-        }
+        float S, dS;
+        if (P.m_c == 12) saturation_sum<12>(y, P.inv_m, S, dS);  // Dion et al.'s choice, unrolled
+        else saturation_sum_n(y, P.m_c, P.inv_m, S, dS);
         // 1 - exp(-S) through expm1: no cancellation for small q0
         const float em1 = expm1f(-S);
         h = -P.q_c * em1;

@@ -283,9 +283,10 @@ def load(path=TRAINED_PATH):
 
 
 def run(n_train=200, n_test=50, shape=(72, 180, 180), fit_steps=0, epochs=30, seed=0, out=TRAINED_PATH,
-        log=print):
+        beta=0.0, log=print):
     """The full experiment: 200 training and 50 held-out tube densities
-    (seeds 1000-1249), initialisation, training, evaluation."""
+    (seeds 1000-1249), initialisation, training (potential weight beta),
+    evaluation."""
     import torch
     t0 = time.time()
     ctx20 = vdwnl.VdwNL(vdwnl.Params(Nq=20))
@@ -311,9 +312,11 @@ def run(n_train=200, n_test=50, shape=(72, 180, 180), fit_steps=0, epochs=30, se
     err_init = energy_error_per_atom(ctx, test_s)
     log("held-out |dE|/atom: plain Nq=8 %.4f meV, learned init %.4f meV" %
         (np.abs(err8).mean() / HA_PER_MEV, np.abs(err_init).mean() / HA_PER_MEV))
-    hist = train(ctx, params, feat, train_s, epochs, base=base, log=log)
+    verr8 = potential_error(ctx8, test_s, learned=False)
+    hist = train(ctx, params, feat, train_s, epochs, base=base, beta=beta, log=log)
     err_tr = energy_error_per_atom(ctx, test_s)
     verr = potential_error(ctx, test_s)
+    vnorm = np.array([float(torch.sqrt((s.n * s.v_ref ** 2).sum() / s.n.sum())) for s in test_s])
     status = ctx.learned_status()
     res = dict(n_train=n_train, n_test=n_test, shape=list(shape), epochs=epochs, fit_steps=fit_steps,
                mae_mev_plain8=float(np.abs(err8).mean() / HA_PER_MEV),
@@ -322,7 +325,9 @@ def run(n_train=200, n_test=50, shape=(72, 180, 180), fit_steps=0, epochs=30, se
                max_mev_trained=float(np.abs(err_tr).max() / HA_PER_MEV),
                spread_mev_plain8=float((err8 - err8.mean()).std() / HA_PER_MEV),
                spread_mev_trained=float((err_tr - err_tr.mean()).std() / HA_PER_MEV),
-               v_wrms_trained=float(verr.mean()), history=hist, tc_error=status,
+               beta=beta, v_wrms_trained=float(verr.mean()),
+               v_rel_wrms_plain8=float((verr8 / vnorm).mean()), v_rel_wrms_trained=float((verr / vnorm).mean()),
+               history=hist, tc_error=status,
                seconds=time.time() - t0)
     log(json.dumps({k: v for k, v in res.items() if k != "history"}))
     if out:
@@ -337,6 +342,7 @@ if __name__ == "__main__":
     ap.add_argument("--test", type=int, default=50)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--fit-steps", type=int, default=0)
+    ap.add_argument("--beta", type=float, default=0.0)
     ap.add_argument("--out", default=TRAINED_PATH)
     a = ap.parse_args()
-    run(a.train, a.test, fit_steps=a.fit_steps, epochs=a.epochs, out=a.out)
+    run(a.train, a.test, fit_steps=a.fit_steps, epochs=a.epochs, out=a.out, beta=a.beta)

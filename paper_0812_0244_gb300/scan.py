@@ -78,7 +78,7 @@ def scan_energies(ctx, shape, z, phi, seed, dr_out, sub, learned, batch):
         ns = []
         for i, j, t in part:
             n64, _, _ = S.tube_density_torch(seed, shape=shape, shift_ang=float(z[i]), rot_deg=float(phi[j]),
-                                             dr_out_ang=dr_out, origin_bohr=t, device="cuda")
+                                             dr_out_ang=dr_out, origin_bohr=t, device="cuda", sites_alike=True)
             ns.append(n64.to(torch.float32))
         n = torch.stack(ns).contiguous()
         g = torch.stack([ctx.spectral_gradient(n[k]) for k in range(len(part))]).contiguous()
@@ -97,8 +97,10 @@ def run(nz=8, nphi=8, grids=(144, 180, 200), dr_out=(-0.2, 0.0, 0.2), seed=0, le
     """The wall scan: for each grid N x N x 72 and each outer-wall radius
     change dr (Angstrom), energies on an nz x nphi lattice of outer-wall
     shifts in [0, 2.46 A) and rotations in [0, 36 deg) (one density seed, so
-    the sites move rigidly), averaged over the sub^3 half-spacing
-    translations, and their energy maps (Eq. Uofx).  The learned path runs on
+    the sites move rigidly; all sites of a wall alike, so that each wall has
+    its translation, rotation and screw symmetries and the energy depends on
+    the wall position through the common superlattice only), averaged over the
+    sub^3 half-spacing translations, and their energy maps (Eq. Uofx).  The learned path runs on
     the grids whose largest |G| lies within its knots."""
     import torch
     z = np.arange(nz) * (2.0 * DZ_ANG) / nz

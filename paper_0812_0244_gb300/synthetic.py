@@ -102,11 +102,12 @@ def _gaussian_sum_torch(shape, L, centers, amps, sigmas, floor, device, cut=8.0)
 
 def tube_density_torch(seed=0, shape=(72, 180, 180), inner=5, outer=10, shift_ang=0.0, rot_deg=0.0,
                        dr_in_ang=0.0, dr_out_ang=0.0, cell_ang=(25.0, 25.0, 9.84), floor=1e-6, device="cuda",
-                       origin_bohr=(0.0, 0.0, 0.0)):
+                       origin_bohr=(0.0, 0.0, 0.0), sites_alike=False):
     """tube_density's density (same seeded draws) evaluated on a torch device;
     returns (n as an FP64 tensor, L, natoms).  For generating many training
     densities quickly; the gradient is left to the caller.  origin_bohr moves
-    the whole tube rigidly (periodic images included)."""
+    the whole tube rigidly (periodic images included); sites_alike as in
+    tube_density."""
     rng = np.random.default_rng(seed)
     L = np.asarray(cell_ang, np.float64) * BOHR_PER_ANG
     R_in = 3.0 * A_CC * inner / (2.0 * np.pi) + dr_in_ang
@@ -118,13 +119,7 @@ def tube_density_torch(seed=0, shape=(72, 180, 180), inner=5, outer=10, shift_an
     sites[:, 0] += 0.5 * L[0] + origin_bohr[0]
     sites[:, 1] += 0.5 * L[1] + origin_bohr[1]
     sites[:, 2] = np.mod(sites[:, 2] + origin_bohr[2], L[2])
-    centers, amps, sigmas = [], [], []
-    for c in sites:
-        w = rng.uniform(0.3, 0.7)
-        for q, s in ((4.0 * w, rng.uniform(0.4, 1.2)), (4.0 * (1.0 - w), rng.uniform(0.4, 1.2))):
-            centers.append(c)
-            amps.append(q / ((2.0 * np.pi) ** 1.5 * s ** 3))
-            sigmas.append(s)
+    centers, amps, sigmas = _site_gaussians(rng, sites, len(s_in), sites_alike)
     n = _gaussian_sum_torch(shape, L, centers, amps, sigmas, floor, device)
     return n, L, len(sites)
 
@@ -166,9 +161,31 @@ def armchair_sites(nidx, radius_ang, n_periods=4, phase_rad=0.0, z_shift_ang=0.0
     return np.array(out)
 
 
+def _site_gaussians(rng, sites, n_inner, alike):
+    """Two Gaussians per site carrying 4 e: charge split w : 1 - w with
+    w ~ U(0.3, 0.7) and widths ~ U(0.4, 1.2) bohr, drawn per site, or once per
+    wall when alike (every site of a wall the same, as carbon atoms are)."""
+    def draw():
+        w = rng.uniform(0.3, 0.7)
+        return w, rng.uniform(0.4, 1.2), rng.uniform(0.4, 1.2)
+
+    wall = (draw(), draw()) if alike else None
+    centers, amps, sigmas = [], [], []
+    for i, c in enumerate(sites):
+        w, s1, s2 = wall[0 if i < n_inner else 1] if alike else draw()
+        for q, s in ((4.0 * w, s1), (4.0 * (1.0 - w), s2)):
+            centers.append(c)
+            amps.append(q / ((2.0 * np.pi) ** 1.5 * s ** 3))
+            sigmas.append(s)
+    return centers, amps, sigmas
+
+
 def tube_density(seed=0, shape=(72, 180, 180), inner=5, outer=10, shift_ang=0.0, rot_deg=0.0,
-                 dr_in_ang=0.0, dr_out_ang=0.0, cell_ang=(25.0, 25.0, 9.84), floor=1e-6):
-    """Double-wall armchair tube density (4 e per carbon site, two Gaussians each)."""
+                 dr_in_ang=0.0, dr_out_ang=0.0, cell_ang=(25.0, 25.0, 9.84), floor=1e-6, sites_alike=False):
+    """Double-wall armchair tube density (4 e per carbon site, two Gaussians
+    each).  sites_alike: one set of Gaussian parameters per wall, so that the
+    density has the tube's translation, rotation and screw symmetries (the
+    wall scan needs them); otherwise independent parameters per site."""
     rng = np.random.default_rng(seed)
     L = np.asarray(cell_ang, np.float64) * BOHR_PER_ANG
     R_in = 3.0 * A_CC * inner / (2.0 * np.pi) + dr_in_ang
@@ -180,13 +197,7 @@ def tube_density(seed=0, shape=(72, 180, 180), inner=5, outer=10, shift_ang=0.0,
     sites[:, 0] += 0.5 * L[0]
     sites[:, 1] += 0.5 * L[1]
     sites[:, 2] = np.mod(sites[:, 2], L[2])
-    centers, amps, sigmas = [], [], []
-    for c in sites:
-        w = rng.uniform(0.3, 0.7)
-        for q, s in ((4.0 * w, rng.uniform(0.4, 1.2)), (4.0 * (1.0 - w), rng.uniform(0.4, 1.2))):
-            centers.append(c)
-            amps.append(q / ((2.0 * np.pi) ** 1.5 * s ** 3))
-            sigmas.append(s)
+    centers, amps, sigmas = _site_gaussians(rng, sites, len(s_in), sites_alike)
     n, g = _gaussian_sum(shape, L, centers, amps, sigmas, floor)
     return dict(n=n, grad=g, L=L, natoms=len(sites), centers=sites)
 

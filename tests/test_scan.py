@@ -59,7 +59,7 @@ def test_scan_energies_match_oracle(table):
     for i, zi in enumerate(z):
         for j, pj in enumerate(phi):
             n64, L, _ = S.tube_density_torch(0, shape=(72, 180, 180), shift_ang=float(zi), rot_deg=float(pj),
-                                             device="cuda")
+                                             device="cuda", sites_alike=True)
             n32 = n64.to(torch.float32).contiguous()
             if ctx is None:
                 ctx = vdwnl.VdwNL(vdwnl.Params()).plan(n32.shape, L)

@@ -21,3 +21,16 @@ def test_tube_charge_is_four_electrons_per_site():
     dOmega = np.prod(d["L"]) / d["n"].size
     floor = 1e-6 * np.prod(d["L"])
     assert abs((d["n"].sum() * dOmega - floor) / (4.0 * d["natoms"]) - 1.0) < 1e-3
+
+
+def test_alike_sites_have_the_outer_walls_screw_symmetry():
+    """With one set of Gaussian parameters per wall the outer (10,10) wall
+    is unchanged by its screw operation (half the axial period with 18
+    degrees) and by a full period; independent parameters per site are not."""
+    shape = (24, 48, 48)
+    ref = S.tube_density(7, shape=shape, sites_alike=True)["n"]
+    for z, phi in ((0.5 * S.T_ARM, 18.0), (S.T_ARM, 0.0), (0.0, 36.0)):
+        d = S.tube_density(7, shape=shape, shift_ang=z, rot_deg=phi, sites_alike=True)["n"]
+        assert np.abs(d - ref).max() <= 1e-12 * ref.max()
+    d = S.tube_density(7, shape=shape, shift_ang=0.5 * S.T_ARM, rot_deg=18.0)["n"]
+    assert np.abs(d - S.tube_density(7, shape=shape)["n"]).max() > 1e-3 * ref.max()
