@@ -63,10 +63,18 @@ TRAINED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "trained
 TAB_T, TAB_D = 769, 12.0
 
 
-def tube_config(seed, rng_seed=None):
-    """Seeded nanotube variant: outer wall shift U(0, 2.46 A), rotation U(0, 36 deg)."""
+# every ALIKE_EVERY-th seed (seed % ALIKE_EVERY == 0) gives a tube whose sites
+# are alike within each wall (synthetic.tube_density's sites_alike); 0: none
+ALIKE_EVERY = 0
+
+
+def tube_config(seed, rng_seed=None, alike_every=None):
+    """Seeded nanotube variant: outer wall shift U(0, 2.46 A), rotation
+    U(0, 36 deg); independent or (every alike_every-th seed) alike sites."""
     rng = np.random.default_rng(seed if rng_seed is None else rng_seed)
-    return dict(seed=int(seed), shift_ang=float(rng.uniform(0.0, 2.46)), rot_deg=float(rng.uniform(0.0, 36.0)))
+    k = ALIKE_EVERY if alike_every is None else alike_every
+    return dict(seed=int(seed), shift_ang=float(rng.uniform(0.0, 2.46)), rot_deg=float(rng.uniform(0.0, 36.0)),
+                alike=bool(k > 0 and seed % k == 0))
 
 
 @dataclass
@@ -91,7 +99,8 @@ def make_samples(configs, shape, ctx20, device="cuda", batch=8):
         ns, nas = [], []
         for cfg in part:
             n64, L, na = S.tube_density_torch(cfg["seed"], shape=shape, shift_ang=cfg["shift_ang"],
-                                              rot_deg=cfg["rot_deg"], device=device)
+                                              rot_deg=cfg["rot_deg"], device=device,
+                                              sites_alike=cfg.get("alike", False))
             ns.append(n64.to(torch.float32))
             nas.append(na)
         n = torch.stack(ns).contiguous()
@@ -283,7 +292,7 @@ def load(path=TRAINED_PATH):
 
 
 def run(n_train=200, n_test=50, shape=(72, 180, 180), fit_steps=0, epochs=30, seed=0, out=TRAINED_PATH,
-        beta=0.0, log=print):
+        beta=0.0, alike_every=None, lr_net=1e-5, lr_knots_rel=1e-5, log=print):
     """The full experiment: 200 training and 50 held-out tube densities
     (seeds 1000-1249), initialisation, training (potential weight beta),
     evaluation."""
@@ -294,7 +303,7 @@ def run(n_train=200, n_test=50, shape=(72, 180, 180), fit_steps=0, epochs=30, se
     ctx8 = vdwnl.VdwNL(p8)
     table8 = vdwnl.kernel_table(p8)
     table8["k_max"] = p8.k_max
-    cfgs = [tube_config(1000 + i) for i in range(n_train + n_test)]
+    cfgs = [tube_config(1000 + i, alike_every=alike_every) for i in range(n_train + n_test)]
     _, L, _ = S.tube_density_torch(cfgs[0]["seed"], shape=(8, 8, 8), device="cpu")
     ctx20.plan(shape, L)
     ctx8.plan(shape, L)
@@ -313,19 +322,24 @@ def run(n_train=200, n_test=50, shape=(72, 180, 180), fit_steps=0, epochs=30, se
     log("held-out |dE|/atom: plain Nq=8 %.4f meV, learned init %.4f meV" %
         (np.abs(err8).mean() / HA_PER_MEV, np.abs(err_init).mean() / HA_PER_MEV))
     verr8 = potential_error(ctx8, test_s, learned=False)
-    hist = train(ctx, params, feat, train_s, epochs, base=base, beta=beta, log=log)
+    hist = train(ctx, params, feat, train_s, epochs, lr_net=lr_net, lr_knots_rel=lr_knots_rel, base=base, beta=beta,
+                 log=log)
     err_tr = energy_error_per_atom(ctx, test_s)
     verr = potential_error(ctx, test_s)
     vnorm = np.array([float(torch.sqrt((s.n * s.v_ref ** 2).sum() / s.n.sum())) for s in test_s])
     status = ctx.learned_status()
+    alike_test = np.array([c["alike"] for c in cfgs[n_train:]])
     res = dict(n_train=n_train, n_test=n_test, shape=list(shape), epochs=epochs, fit_steps=fit_steps,
+               alike_every=ALIKE_EVERY if alike_every is None else alike_every,
+               mae_mev_trained_alike=float(np.abs(err_tr[alike_test]).mean() / HA_PER_MEV) if alike_test.any() else None,
+               mae_mev_plain8_alike=float(np.abs(err8[alike_test]).mean() / HA_PER_MEV) if alike_test.any() else None,
                mae_mev_plain8=float(np.abs(err8).mean() / HA_PER_MEV),
                mae_mev_init=float(np.abs(err_init).mean() / HA_PER_MEV),
                mae_mev_trained=float(np.abs(err_tr).mean() / HA_PER_MEV),
                max_mev_trained=float(np.abs(err_tr).max() / HA_PER_MEV),
                spread_mev_plain8=float((err8 - err8.mean()).std() / HA_PER_MEV),
                spread_mev_trained=float((err_tr - err_tr.mean()).std() / HA_PER_MEV),
-               beta=beta, v_wrms_trained=float(verr.mean()),
+               beta=beta, lr_net=lr_net, lr_knots_rel=lr_knots_rel, v_wrms_trained=float(verr.mean()),
                v_rel_wrms_plain8=float((verr8 / vnorm).mean()), v_rel_wrms_trained=float((verr / vnorm).mean()),
                history=hist, tc_error=status,
                seconds=time.time() - t0)
@@ -343,6 +357,10 @@ if __name__ == "__main__":
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--fit-steps", type=int, default=0)
     ap.add_argument("--beta", type=float, default=0.0)
+    ap.add_argument("--alike-every", type=int, default=None)
+    ap.add_argument("--lr-net", type=float, default=1e-5)
+    ap.add_argument("--lr-knots", type=float, default=1e-5)
     ap.add_argument("--out", default=TRAINED_PATH)
     a = ap.parse_args()
-    run(a.train, a.test, fit_steps=a.fit_steps, epochs=a.epochs, out=a.out, beta=a.beta)
+    run(a.train, a.test, fit_steps=a.fit_steps, epochs=a.epochs, out=a.out, beta=a.beta, alike_every=a.alike_every,
+        lr_net=a.lr_net, lr_knots_rel=a.lr_knots)
