@@ -39,7 +39,7 @@ extern "C" {
 #define VDW_ERR_CUDA (-3)    /* a CUDA runtime call failed                      */
 #define VDW_ERR_OOM (-4)     /* device allocation failed                         */
 #define VDW_ERR_STATE (-5)   /* call made before vdw_plan                        */
-#define VDW_ERR_UNSUPPORTED (-6) /* Nq not compiled in                           */
+#define VDW_ERR_UNSUPPORTED (-6) /* Nq not compiled in; non-orthorhombic cell     */
 #define VDW_ERR_TIMEOUT (-7) /* a kernel of an earlier call gave up a bounded
                                 wait (see vdw_wait_status); that call's
                                 results may be wrong                        */
@@ -114,6 +114,17 @@ int vdw_create(vdw_handle* h, const vdw_params* p, const double* phi_k, double C
  * N1 and N3 even, the largest |G| of the grid <= k_max.  May be called again
  * to re-plan.  Synchronous. */
 int vdw_plan(vdw_handle h, int n1, int n2, int n3, const double L[3]);
+
+/* vdw_plan with the cell given as its three lattice vectors (the form the
+ * method's reciprocal-space sums take for any cell: the wavevectors G of the
+ * grid and their lengths |G| come from the cell), cell[9] row-major, row i =
+ * lattice vector a_i (bohr) along which grid axis i (N1, N2, N3) runs.  This
+ * implementation takes orthorhombic cells: a cell whose off-diagonal entries
+ * are not zero (beyond 1e-12 of its largest diagonal entry) returns
+ * VDW_ERR_UNSUPPORTED and leaves the context as it was; otherwise it is
+ * vdw_plan with L = the diagonal (VDW_ERR_ARG if a diagonal entry is not
+ * positive).  Synchronous. */
+int vdw_plan_cell(vdw_handle h, int n1, int n2, int n3, const double cell[9]);
 
 /* E_c^nl and, on request, its potential (device pointers, caller-owned).
  *   n        [N]    density (FP32)

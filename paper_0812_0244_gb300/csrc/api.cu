@@ -308,6 +308,20 @@ int vdw_energy_potential(vdw_handle c, const float* n, const float* grad, double
     return pipeline_run(c, n, grad, E, v, w, (cudaStream_t)stream);
 }
 
+int vdw_plan_cell(vdw_handle c, int n1, int n2, int n3, const double cell[9]) {
+    if (!c || !cell) return VDW_ERR_ARG;
+    double dmax = 0.0;
+    for (int i = 0; i < 3; ++i) dmax = std::max(dmax, std::fabs(cell[4 * i]));
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (i != j && !(std::fabs(cell[3 * i + j]) <= 1e-12 * dmax)) {
+                set_error("vdw_plan_cell: only orthorhombic cells (diagonal lattice vectors) are supported");
+                return VDW_ERR_UNSUPPORTED;
+            }
+    const double L[3] = {cell[0], cell[4], cell[8]};
+    return vdw_plan(c, n1, n2, n3, L);
+}
+
 int vdw_plan_batch(vdw_handle c, int Bmax) {
     if (!c || Bmax < 1) return VDW_ERR_ARG;
     if (!c->planned) return VDW_ERR_STATE;

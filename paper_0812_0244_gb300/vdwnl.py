@@ -71,7 +71,7 @@ class Params:
 
 
 EXPORTS = ["vdw_params_default", "vdw_kernel_table", "vdw_create", "vdw_plan", "vdw_energy_potential",
-           "vdw_plan_batch", "vdw_energy_potential_batched",
+           "vdw_plan_batch", "vdw_plan_cell", "vdw_energy_potential_batched",
            "vdw_energy_potential_fd", "vdw_xc_energy_potential",
            "vdw_energy_potential_host", "vdw_last_invalid_points", "vdw_profile_enable", "vdw_profile_read",
            "vdw_delta_energy_noalloc", "vdw_spectral_gradient", "vdw_learned_param_count", "vdw_learned_load",
@@ -102,6 +102,7 @@ def lib():
     L.vdw_energy_potential.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.vdw_energy_potential_host.argtypes = [vp, fp, fp, dp, fp, vp]
     L.vdw_plan_batch.argtypes = [vp, ctypes.c_int]
+    L.vdw_plan_cell.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
     L.vdw_energy_potential_batched.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp]
     L.vdw_energy_potential_fd.argtypes = [vp, vp, vp, vp, vp, vp]
     L.vdw_xc_energy_potential.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, vp]
@@ -211,6 +212,16 @@ class VdwNL:
         _check(lib().vdw_plan(self._h, N1, N2, N3, _dptr(Lc)), "vdw_plan")
         self.shape = (N3, N2, N1)
         self.L = Lc.copy()
+        return self
+
+    def plan_cell(self, shape, cell):
+        """vdw_plan_cell: shape = (N3, N2, N1), cell = 3 x 3 lattice vectors
+        (rows, bohr) along the grid axes N1, N2, N3; orthorhombic only."""
+        N3, N2, N1 = (int(s) for s in shape)
+        cc = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
+        _check(lib().vdw_plan_cell(self._h, N1, N2, N3, _dptr(cc)), "vdw_plan_cell")
+        self.shape = (N3, N2, N1)
+        self.L = np.array([cc[0], cc[4], cc[8]])
         return self
 
     @property

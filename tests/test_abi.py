@@ -50,6 +50,7 @@ def test_host_only_entry_points(lib):
     assert lib.vdw_params_default(None) == -1
     assert lib.vdw_destroy(None) == -1
     assert lib.vdw_plan(None, 8, 8, 8, None) == -1
+    assert lib.vdw_plan_cell(None, 8, 8, 8, None) == -1
 
 
 def test_product_path_has_no_oracle_import():

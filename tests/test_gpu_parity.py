@@ -225,3 +225,26 @@ def test_two_live_contexts_of_different_grids(torch_cuda, vd, table):
             assert abs(float(E[0]) - ref["E"]) <= E_TOL
             vv = v.cpu().numpy().astype(np.float64)
             assert np.max(np.abs(vv - ref["v"])) <= V_REL * np.abs(ref["v"]).max()
+
+
+def test_plan_cell_takes_orthorhombic_cells(torch_cuda, vd, table):
+    """vdw_plan_cell with a diagonal cell is vdw_plan with its diagonal; a
+    skewed cell is refused and leaves the context's plan in place."""
+    torch = torch_cuda
+    d = S.two_atom_density(11, shape=(12, 12, 12))
+    n, g, L = f32(d["n"]), f32(d["grad"]), d["L"]
+    c = vd.VdwNL(vd.Params()).plan_cell(n.shape, np.diag(L))
+    nt = torch.tensor(np.asarray(n, np.float32), device="cuda")
+    gt = torch.tensor(np.asarray(g, np.float32), device="cuda")
+    E, v, _ = c.compute(nt, gt)
+    torch.cuda.synchronize()
+    ref = O.energy_potential(n, g, L, table)
+    assert abs(float(E[0]) - ref["E"]) <= E_TOL
+    skew = np.diag(L)
+    skew[1, 0] = 0.5
+    with pytest.raises(vd.VdwError) as e:
+        c.plan_cell(n.shape, skew)
+    assert e.value.code == -6
+    E2, _, _ = c.compute(nt, gt)
+    torch.cuda.synchronize()
+    assert float(E2[0]) == float(E[0])
