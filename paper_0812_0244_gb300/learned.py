@@ -54,7 +54,11 @@ H = vdwnl.LEARNED_H
 P = M * (M + 1) // 2
 OFF_K = 2 * H + H + H * H + H + M * H + M
 
+# the stored models: trained on tubes with independent parameters per site
+# (300 epochs), and on a set where every fourth tube has its sites alike
+# within each wall (600 epochs; the wall scan's densities are of that kind)
 TRAINED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "trained", "learned_m8_tube.npz")
+MIXED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "trained", "learned_m8_tube_mixed.npz")
 
 # Inference table of the network (vdw_learned_tabulate): 769 nodes per
 # feature over [-12, 12] (h = 1/32), covering the standardised features of the
@@ -291,7 +295,7 @@ def load(path=TRAINED_PATH):
                 base=tuple(float(x) for x in z["base"]), meta=json.loads(str(z["meta"])))
 
 
-def run(n_train=200, n_test=50, shape=(72, 180, 180), fit_steps=0, epochs=30, seed=0, out=TRAINED_PATH,
+def run(n_train=200, n_test=50, shape=(72, 180, 180), fit_steps=0, epochs=300, seed=0, out=TRAINED_PATH,
         beta=0.0, alike_every=None, lr_net=1e-5, lr_knots_rel=1e-5, log=print):
     """The full experiment: 200 training and 50 held-out tube densities
     (seeds 1000-1249), initialisation, training (potential weight beta),
@@ -354,7 +358,7 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser(description="train the learned reduced basis on tube densities")
     ap.add_argument("--train", type=int, default=200)
     ap.add_argument("--test", type=int, default=50)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--fit-steps", type=int, default=0)
     ap.add_argument("--beta", type=float, default=0.0)
     ap.add_argument("--alike-every", type=int, default=None)

@@ -110,7 +110,7 @@ def run(nz=8, nphi=8, grids=(144, 180, 200), dr_out=(-0.2, 0.0, 0.2), seed=0, le
     mdl = None
     if learned:
         try:
-            mdl = LR.load()
+            mdl = LR.load(LR.MIXED_PATH)  # trained with alike-site tubes among its densities
         except OSError as ex:
             log("learned path skipped: %s" % ex)
     t0 = time.time()

@@ -1,13 +1,15 @@
 """What the trained network gains over the method without it, as inference
 runs it (the network tabulated on its feature nodes).
 
-The stored model (paper_0812_0244_gb300/trained/learned_m8_tube.npz) was
-trained on the GPU by ``python -m paper_0812_0244_gb300.learned`` (the
-library's own forward, parameter-gradient and Adam kernels) on 200 tube
-densities (seeds 1000-1199).  On the 50 held-out densities (seeds 1200-1249)
-its energy error against the plain Nq = 20 path is compared with that of the
-plain method at equal cost: 8 channels on the same mesh, which is also the
-learned model's starting point."""
+The stored models (paper_0812_0244_gb300/trained/) were trained on the GPU by
+``python -m paper_0812_0244_gb300.learned`` (the library's own forward,
+parameter-gradient and Adam kernels) on 200 tube densities (seeds
+1000-1199): learned_m8_tube.npz on tubes with independent Gaussian parameters
+per site, learned_m8_tube_mixed.npz on a set where every fourth tube has its
+sites alike within each wall.  On the 50 held-out densities of the same
+recipe (seeds 1200-1249) each model's energy error against the plain Nq = 20
+path is compared with that of the plain method at equal cost: 8 channels on
+the same mesh, which is also the learned model's starting point."""
 import os
 
 import numpy as np
@@ -16,16 +18,25 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
+# (model, bound on the mean, bound on the largest held-out error), meV/atom;
+# the 0.1 meV/atom tolerance of the learned path holds at every held-out
+# density for the first model and on average for the second
+MODELS = [("learned_m8_tube.npz", 0.1, 0.1), ("learned_m8_tube_mixed.npz", 0.1, 0.15)]
+
+
 @pytest.mark.slow
-def test_trained_model_beats_plain_eight_channels():
+@pytest.mark.parametrize("name,mean_bound,max_bound", MODELS, ids=["independent_sites", "mixed"])
+def test_trained_model_beats_plain_eight_channels(name, mean_bound, max_bound):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_0812_0244_gb300 import learned as LR
     from paper_0812_0244_gb300 import synthetic as S
     from paper_0812_0244_gb300 import vdwnl
-    assert os.path.exists(LR.TRAINED_PATH)
-    mdl = LR.load()
+    path = os.path.join(os.path.dirname(LR.TRAINED_PATH), name)
+    assert os.path.exists(path)
+    mdl = LR.load(path)
+    alike_every = int(mdl["meta"]["alike_every"])
     shape = (72, 180, 180)
     _, L, _ = S.tube_density_torch(1200, shape=(8, 8, 8), device="cpu")
     ctx20 = vdwnl.VdwNL(vdwnl.Params()).plan(shape, L)
@@ -35,7 +46,8 @@ def test_trained_model_beats_plain_eight_channels():
     params = torch.tensor(mdl["params"], dtype=torch.float32, device="cuda")
     ctx.learned_load(params, mdl["J"], mdl["k_max"], mdl["feat"], mdl["base"])
     ctx.learned_tabulate(LR.TAB_T, LR.TAB_D)
-    test_s, _ = LR.make_samples([LR.tube_config(1200 + i) for i in range(50)], shape, ctx20)
+    cfgs = [LR.tube_config(1200 + i, alike_every=alike_every) for i in range(50)]
+    test_s, _ = LR.make_samples(cfgs, shape, ctx20)
     err8 = LR.energy_error_per_atom(ctx8, test_s, learned=False) / LR.HA_PER_MEV
     errl = LR.energy_error_per_atom(ctx, test_s) / LR.HA_PER_MEV
     assert ctx.learned_status() == 0
@@ -45,10 +57,12 @@ def test_trained_model_beats_plain_eight_channels():
     v8 = LR.potential_error(ctx8, test_s, learned=False)
     vl = LR.potential_error(ctx, test_s)
     vref = np.array([float(torch.sqrt((s.n * s.v_ref ** 2).sum() / s.n.sum())) for s in test_s])
-    print("held-out MAE meV/atom: plain 8 channels %.4f, trained %.4f (max %.4f); potential rel. RMS: plain 8 "
-          "channels %.3f, trained %.3f" % (mae8, mael, np.abs(errl).max(), (v8 / vref).mean(), (vl / vref).mean()))
+    print("%s held-out MAE meV/atom: plain 8 channels %.4f, trained %.4f (max %.4f); potential rel. RMS: plain 8 "
+          "channels %.3f, trained %.3f" % (name, mae8, mael, np.abs(errl).max(), (v8 / vref).mean(),
+                                           (vl / vref).mean()))
     assert mael < mae8
-    assert mael < 0.1
+    assert mael < mean_bound
+    assert np.abs(errl).max() < max_bound
     # no 8-channel basis follows the Nq = 20 potential closely (its divergence
     # term at low density differs by the size of v): the learned potential
     # is pinned to be no worse than the plain method at equal cost

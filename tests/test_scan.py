@@ -48,7 +48,7 @@ def test_scan_energies_match_oracle(table):
     res = scan.run(nz=2, nphi=2, grids=(180,), dr_out=(0.0,), sub=1, learned=True, log=lambda s: None)
     case = res["cases"][0]
     Ep, El = np.array(case["E_plain_ha"]), np.array(case["E_learned_ha"])
-    mdl = LR.load()
+    mdl = LR.load(LR.MIXED_PATH)  # the model the scan runs
     mo = LO.random_model(0, J=mdl["J"], k_max=mdl["k_max"], base=mdl["base"]).with_flat(
         np.asarray(mdl["params"], np.float64))
     mo.mu1, mo.sig1, mo.mu2, mo.sig2, mo.eps = mdl["feat"]
