@@ -255,8 +255,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 4) k_contract_sorted(float4* __r
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// forward kernel: lines and twiddles; inverse kernel: also the staged positions
+size_t sorted_pencil_smem_fwd(const GridArgs& g) { return pencil_pos_offset(PEN_COLS, pencil_stride(g.N2), g.N2); }
 size_t sorted_pencil_smem(const GridArgs& g) {
-    return pencil_pos_offset(PEN_COLS, pencil_stride(g.N2), g.N2) + sizeof(unsigned) * PEN_COLS * g.N2;
+    return sorted_pencil_smem_fwd(g) + sizeof(unsigned) * PEN_COLS * g.N2;
 }
 
 // |G| order of the half spectrum: pos[col N2 + y] = sorted position of the
@@ -315,9 +317,8 @@ void sorted_free(vdw_ctx* c) {
 
 template <int CN2>
 static int configure_sorted_sized(vdw_ctx* c) {
-    const int sm = (int)sorted_pencil_smem(c->g);
-    int rc = raise_smem_limit(k_pencil_fwd<CN2>, sm);
-    if (!rc) rc = raise_smem_limit(k_pencil_inv<CN2>, sm);
+    int rc = raise_smem_limit(k_pencil_fwd<CN2>, (int)sorted_pencil_smem_fwd(c->g));
+    if (!rc) rc = raise_smem_limit(k_pencil_inv<CN2>, (int)sorted_pencil_smem(c->g));
     if (rc) return rc;
     int dev = 0;
     VDW_CUDA(cudaGetDevice(&dev));
@@ -350,7 +351,7 @@ static int sized_n2(const GridArgs& g) {
 int sorted_forward(vdw_ctx* c, int nfields, cudaStream_t s, int B) {
     const GridArgs& g = c->g;
     const dim3 grid((g.ncols + PEN_COLS - 1) / PEN_COLS, nfields / 4, B);
-    const size_t sm = sorted_pencil_smem(g);
+    const size_t sm = sorted_pencil_smem_fwd(g);
     VDW_SORTED_LAUNCH(k_pencil_fwd, c->d_spec, g, c->d_tw, c->d_pos, c->d_Q, 2 * c->Npad, PEN_COLS)
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
