@@ -171,10 +171,13 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity)
     return false;
 }
 
+// Three blocks per SM at N1 = 180 (80 registers, a few spilled: 0.160 and
+// 0.157 ms for the forward and inverse stage against 0.171 and 0.165 ms at
+// two blocks); two elsewhere.
 template <int CN1, int CN3, bool INV>
-__global__ void __launch_bounds__(PLANE_THREADS, 2) k_planes_inplace(float2* __restrict__ spec, GridArgs g,
-                                                                     const Tw* __restrict__ tw, int bulk,
-                                                                     int* __restrict__ wait_err) {
+__global__ void __launch_bounds__(PLANE_THREADS, CN1 == 180 ? 3 : 2)
+    k_planes_inplace(float2* __restrict__ spec, GridArgs g, const Tw* __restrict__ tw, int bulk,
+                     int* __restrict__ wait_err) {
     extern __shared__ float2 sm[];
     __shared__ uint64_t bar;
     float2* plane = sm;
