@@ -114,6 +114,19 @@ def captured_traffic(stage):
     return int(vals[stage])
 
 
+def slowest_rank(x, world, dev=None):
+    """The largest of each rank's x (max over the ranks of the process group;
+    x itself for one rank): the timed region of a replica run is that of its
+    slowest replica."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def b_alg(Nq):
     """Whole-call algorithmic bytes per point, 16 Nq + 76 (one HBM round trip
     of the Nq spectra per direction, inputs and outputs once)."""
@@ -413,12 +426,8 @@ def main():
         torch.cuda.synchronize()
         clk.mark("stop")
         barrier()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N / (ms * 1e-3)
+    ms = slowest_rank(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / K, world, dev)
+    value = world * N / (ms * 1e-3)  # the points of all replicas over the slowest one's time
     Eh = E.cpu().numpy()
     peak, peak_kind = measured_peaks()
     clocks = clk.summary() if rank == 0 else None
@@ -587,10 +596,7 @@ def main():
         ctx.energy_potential_host(n_p.numpy(), g_p.numpy(), E_p, v_p.numpy())
     e2e_s = (time.perf_counter() - t0) / Ke
     barrier()
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = slowest_rank(e2e_s, world, dev)
 
     if rank == 0:
         stage_frac = {k2: round(sb[k2] * N / (t2 * 1e-3) / 1e9 / peak, 4) for k2, t2 in acc.items() if sb[k2] > 0}

@@ -52,3 +52,37 @@ def test_committed_traffic_file_names_its_sources():
     path = os.path.join(os.path.dirname(bench.__file__), "profiles", "dram_traffic_dwnt_180x180x72_nq20.txt")
     keys = [line.split()[0] for line in open(path) if line.strip() and not line.startswith("#")]
     assert keys[0] == "source_sha1" and "contract" in keys
+
+
+def _replica_rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.slowest_rank(1.0 + rank, world)   # rank r took 1 + r ms
+        dist.barrier()
+        out[rank] = ms
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_timing_takes_the_slowest_rank():
+    """The N > 1 path of bench.py (replicas, one cell per rank): every rank
+    ends with the slowest rank's time, so value = world x points / max time.
+    Two gloo ranks on the CPU."""
+    torch = pytest.importorskip("torch")
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    procs = [ctx.Process(target=_replica_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert dict(out) == {0: 2.0, 1: 2.0}
+    assert bench.slowest_rank(3.5, 1) == 3.5
