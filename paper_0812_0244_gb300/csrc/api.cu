@@ -96,7 +96,7 @@ int alloc_density_work(vdw_ctx* c, int Bmax) {
     const size_t Nq = (size_t)c->p.Nq, N = (size_t)g.N;
     const size_t spec_n = Nq * g.N2 * g.ncols, wspec_n = 3 * (size_t)g.N2 * g.ncols;
     const size_t q_n = Nq * (size_t)c->Npad / 2;  // float4 values (Nq/4 quads of Npad 32-byte records)
-    const size_t ep_n = (size_t)c->nb_point + c->nb_sorted;
+    const size_t ep_n = (size_t)c->nb_point + c->nb_sorted + 2 * EPART_SPLIT;
     const size_t old = c->batch_max > 0
                            ? (size_t)c->batch_max * (8 * (spec_n + wspec_n) + 16 * q_n + 25 * N + 8 * ep_n)
                            : 0;

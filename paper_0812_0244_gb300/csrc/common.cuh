@@ -264,6 +264,12 @@ int sorted_contract(vdw_ctx* c, double* epart, int write_back, cudaStream_t s, i
 int sorted_contract_table(vdw_ctx* c, int nq, const float4* table, float inv_dk, int nk, double* epart,
                           int write_back, cudaStream_t s, int B = 1);
 constexpr int SORTED_BLOCK = 128;  // sorted points per contraction block
+// The energy's partial sums (one per block of the pointwise pass and of the
+// contraction) are reduced in two passes: EPART_SPLIT blocks each sum a fixed
+// contiguous share of both arrays, one block sums their EPART_SPLIT results in
+// index order.  The per-density partial-sum array ends with those 2
+// EPART_SPLIT values.
+constexpr int EPART_SPLIT = 64;
 
 // learned reduced basis (learned.cu)
 int learned_run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, float* w, cudaStream_t s);

@@ -544,34 +544,43 @@ __global__ void k_xc_final(const double* __restrict__ Enl, const double* __restr
 }
 
 // ---------------------------------------------------------------------------
-// energy: fixed-order FP64 reduction of the block partials
+// energy: fixed-order FP64 reduction of the block partials, in two passes
+// (the GPU's FP64 rate is low: one block summing all partials took 17 us)
 // ---------------------------------------------------------------------------
-// Fixed order: thread i sums entries i, i + 4 B, i + 8 B, ... into four
-// interleaved accumulators (B threads), then the block sum.
-__device__ __forceinline__ double strided_sum4(const double* __restrict__ p, int n) {
-    const int B = blockDim.x;
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < n; i += 4 * B) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (i + k * B < n) a[k] += p[i + k * B];
-    }
-    return (a[0] + a[1]) + (a[2] + a[3]);
-}
+constexpr int ESPLIT_THREADS = 256;
 
-constexpr int ENERGY_THREADS = 1024;
-
-__global__ void __launch_bounds__(ENERGY_THREADS) k_energy_final(const double* __restrict__ epart, int nb0, int nb2,
-                                                                 double s0, double s2, double* __restrict__ E,
-                                                                 int bs_epart) {
+// First pass: block b of density blockIdx.y sums the share
+// [b n / EPART_SPLIT, (b + 1) n / EPART_SPLIT) of each partial-sum array.
+__global__ void __launch_bounds__(ESPLIT_THREADS) k_energy_split(const double* __restrict__ epart, int nb0, int nb2,
+                                                                 double* __restrict__ escr, int bs_epart) {
     __shared__ double red[32];
-    epart += (long long)blockIdx.x * bs_epart;  // density blockIdx.x of a batch
-    E += 3 * blockIdx.x;
-    const double a0 = strided_sum4(epart, nb0);
-    const double a2 = strided_sum4(epart + nb0, nb2);
+    epart += (long long)blockIdx.y * bs_epart;  // density blockIdx.y of a batch
+    escr += (long long)blockIdx.y * bs_epart;
+    const long long b = blockIdx.x;
+    const int lo0 = (int)(b * nb0 / EPART_SPLIT), hi0 = (int)((b + 1) * nb0 / EPART_SPLIT);
+    const int lo2 = (int)(b * nb2 / EPART_SPLIT), hi2 = (int)((b + 1) * nb2 / EPART_SPLIT);
+    double a0 = 0.0, a2 = 0.0;
+    for (int i = lo0 + threadIdx.x; i < hi0; i += blockDim.x) a0 += epart[i];
+    for (int i = lo2 + threadIdx.x; i < hi2; i += blockDim.x) a2 += epart[nb0 + i];
     const double t0 = block_sum(a0, red);
     __syncthreads();
     const double t2 = block_sum(a2, red);
+    if (threadIdx.x == 0) {
+        escr[b] = t0;
+        escr[EPART_SPLIT + b] = t2;
+    }
+}
+
+// Second pass (EPART_SPLIT threads per density): the shares in index order,
+// scaled into {E, E_soft, Delta E}.
+__global__ void __launch_bounds__(EPART_SPLIT) k_energy_final(const double* __restrict__ escr, double s0, double s2,
+                                                              double* __restrict__ E, int bs_epart) {
+    __shared__ double red[32];
+    escr += (long long)blockIdx.x * bs_epart;  // density blockIdx.x of a batch
+    E += 3 * blockIdx.x;
+    const double t0 = block_sum(escr[threadIdx.x], red);
+    __syncthreads();
+    const double t2 = block_sum(escr[EPART_SPLIT + threadIdx.x], red);
     if (threadIdx.x == 0) {
         const double dE = s0 * t0, Es = s2 * t2;
         E[0] = Es + dE;
@@ -732,8 +741,10 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
     if (E) {
         const double Omega = c->L[0] * c->L[1] * c->L[2];
         const double Nd = (double)g.N;
-        k_energy_final<<<B, ENERGY_THREADS, 0, s>>>(c->d_epart, c->nb_point, c->nb_sorted, Omega / Nd,
-                                         0.5 * Omega / (Nd * Nd), E, g.bs_epart);
+        double* escr = c->d_epart + c->nb_point + c->nb_sorted;
+        k_energy_split<<<dim3(EPART_SPLIT, B), ESPLIT_THREADS, 0, s>>>(c->d_epart, c->nb_point, c->nb_sorted, escr,
+                                                                       g.bs_epart);
+        k_energy_final<<<B, EPART_SPLIT, 0, s>>>(escr, Omega / Nd, 0.5 * Omega / (Nd * Nd), E, g.bs_epart);
         mark(ST_ENERGY);
     }
     if (xc && !want_pot)
@@ -875,7 +886,10 @@ int pipeline_divergence(vdw_ctx* c, float* v, cudaStream_t s) {
 int pipeline_energy_final(vdw_ctx* c, const double* epart, int nb0, int nb2, double* E, cudaStream_t s) {
     const double Omega = c->L[0] * c->L[1] * c->L[2];
     const double Nd = (double)c->g.N;
-    k_energy_final<<<1, ENERGY_THREADS, 0, s>>>(epart, nb0, nb2, Omega / Nd, 0.5 * Omega / (Nd * Nd), E, 0);
+    // the shares go to the context's own scratch (after density 0's partial sums)
+    double* escr = c->d_epart + c->nb_point + c->nb_sorted;
+    k_energy_split<<<dim3(EPART_SPLIT, 1), ESPLIT_THREADS, 0, s>>>(epart, nb0, nb2, escr, 0);
+    k_energy_final<<<1, EPART_SPLIT, 0, s>>>(escr, Omega / Nd, 0.5 * Omega / (Nd * Nd), E, 0);
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
 }
