@@ -8,7 +8,7 @@ results:
 * the library's spectral gradient of a seeded field against numpy's FFT
   (both directions of every line transform at lengths 256 and 96, including
   the rotated radix-16 first pass of length 256);
-* E_c^nl and v_nl of the tube against the FP64 oracle, at the north-star
+* E_c^nl and v_nl of the tube against the FP64 oracle, within the path's
   tolerances |Delta E| <= 1e-6 Ha and max|Delta v| <= 1e-5 max|v|;
 * the autograd Function (theta recomputed in the backward) against the same
   oracle potential.
