@@ -22,6 +22,7 @@ of the paper's Table I.
 from __future__ import annotations
 
 import json
+import math
 import time
 
 import numpy as np
@@ -31,9 +32,64 @@ from . import synthetic as S
 from . import vdwnl
 
 MEV_PER_HA = 27211.386245988
-DZ_ANG = 0.5 * S.T_ARM          # axial period of the energy map
-DPHI_DEG = 18.0                  # rotational period of the energy map
 OUTER_ATOMS = 160                # (10,10) wall, four axial periods
+
+
+def wall_lattice(n, m, a_cc=S.A_CC, axial_scale=1.0):
+    """Bravais lattice of the unrolled (n, m) wall: two primitive vectors as
+    rows, in (s, z) = (along the circumference, along the axis), Angstrom;
+    with the circumference |C| and the axial period |T|.  C = n a1 + m a2 is
+    the chiral vector of the graphene lattice (|a1| = |a2| = sqrt(3) a_cc),
+    T the shortest lattice vector perpendicular to it; axial_scale stretches
+    z (the synthetic armchair walls use an axial period of 2.46 A)."""
+    a = np.sqrt(3.0) * a_cc
+    a1 = a * np.array([np.sqrt(3.0) / 2.0, 0.5])
+    a2 = a * np.array([np.sqrt(3.0) / 2.0, -0.5])
+    C = n * a1 + m * a2
+    dR = math.gcd(2 * m + n, 2 * n + m)
+    T = ((2 * m + n) // dR) * a1 - ((2 * n + m) // dR) * a2
+    c, t = C / np.linalg.norm(C), T / np.linalg.norm(T)
+    A = np.array([[a1 @ c, axial_scale * (a1 @ t)], [a2 @ c, axial_scale * (a2 @ t)]])
+    return A, float(np.linalg.norm(C)), float(axial_scale * np.linalg.norm(T))
+
+
+def superlattice_periods(inner, outer, a_cc=S.A_CC, axial_scale=1.0, kmax=40):
+    """The construction of the energy map (text before Eq. Uofx): the inner
+    wall projected onto the outer surface (its circumferential coordinate
+    scaled by R_out/R_in = |C_out|/|C_in|), both walls unrolled, and the
+    superlattice wavevectors G = those common to both reciprocal lattices.
+    Returns the periodicities 2 pi/|G| of the shortest G along the axis
+    (dx_z) and along the circumference (dx_phi, measured on the outer
+    circumference), both in Angstrom, the angular period dphi_deg, and the
+    shortest common G (length, angle from the axis in degrees)."""
+    Ai, Li, _ = wall_lattice(*inner, a_cc=a_cc, axial_scale=axial_scale)
+    Ao, Lo, _ = wall_lattice(*outer, a_cc=a_cc, axial_scale=axial_scale)
+    Ai = Ai * np.array([Lo / Li, 1.0])
+    common = []
+    for k1 in range(-kmax, kmax + 1):
+        for k2 in range(-kmax, kmax + 1):
+            if k1 == 0 and k2 == 0:
+                continue
+            G = 2.0 * np.pi * np.linalg.solve(Ao, np.array([k1, k2], np.float64))  # G . a_j = 2 pi k_j
+            ki = Ai @ G / (2.0 * np.pi)
+            if np.all(np.abs(ki - np.round(ki)) < 1e-6):
+                common.append(G)
+    common = np.array(common)
+    length = np.linalg.norm(common, axis=1)
+    tol = 1e-9 * length.max()
+    gz = np.abs(common[np.abs(common[:, 0]) < tol, 1])
+    gs = np.abs(common[np.abs(common[:, 1]) < tol, 0])
+    dx_z = 2.0 * np.pi / gz.min()
+    dx_phi = 2.0 * np.pi / gs.min()
+    i = int(np.argmin(length))
+    return dict(dx_z=float(dx_z), dx_phi=float(dx_phi), dphi_deg=float(360.0 * dx_phi / Lo),
+                shortest=(float(length[i]), float(np.degrees(np.arctan2(abs(common[i, 0]), abs(common[i, 1]))))))
+
+
+# the scanned (5,5)@(10,10) tube: the walls of synthetic.armchair_sites
+_PERIODS = superlattice_periods((5, 5), (10, 10), axial_scale=S.T_ARM / (np.sqrt(3.0) * S.A_CC))
+DZ_ANG = _PERIODS["dx_z"]         # axial period of the energy map (1.23 A)
+DPHI_DEG = _PERIODS["dphi_deg"]   # rotational period of the energy map (18 degrees)
 
 
 def fit_energy_map(z_ang, phi_deg, E_mev, r_out_ang):
@@ -142,7 +198,8 @@ def run(nz=8, nphi=8, grids=(144, 180, 200), dr_out=(-0.2, 0.0, 0.2), seed=0, le
             log(json.dumps({k: v for k, v in case.items() if not k.startswith("E_")}))
         ctx.close()
     torch.cuda.synchronize()
-    return dict(nz=nz, nphi=nphi, sub=sub, seconds=time.time() - t0, cases=cases)
+    return dict(nz=nz, nphi=nphi, sub=sub, seconds=time.time() - t0, dx_z_ang=DZ_ANG,
+                dx_phi_ang=_PERIODS["dx_phi"], dphi_deg=DPHI_DEG, cases=cases)
 
 
 if __name__ == "__main__":

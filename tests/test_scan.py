@@ -72,3 +72,37 @@ def test_scan_energies_match_oracle(table):
             assert abs(Ep[i, j] - Eo) < 1e-6, (i, j, Ep[i, j], Eo)
             Elo = LO.energy_potential(n, g, L, mo, table, want_v=False, table=tab)["E"]
             assert abs(El[i, j] - Elo) <= 1e-5 * abs(Elo), (i, j, El[i, j], Elo)
+
+
+def test_superlattice_periods_reproduce_table_I():
+    """The periodicities of the energy maps follow from the walls' lattices
+    alone (project the inner wall onto the outer surface, unroll, intersect
+    the reciprocal lattices).  With a_cc = 1.42 A they reproduce the six
+    values the paper prints for its three tubes to within their rounding and
+    a common scale (the paper's relaxed bond is ~1 % longer), including the
+    chiral (8,2)@(16,4) tube whose superlattice is much finer."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table1_periodicities.json")))
+    ratios = []
+    for name, t in gold["tubes"].items():
+        p = scan.superlattice_periods(tuple(t["inner"]), tuple(t["outer"]), a_cc=1.42)
+        for key in ("dx_z", "dx_phi"):
+            ratios.append(t[key] / p[key])
+            assert abs(p[key] / t[key] - 1.0) < 0.02, (name, key, p[key], t[key])
+    ratios = np.array(ratios)
+    # one scale for all six (printed to two decimals: +-0.005 / 0.47 at worst)
+    assert np.ptp(ratios) < 0.02
+    assert abs(ratios.mean() - 1.01) < 0.01
+
+
+def test_scan_periods_are_those_of_the_scanned_walls():
+    """The (5,5)@(10,10) tube of the scan: half its axial period and the arc
+    of 18 degrees (a twentieth of the turn) on the outer wall."""
+    assert abs(scan.DZ_ANG - 0.5 * 2.46) < 1e-12
+    assert abs(scan.DPHI_DEG - 18.0) < 1e-9
+    # the projection stretches the inner wall's circumference onto the outer one's
+    Ai, Li, _ = scan.wall_lattice(5, 5)
+    Ao, Lo, _ = scan.wall_lattice(10, 10)
+    assert abs(Lo / Li - 2.0) < 1e-12
+    assert abs(Lo - 3.0 * 1.42 * 10) < 1e-12
