@@ -79,6 +79,11 @@ static void free_plan(vdw_ctx* c) {
     learned_free(c);
     sorted_free(c);
     if (c->s_copy) cudaStreamDestroy(c->s_copy);
+    if (c->s_side) cudaStreamDestroy(c->s_side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    c->s_side = nullptr;
+    c->ev_fork = c->ev_join = nullptr;
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     for (int i = 0; i < 4; ++i)
         if (c->ev_slab[i]) cudaEventDestroy(c->ev_slab[i]);
@@ -279,6 +284,9 @@ int vdw_plan(vdw_handle c, int n1, int n2, int n3, const double L[3]) {
     c->wait_seen = 0;
     VDW_CUDA(cudaMalloc(&c->d_xc, sizeof(double) * (4 + 2 * 1024)));
     VDW_CUDA(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
+    VDW_CUDA(cudaStreamCreateWithFlags(&c->s_side, cudaStreamNonBlocking));
+    VDW_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    VDW_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     VDW_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     for (int i = 0; i < 4; ++i) VDW_CUDA(cudaEventCreateWithFlags(&c->ev_slab[i], cudaEventDisableTiming));
     VDW_CUDA(cudaMemset(c->d_invalid, 0, sizeof(unsigned long long)));

@@ -157,6 +157,8 @@ struct vdw_ctx {
     cudaStream_t s_copy;        // copy stream of the host entry point
     cudaEvent_t ev_in;          // orders the copy stream after the caller's stream
     cudaEvent_t ev_slab[4];     // slab c of the inputs is on the device
+    cudaStream_t s_side;        // the energy reduction beside the inverse transforms
+    cudaEvent_t ev_fork, ev_join;
     unsigned long long* d_invalid;  // count of negative / non-finite densities
     int bulk_planes;            // inverse plane transforms load their planes by bulk copies
     float* d_gg;                // [N] g of w = g grad n (assembly -> w plane transforms)

@@ -738,27 +738,52 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
     rc = sorted_contract(c, c->d_epart + c->nb_point, want_pot ? 1 : 0, s, B);
     if (rc) return rc;
     mark(ST_CONTRACT);
+    // With a potential to follow (and no stage timing), the energy reduction
+    // runs on the context's side stream beside the inverse transforms, which
+    // do not touch the partial sums; the caller's stream waits for it before
+    // the call returns (so the next call's partial sums come after it).
+    bool forked = false;
+    auto join = [&]() {
+        if (forked) cudaStreamWaitEvent(s, c->ev_join, 0);
+        forked = false;
+    };
     if (E) {
         const double Omega = c->L[0] * c->L[1] * c->L[2];
         const double Nd = (double)g.N;
         double* escr = c->d_epart + c->nb_point + c->nb_sorted;
-        k_energy_split<<<dim3(EPART_SPLIT, B), ESPLIT_THREADS, 0, s>>>(c->d_epart, c->nb_point, c->nb_sorted, escr,
-                                                                       g.bs_epart);
-        k_energy_final<<<B, EPART_SPLIT, 0, s>>>(escr, Omega / Nd, 0.5 * Omega / (Nd * Nd), E, g.bs_epart);
+        cudaStream_t se = s;
+        if (want_pot && !c->prof) {
+            VDW_CUDA(cudaEventRecord(c->ev_fork, s));
+            VDW_CUDA(cudaStreamWaitEvent(c->s_side, c->ev_fork, 0));
+            se = c->s_side;
+        }
+        k_energy_split<<<dim3(EPART_SPLIT, B), ESPLIT_THREADS, 0, se>>>(c->d_epart, c->nb_point, c->nb_sorted, escr,
+                                                                        g.bs_epart);
+        k_energy_final<<<B, EPART_SPLIT, 0, se>>>(escr, Omega / Nd, 0.5 * Omega / (Nd * Nd), E, g.bs_epart);
+        if (se != s) {
+            VDW_CUDA(cudaEventRecord(c->ev_join, se));
+            forked = true;
+        }
         mark(ST_ENERGY);
     }
     if (xc && !want_pot)
         k_semilocal<<<XC_BLOCKS, 256, 0, s>>>(n, grad, g.N, P.n_min, nullptr, nullptr, c->d_xc + 4);
     if (want_pot) {
         rc = sorted_inverse(c, P.Nq, s, B);
-        if (rc) return rc;
+        if (rc) {
+            join();
+            return rc;
+        }
         mark(ST_PENCILS_INV);
         const int mode = (w != nullptr) ? 0 : 1;
         k_planes_inplace<CN1, CN3, true><<<dim3(g.N2, P.Nq, B), PLANE_THREADS, sp, s>>>(c->d_spec, g, c->d_tw,
                                                                                         c->bulk_planes, c->d_flags);
         mark(ST_PLANES_INV);
         const int rcs = launch_u_sum(c, n, grad, v, w, mode, s, B);
-        if (rcs) return rcs;
+        if (rcs) {
+            join();
+            return rcs;
+        }
         if (xc)
             k_semilocal<<<XC_BLOCKS, 256, 0, s>>>(n, grad, g.N, P.n_min, v, mode == 1 ? c->d_gg : nullptr,
                                                   c->d_xc + 4);
@@ -778,6 +803,7 @@ static int run_sized(vdw_ctx* c, const float* n, const float* grad, double* E, f
             mark(ST_DIV_FINAL);
         }
     }
+    join();
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
 }
