@@ -1347,15 +1347,39 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
         if (rc) return rc;
     }
     mark(ST_CONTRACT);
+    // as in the plain path: with a potential to follow (and no stage timing)
+    // the energy reduction runs on the side stream beside the inverse
+    // transforms, joined before the call returns
+    bool forked = false;
+    auto join = [&]() {
+        if (forked) cudaStreamWaitEvent(s, c->ev_join, 0);
+        forked = false;
+    };
     if (E) {
-        rc = pipeline_energy_final(c, ep, nb0, c->nb_sorted, E, s);
-        if (rc) return rc;
+        cudaStream_t se = s;
+        if (want_pot && kind != RUN_GRAD && !c->prof) {
+            VDW_CUDA(cudaEventRecord(c->ev_fork, s));
+            VDW_CUDA(cudaStreamWaitEvent(c->s_side, c->ev_fork, 0));
+            se = c->s_side;
+        }
+        rc = pipeline_energy_final(c, ep, nb0, c->nb_sorted, E, se);
+        if (se != s) {
+            VDW_CUDA(cudaEventRecord(c->ev_join, se));
+            forked = true;
+        }
+        if (rc) {
+            join();
+            return rc;
+        }
         mark(ST_ENERGY);
     }
     const int nb_pt = (int)std::min<long long>((g.N + 255) / 256, 1 << 16);
     if (kind == RUN_GRAD || want_pot) {
         rc = sorted_inverse(c, LRN_M, s);
-        if (rc) return rc;
+        if (rc) {
+            join();
+            return rc;
+        }
         mark(ST_PENCILS_INV);
     }
     if (kind == RUN_GRAD) {
@@ -1372,19 +1396,23 @@ int run(vdw_ctx* c, const float* n, const float* grad, double* E, float* v, floa
     } else if (want_pot) {
         const int mode = (w != nullptr) ? 0 : 1;
         rc = pipeline_planes_inplace(c, LRN_M, true, s);
-        if (rc) return rc;
-        mark(ST_PLANES_INV);
-        k_learned_usum<<<nb_pt, 256, 0, s>>>(specf, grad, g, c->d_lw, v, w, c->d_gg, mode);
-        mark(ST_USUM);
-        if (mode == 1) {
-            rc = pipeline_w_planes(c, grad, s);
-            if (rc) return rc;
-            mark(ST_W_PLANES);
-            rc = pipeline_divergence(c, v, s);
-            if (rc) return rc;
-            mark(ST_DIV_FINAL);
+        if (!rc) {
+            mark(ST_PLANES_INV);
+            k_learned_usum<<<nb_pt, 256, 0, s>>>(specf, grad, g, c->d_lw, v, w, c->d_gg, mode);
+            mark(ST_USUM);
         }
+        if (!rc && mode == 1) {
+            rc = pipeline_w_planes(c, grad, s);
+            if (!rc) {
+                mark(ST_W_PLANES);
+                rc = pipeline_divergence(c, v, s);
+            }
+            if (!rc) mark(ST_DIV_FINAL);
+        }
+        join();
+        if (rc) return rc;
     }
+    join();
     VDW_CUDA(cudaGetLastError());
     return VDW_OK;
 }

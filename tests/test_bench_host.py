@@ -35,7 +35,8 @@ def test_contraction_flops_and_fp32_peak():
 def test_traffic_reported_only_for_matching_sources(tmp_path, monkeypatch):
     csrc = tmp_path / "paper_0812_0244_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    (csrc / "a.cu").write_text("kernel one")
+    (csrc / "pipeline.cu").write_text("kernel one")
+    (csrc / "learned.cu").write_text("other kernels")
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     sha = bench.source_sha1()
@@ -43,7 +44,9 @@ def test_traffic_reported_only_for_matching_sources(tmp_path, monkeypatch):
         "# comment\nsource_sha1 %s\ncontract 123456\n" % sha)
     assert bench.captured_traffic("contract") == 123456
     assert bench.captured_traffic("usum") is None  # not captured
-    (csrc / "a.cu").write_text("kernel two")               # sources changed since the capture
+    (csrc / "learned.cu").write_text("other kernels, changed")  # not a plain-path source
+    assert bench.source_sha1() == sha
+    (csrc / "pipeline.cu").write_text("kernel two")               # sources changed since the capture
     assert bench.source_sha1() != sha
     assert bench.captured_traffic("contract") is None
 
